@@ -1,0 +1,108 @@
+"""Pins of the oracle's Peng-Robinson thermodynamics (Sec. II.C and Sec. IV.A of arXiv:1912.02018)."""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import synthetic_inputs as si
+from oracle import stepper
+from oracle.thermo import PR
+
+GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_constants.json")))
+
+
+def _sig(x, digits):
+    return float(f"{x:.{digits}g}")
+
+
+def paper_eos():
+    return PR(GOLD["eos_a"]["value"], GOLD["eos_b"]["value"], 1.0, GOLD["acentric"]["value"])
+
+
+def test_critical_constants_match_paper():
+    e = paper_eos()
+    assert _sig(e.Tc, 4) == GOLD["T_c"]["value"]
+    assert _sig(e.pc, 4) == GOLD["p_c"]["value"]
+    assert _sig(e.rho_c(), 4) == GOLD["rho_c"]["value"]
+
+
+def test_density_ratio_and_latent_heat_match_paper():
+    e = paper_eos()
+    T = GOLD["Tr_sat"]["value"] * e.Tc
+    rv, rl, _ = e.maxwell(T)
+    assert round(rl / rv) == GOLD["density_ratio"]["value"]
+    assert _sig(e.h_fg(T), 3) == GOLD["h_fg"]["value"]
+
+
+@pytest.mark.parametrize("Tr", [0.86, 0.90, 0.95])
+def test_maxwell_equals_closed_form_fugacity_equality(Tr):
+    # Textbook PR fugacity coefficient: ln phi = Z-1-ln(Z-B) - A/(2 sqrt2 B) ln((Z+(1+sqrt2)B)/(Z+(1-sqrt2)B)),
+    # A = a_T p/(RT)^2, B = b p/(RT).  Equal fugacities <=> Maxwell's equal-area rule.
+    e = PR(2 / 49, 2 / 21)
+    T = Tr * e.Tc
+    rv, rl, ps = e.maxwell(T)
+    assert abs(e.p(rv, T) - ps) < 1e-13 and abs(e.p(rl, T) - ps) < 1e-13
+    aT = e.a * e.phi(T)
+    A = aT * ps / T ** 2
+    B = e.b * ps / T
+    s2 = math.sqrt(2.0)
+
+    def lnphi(rho):
+        Z = ps / (rho * T)
+        return Z - 1 - math.log(Z - B) - A / (2 * s2 * B) * math.log((Z + (1 + s2) * B) / (Z + (1 - s2) * B))
+
+    assert abs(lnphi(rv) - lnphi(rl)) < 1e-10
+
+
+def test_maxwell_densities_do_not_depend_on_a_at_fixed_Tr():
+    r1 = PR(2 / 49, 2 / 21).maxwell(0.86 * PR(2 / 49, 2 / 21).Tc)
+    r2 = PR(3 / 49, 2 / 21).maxwell(0.86 * PR(3 / 49, 2 / 21).Tc)
+    assert abs(r1[0] - r2[0]) < 1e-10 and abs(r1[1] - r2[1]) < 1e-10
+
+
+def test_c_eos_matches_python_eos_and_dpdT_matches_difference():
+    case = si.SMALL
+    _, d = stepper.derive(case)
+    fn = stepper.eos_funcs(case)
+    e = d.eos
+    for rho in (0.3, 1.0, 2.6, 5.0, 6.5):
+        for T in (0.8 * e.Tc, d.T_sat, d.T_wall):
+            assert abs(fn["p"](rho, T) - e.p(rho, T)) < 1e-15
+            h = 1e-6 * T
+            fd = (e.p(rho, T + h) - e.p(rho, T - h)) / (2 * h)
+            assert abs(fn["dpdT"](rho, T) - fd) < 1e-7 * max(1.0, abs(fd))
+            assert abs(e.dp_dT(rho, T) - fd) < 1e-7 * max(1.0, abs(fd))
+
+
+def test_psi_definition_and_radicand_positive():
+    case = si.SMALL
+    _, d = stepper.derive(case)
+    fn = stepper.eos_funcs(case)
+    for rho in (d.rho_v, 1.0, 3.0, d.rho_l):
+        for T in (d.T_sat, d.T_wall):
+            psi = fn["psi"](rho, T)
+            assert psi > 0
+            # G cs^2 psi^2 / 2 = p - rho cs^2 with G = -1, Eq. (potential)
+            assert abs(-1.0 / 3.0 * psi ** 2 / 2 - (d.eos.p(rho, T) - rho / 3)) < 1e-14
+
+
+def test_gravity_from_froude_number_matches_paper():
+    g = GOLD["gravity"]
+    case = si.SMALL.replace(D=float(g["D"]), u_in=g["u_l"])
+    _, d = stepper.derive(case)
+    assert _sig(d.g, 3) == g["value"]
+    assert abs(case.u_in / math.sqrt(d.g * case.D) - g["froude"]) < 1e-12
+
+
+def test_transport_interpolation_between_phases():
+    case = si.SMALL.replace(nu_ratio=2.0, Pr_l=0.862, Pr_v=1.5)
+    _, d = stepper.derive(case)
+    fn = stepper.eos_funcs(case)
+    assert abs(fn["nu"](d.rho_l) - d.nu_l) < 1e-16 and abs(fn["nu"](d.rho_v) - d.nu_v) < 1e-16
+    assert abs(fn["nu"](100.0) - d.nu_l) < 1e-16 and abs(fn["nu"](0.01) - d.nu_v) < 1e-16
+    assert abs(fn["lambda"](d.rho_l) - d.rho_l * case.c_v * d.alpha_l) < 1e-15
+    assert abs(fn["lambda"](d.rho_v) - d.rho_v * case.c_v * d.alpha_v) < 1e-15
+    mid = 0.5 * (d.rho_l + d.rho_v)
+    assert np.isclose(fn["nu"](mid), 0.5 * (d.nu_l + d.nu_v), rtol=1e-14)
