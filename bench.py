@@ -1,0 +1,304 @@
+#!/usr/bin/env python
+"""Throughput of the boiling-LBM time step on GB300, printed as one JSON line.
+
+A step is one full lattice update of the workload (pull-streaming with boundary
+substitutions, rho/psi, interaction force, CM collision, wall heat flux, two Runge-Kutta
+stages of the temperature equation).  Default workload: the paper-shaped single domain,
+1536 x 768 lattice, cylinder D = 96 at (384, 384), Re = 300, superheat 0.10 Tc, FP32.
+
+  value      MLUPS over the K timed steps, inputs resident in HBM, L2 flushed (a 256 MB
+             write) before every timed step; CUDA events on the library's stream.
+  e2e        the same metric through the C ABI with host buffers: each step restores the
+             state from pinned host memory (lbm_set_state), steps once and reads T back
+             (lbm_fields) plus the heat flux.
+  roofline   the dominant kernel's algorithmic bytes per launch / its mean event-timed
+             duration, against the measured HBM copy bandwidth.
+  cpu_baseline  the FP64 CPU oracle on a bounded number of steps of the same workload.
+
+--impl reference times that oracle alone (the reference arm for this method: the
+paper ships no code).  Under torchrun (N > 1) every rank runs its own replica
+(replicas only: the method has no data-path exchange between independent domains).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import synthetic_inputs as si  # noqa: E402
+
+METRIC = "MLUPS and % HBM roofline per boiling step"
+UNIT = "MLUPS"
+WORKLOADS = {
+    "paper_shaped": si.PAPER_SHAPED.replace(warmup=0, name="1536x768_D96_Re300_dT0.10Tc_fp32"),
+    "precision": si.PRECISION.replace(warmup=0, name="2048x1024_D128_Re30000_dT0.20Tc_fp32"),
+    "small": si.SMALL.replace(name="128x64_D16_Re30_dT0.05Tc_fp32"),
+    "probe": si.cylinder_case(8192, 4096, 512.0, Re=300.0, superheat_Tc=0.1, name="8192x4096_D512_probe_fp32"),
+}
+# Algorithmic bytes per lattice update of each kernel (FP32 storage and compute): the
+# values a kernel must read and write by its contract, each once.
+ALG_BYTES = {
+    "k_rho_psi": 9 * 4 + 4 + 4,          # f in, T in, psi out
+    "k_collide": 9 * 4 + 4 + 9 * 4 + 12,  # f in, psi in, f* out, rho/ux/uy out
+    "k_T_stage1": 4 * 4 + 4,             # T, rho, ux, uy in; T1 out
+    "k_T_stage2": 5 * 4 + 4,             # T1, T, rho, ux, uy in; T out
+}
+STEP_ALG_BYTES = 9 * 4 * 2 + 4 * 2        # the whole step: populations and T in and out
+KERNEL_SRC = os.path.join(ROOT, "paper_1912_02018_gb300", "csrc", "lbm_kernels.cuh")
+
+
+def kernel_hash() -> str:
+    return hashlib.sha256(open(KERNEL_SRC, "rb").read()).hexdigest()[:16]
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def ncu_traffic(kernel: str, workload: str):
+    """Per-launch DRAM bytes from a committed ncu summary, if its kernel hash is current."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.md")
+    if not os.path.exists(path):
+        return None
+    txt = open(path).read()
+    h = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", txt)
+    t = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+    if not h or not t or h.group(1) != kernel_hash():
+        return None
+    return float(t.group(1))
+
+
+class Clocks:
+    """nvidia-smi sampler (every 200 ms) for SM clock and throttle reasons."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.rows = []
+        self.mark = None
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(index), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, ValueError):
+            self.p = None
+
+    def _read(self):
+        for line in self.p.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) == 7:
+                self.rows.append((time.time(), parts))
+
+    def window(self, t0, t1):
+        if self.p:
+            time.sleep(0.5)
+            self.p.terminate()
+        rows = [r for t, r in self.rows if t0 <= t <= t1] or [r for _, r in self.rows]
+        if not rows:
+            return None
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+
+        sm = [num(r[0]) for r in rows if num(r[0]) is not None]
+        mx = [num(r[1]) for r in rows if num(r[1]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[3 + k].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def oracle_sample(case, budget_s: float, max_steps: int):
+    """Time the FP64 oracle on the full workload for as many steps as fit in budget_s."""
+    from oracle import Oracle
+
+    o = Oracle(case, drho=case.drho())
+    t = time.perf_counter()
+    o.step(1)
+    t1 = time.perf_counter() - t
+    n = max(1, min(max_steps - 1, int(budget_s / max(t1, 1e-6)) - 1))
+    t = time.perf_counter()
+    o.step(n)
+    dt = time.perf_counter() - t
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    if os.environ.get("OMP_NUM_THREADS"):
+        cores = min(cores, int(os.environ["OMP_NUM_THREADS"]))
+    mlups = case.nx * case.ny * n / dt / 1e6
+    return {"value": mlups, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{n} FP64 oracle steps of the full {case.nx}x{case.ny} workload after 1 untimed step "
+                      f"({dt:.2f} s)"}, dt / n * 1e3, n
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    case = WORKLOADS[args.workload]
+    cpu, ms_per_step, n = oracle_sample(case, budget_s=min(120.0, 6.0 * max(args.steps, 1)), max_steps=args.steps + 1)
+    line = {"impl": "reference", "metric": METRIC, "value": cpu["value"], "unit": UNIT,
+            "n_gpus": args.gpus, "steps": n, "warmup": args.warmup, "ms_per_step": ms_per_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": case.name, "nx": case.nx, "ny": case.ny,
+                                            "D": case.D, "l2": "inputs larger than L2 (CPU run)"},
+            "cpu_baseline": cpu,
+            "e2e": {"value": cpu["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1912_02018_gb300 import Sim
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    case = WORKLOADS[args.workload]
+    nodes = case.nx * case.ny
+    sim = Sim.from_case(case, f64=False)  # seeded state generated on the device
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    clocks = Clocks(local) if rank == 0 else None
+    for _ in range(args.warmup):
+        flush.zero_()
+        sim.step(1)
+    sim.sync()
+    launches0 = sim.info()["kernel_launches"]
+    sim.profile(True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t_wall0 = time.time()
+    for k in range(args.steps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        sim.step(1)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    t_wall1 = time.time()
+    if world > 1:
+        dist.barrier()
+    sim.sync()
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    prof = sim.profile_read()
+    sim.profile(False)
+    launches = sim.info()["kernel_launches"] - launches0
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = nodes * args.steps * world / (ms / 1e3) / 1e6
+
+    # end to end through the C ABI with pinned host buffers
+    f0, T0, side0, n0 = sim.get_state()
+    f_h = torch.from_numpy(f0).pin_memory()
+    T_h = torch.from_numpy(T0).pin_memory()
+    out_h = torch.empty((case.ny, case.nx), dtype=torch.float64).pin_memory()
+    import ctypes as C
+
+    from paper_1912_02018_gb300 import _native as N
+
+    L = N.lib()
+    e2e_steps = max(1, min(args.steps, 10))
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    t = time.perf_counter()
+    for _ in range(e2e_steps):
+        N.check(L.lbm_set_state(sim.h, f_h.data_ptr(), T_h.data_ptr(), None, -1), sim.h)
+        N.check(L.lbm_step(sim.h, 1), sim.h)
+        N.check(L.lbm_fields(sim.h, N.FIELD_BITS["T"], out_h.data_ptr(), out_h.numel() * 8, 0), sim.h)
+        sim.heat_flux()
+    e2e_s = time.perf_counter() - t
+    if world > 1:
+        tt = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_s = float(tt.item())
+    e2e = {"value": nodes * e2e_steps * world / e2e_s / 1e6, "unit": UNIT,
+           "h2d_bytes_per_step": int(f_h.numel() * 8 + T_h.numel() * 8),
+           "d2h_bytes_per_step": int(out_h.numel() * 8 + 5 * 8), "steps": e2e_steps}
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return 0
+    clk = clocks.window(t_wall0, t_wall1) if clocks else None
+    peak, peak_kind = measured_peaks()
+    ours = {k: v for k, v in prof.items() if v[0] > 0}
+    dom = max(ours, key=lambda k: ours[k][1])
+    per_launch_ms = ours[dom][1] / ours[dom][0]
+    alg = ALG_BYTES.get(dom, 0) * nodes
+    achieved = alg / (per_launch_ms / 1e3) / 1e9
+    traffic = ncu_traffic(dom, args.workload)
+    kernels = {k: {"launches": v[0], "ms_total": round(v[1], 4), "share": round(v[1] / sum(x[1] for x in ours.values()), 4),
+                   "alg_bytes_per_lup": ALG_BYTES.get(k)} for k, v in ours.items()}
+    step_gbs = STEP_ALG_BYTES * nodes * args.steps / (ms / 1e3) / 1e9 / world
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": case.name, "nx": case.nx, "ny": case.ny, "D": case.D, "Re": case.Re,
+                   "superheat_Tc": case.superheat_Tc, "storage": "f32", "psi": "f64",
+                   "l2": "flushed (256 MB write) before every timed step", "parallelism": "replicas"},
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic, "peak_kind": f"{peak_kind} copy bandwidth",
+                     "alg_bytes_per_launch": alg},
+        "step_roofline": {"alg_bytes_per_lup": STEP_ALG_BYTES, "achieved_gbs": step_gbs, "frac": step_gbs / peak},
+        "kernels": kernels, "gpu_launches": launches, "e2e": e2e, "clocks": clk,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        cpu, _, _ = oracle_sample(case, budget_s=args.cpu_seconds, max_steps=10 ** 6)
+        line["cpu_baseline"] = cpu
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=50)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="paper_shaped")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

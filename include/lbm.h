@@ -1,0 +1,216 @@
+/*
+ * lbm.h - C ABI of the GB300 (sm_103a) implementation of the per-step update of the
+ * central-moment pseudopotential lattice Boltzmann model for forced-convection boiling
+ * on a heated cylinder (Saito, De Rosis, Fei, Luo, Ebihara, Kaneko, Abe,
+ * arXiv:1912.02018).
+ *
+ * One time step (lbm_step) is, in this order:
+ *   1. pull-streaming f_i(x) = f*_i(x - c_i)                     Eq. (streaming)
+ *      with a Zou-He velocity inlet at x = 0, a convective outlet at x = nx-1 and a
+ *      linear interpolated bounce-back (Bouzidi) on the cylinder  Sec. IV.A
+ *   2. rho = sum_i f_i and the pseudopotential psi(rho, T) of     Eq. (potential)
+ *      with the Peng-Robinson EOS                                 Eq. (eos)
+ *   3. the interaction force on the 24-neighbour stencil           Eq. (interForce)
+ *      plus gravity (rho - rho_l) g along -x                        Sec. IV.A
+ *   4. u from rho u = sum f c + F/2 and the CM collision with the
+ *      thermodynamic-consistency terms                             Eq. (postColl2)
+ *   5. a wall heat-flux sample -lambda dT/dn averaged over the
+ *      fluid nodes next to the cylinder                            Sec. IV.B
+ *   6. the temperature equation by two-stage Runge-Kutta with
+ *      third-order upwind convection and isotropic differences     Eq. (energy), Sec. II.C
+ * During the first warmup_steps steps the force and steps 5-6 are skipped (Sec. IV.A).
+ *
+ * Conventions shared by every entry point:
+ *   - Lattice units throughout.  The flow runs along +x; the domain is periodic in y
+ *     (and in x too when lbm_domain.periodic_x is set, which removes inlet and outlet).
+ *   - Host arrays are row-major [ny][nx] (node id = y*nx + x), populations
+ *     [9][ny][nx] in the D2Q9 order c_x = {0,1,-1,0,0,1,-1,1,-1},
+ *     c_y = {0,0,0,1,-1,1,-1,-1,1} of Eq. (velVec).  All host-side values are double.
+ *   - The library owns all device memory it allocates (through the caller's
+ *     allocator when one is given).  Buffers passed in are owned by the caller and
+ *     are not retained after the call returns.
+ *   - No exception crosses the ABI.  Every call returns an lbm_status; the text of the
+ *     last error of a context is available from lbm_last_error.
+ *   - lbm_step only enqueues work on the context's stream.  A fault detected by a
+ *     kernel (non-finite density, non-positive psi radicand) is latched on the device
+ *     and reported as LBM_EUNSTABLE by the next call that synchronises (lbm_sync,
+ *     lbm_fields, lbm_get_state, lbm_wall_heat_flux).
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm_ctx lbm_ctx; /* opaque, owned by the library */
+
+typedef enum {
+    LBM_OK = 0,
+    LBM_EINVAL = -1,    /* bad argument; nothing was changed */
+    LBM_ENOMEM = -2,    /* device allocation failed */
+    LBM_ECUDA = -3,     /* a CUDA runtime call failed */
+    LBM_EUNSTABLE = -4, /* a kernel saw a non-finite density or psi radicand <= 0 */
+    LBM_ETIMEOUT = -5,  /* reserved: a bounded device wait gave up */
+    LBM_ESTATE = -6     /* call not valid in the context's current state */
+} lbm_status;
+
+/* Population storage.  Arithmetic is FP64 when compute_f64 is set, FP32 otherwise;
+ * the pseudopotential (Eq. potential) is always evaluated in FP64 and the wall
+ * heat flux is always accumulated in FP64. */
+typedef enum { LBM_STORE_F64 = 0, LBM_STORE_F32 = 1 } lbm_storage;
+
+typedef struct {
+    int32_t nx, ny;     /* lattice size; nx, ny >= 5 */
+    int32_t periodic_x; /* 0: Zou-He inlet at x=0, convective outlet at x=nx-1; 1: periodic in x */
+    int32_t reserved;
+} lbm_domain;
+
+typedef struct {
+    double xc, yc;       /* centre; node (x, y) is solid iff (x-xc)^2 + (y-yc)^2 <= (D/2)^2 */
+    double D;            /* diameter; D <= 0 means no cylinder */
+    double superheat_Tc; /* wall superheat (T_w - T_sat) as a fraction of T_c, Sec. IV.A */
+    double rho_solid;    /* density given to solid nodes for psi; 0 means rho_l */
+} lbm_cylinder;
+
+typedef struct {
+    /* Peng-Robinson EOS, Eq. (eos): a, b, R, acentric factor; T_c = 0.0778 a / (0.4572 b R) */
+    double a, b, R, acentric;
+    double G;           /* interaction strength of Eq. (interForce)/(potential); < 0; 0 = single phase */
+    double sigma;       /* thermodynamic-consistency constant of Eq. (force2) */
+    double Tr_sat;      /* T_sat / T_c */
+    double Re;          /* Reynolds number u_in D / nu_l (used when nu_l == 0) */
+    double u_in;        /* inlet speed (and initial speed) */
+    double nu_l;        /* liquid kinematic viscosity; 0: u_in D / Re */
+    double nu_ratio;    /* eta = nu_l / nu_v */
+    double Pr_l, Pr_v;  /* Prandtl numbers: thermal diffusivity alpha = nu / Pr per phase */
+    double c_v;         /* specific heat */
+    double g;           /* gravity along -x; < 0: u_in^2 / (16 D), i.e. u_in / sqrt(g D) = 4 */
+    double outlet_U;    /* convective-outlet speed; < 0: u_in */
+    int64_t warmup_steps; /* steps with no force and no energy equation */
+    int32_t energy;       /* 1: solve Eq. (energy); 0: keep T fixed */
+    int32_t storage;      /* lbm_storage; must be LBM_STORE_F64 when compute_f64 = 1 */
+    int32_t compute_f64;  /* 1: FP64 arithmetic throughout (the parity build) */
+    int32_t reserved;
+    uint64_t seed;        /* SplitMix64 stream for the default density perturbation */
+    double noise_amp;     /* amplitude of that perturbation (uniform in +/- noise_amp) */
+} lbm_params;
+
+/* Optional initial fields (host, [ny][nx]); any pointer may be NULL.
+ * rho0 = (rho ? rho : rho_l) + (drho ? drho : SplitMix64(seed) noise of amplitude noise_amp),
+ * u0 = (ux, uy) or (u_in, 0), T0 = T or T_sat; solid nodes get rho_solid, u = 0, T_w.
+ * Populations start at the fourth-order Hermite equilibrium of Eq. (equi). */
+typedef struct {
+    const double *rho, *drho, *ux, *uy, *T;
+} lbm_init;
+
+/* Device allocator: alloc returns a device pointer of at least `bytes` bytes (aligned
+ * to 256 B) or NULL; free releases it.  NULL allocator: cudaMalloc / cudaFree. */
+typedef struct {
+    void *(*alloc)(size_t bytes, void *user);
+    void (*free)(void *ptr, void *user);
+    void *user;
+} lbm_allocator;
+
+/* Constants the library derived from the parameters (Sec. II.C, Sec. IV.A). */
+typedef struct {
+    double Tc, pc, T_sat, T_wall;
+    double rho_l, rho_v, p_sat;  /* Maxwell equal-area coexistence at T_sat */
+    double nu_l, nu_v, alpha_l, alpha_v, lambda_v, g, outlet_U;
+    int64_t steps;               /* steps taken so far */
+    int64_t n_boundary;          /* fluid nodes with a D2Q9 link into the cylinder */
+    int64_t kernel_launches;     /* kernels launched by this context so far */
+    int64_t device_bytes;        /* device memory held by this context */
+} lbm_info_t;
+
+/*
+ * Create a simulation.  Validates the parameters on the host (LBM_EINVAL: sizes,
+ * 0 < omega < 2 in both phases, psi radicand > 0 at T_sat and T_w for densities
+ * between rho_v and rho_l, cylinder at least 3 nodes from the inlet and outlet),
+ * computes the derived constants, builds the geometry tables, allocates device
+ * memory and writes the initial state.  cuda_stream is a cudaStream_t (NULL: the
+ * legacy default stream); all work of the context is issued on it.
+ * On success *out receives the handle, to be released with lbm_destroy.
+ */
+lbm_status lbm_create(const lbm_domain *domain, const lbm_cylinder *cyl, const lbm_params *params,
+                      const lbm_init *init, const lbm_allocator *alloc, void *cuda_stream, lbm_ctx **out);
+
+/* Enqueue n >= 0 time steps (the six parts listed at the top).  Asynchronous. */
+lbm_status lbm_step(lbm_ctx *ctx, int64_t n);
+
+/* Wait for the context's stream; LBM_EUNSTABLE if a kernel latched a fault. */
+lbm_status lbm_sync(lbm_ctx *ctx);
+
+/*
+ * Wall heat flux, Sec. IV.B: q(t) = mean over boundary fluid nodes b of
+ * -lambda(rho_b) grad T(x_b) . n_b, n_b the outward unit normal from the cylinder
+ * centre, grad T the isotropic gradient of the temperature entering the step.  One
+ * sample per step after the warm-up (when energy = 1).  Returns the last sample,
+ * the mean and standard deviation of the samples since creation or the last
+ * lbm_reset_heat_flux, the mean Nusselt number D <q> / (lambda_v (T_w - T_sat)),
+ * and the number of samples.  Any output pointer may be NULL.  Synchronises.
+ */
+lbm_status lbm_wall_heat_flux(lbm_ctx *ctx, double *q_now, double *q_mean, double *q_std, double *nu_mean,
+                              int64_t *n_samples);
+
+/* Restart the heat-flux averages (e.g. at the start of the quasi-steady window). */
+lbm_status lbm_reset_heat_flux(lbm_ctx *ctx);
+
+/* Field selection bits for lbm_fields. */
+#define LBM_FIELD_RHO 1u
+#define LBM_FIELD_UX 2u
+#define LBM_FIELD_UY 4u
+#define LBM_FIELD_T 8u
+#define LBM_FIELD_PSI 16u
+#define LBM_FIELD_SOLID 32u
+
+/*
+ * Copy macroscopic fields, as double, into dst: one [ny][nx] plane per set bit of
+ * mask, in increasing bit order.  rho and u are those of the last collision, psi
+ * that of the last step, T the current temperature; solid nodes report rho_solid,
+ * u = 0, T_w; SOLID is 1.0 on solid nodes.  bytes must be at least
+ * popcount(mask) * nx * ny * 8.  dst_on_device: 1 if dst is device memory.
+ * Synchronises.
+ */
+lbm_status lbm_fields(lbm_ctx *ctx, uint32_t mask, void *dst, size_t bytes, int dst_on_device);
+
+/*
+ * Checkpoint: post-collision populations f* ([9][ny][nx]), temperature ([ny][nx]),
+ * the outlet's last streamed values of f_2, f_6, f_8 ([3][ny]) and the step
+ * counter, as host doubles.  Any pointer may be NULL.  Synchronises.
+ */
+lbm_status lbm_get_state(lbm_ctx *ctx, double *f, double *T, double *side, int64_t *steps);
+
+/* Restore (any subset of) a checkpoint written by lbm_get_state; NULL keeps that part.
+ * steps < 0 keeps the step counter.  Host doubles are converted to the storage type. */
+lbm_status lbm_set_state(lbm_ctx *ctx, const double *f, const double *T, const double *side, int64_t steps);
+
+/* Derived constants and counters. */
+lbm_status lbm_info(lbm_ctx *ctx, lbm_info_t *info);
+
+/*
+ * Per-kernel timing with CUDA events on the context's stream.  lbm_profile(ctx, 1)
+ * starts recording an event pair around every kernel launch; lbm_profile_read
+ * synchronises and returns, for up to max_kernels kernels, the name (static
+ * string), the number of launches and the total milliseconds since profiling was
+ * enabled; *n_kernels receives the number of distinct kernels.
+ */
+lbm_status lbm_profile(lbm_ctx *ctx, int enable);
+lbm_status lbm_profile_read(lbm_ctx *ctx, const char **names, int64_t *launches, double *total_ms,
+                            int32_t max_kernels, int32_t *n_kernels);
+
+/* Text of the last error of ctx (never NULL); with ctx == NULL, that of the last
+ * failed lbm_create on this thread. */
+const char *lbm_last_error(const lbm_ctx *ctx);
+
+/* Release the context and all its device memory.  NULL is a no-op. */
+void lbm_destroy(lbm_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_H */

@@ -1,0 +1,18 @@
+"""GB300 (sm_103a) implementation of the per-step update of the central-moment
+pseudopotential lattice Boltzmann model for forced-convection boiling on a cylinder
+(Saito et al., arXiv:1912.02018).
+
+The compute path is the CUDA library liblbm.so (C ABI in include/lbm.h), built by
+build.py; this package only marshals arguments to it.  Importing works without a GPU;
+creating a Sim needs the built library and a CUDA device and fails loudly otherwise.
+"""
+from . import _native  # noqa: F401
+from .sim import Sim  # noqa: F401
+
+__all__ = ["Sim", "build"]
+
+
+def build(force: bool = False, verbose: bool = False) -> str:
+    from .build import build as _b
+
+    return _b(force=force, verbose=verbose)

@@ -1,0 +1,659 @@
+// Host side of the C ABI declared in include/lbm.h: parameter validation, the
+// derived thermodynamic constants (Peng-Robinson EOS and Maxwell's rule, Sec. II.C and
+// Sec. III.D of arXiv:1912.02018), the cylinder geometry tables (Sec. IV.A), device
+// memory, the step loop and state I/O.  All compute of a step runs in the kernels of
+// lbm_kernels.cuh; nothing here falls back to the CPU.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "lbm.h"
+#include "lbm_internal.h"
+
+namespace lbm {
+const char* const kKernelNames[kNumKernels] = {"k_rho_psi", "k_collide", "k_heat_flux", "k_T_stage1",
+                                               "k_T_stage2", "k_export", "k_import"};
+}  // namespace lbm
+
+namespace {
+
+thread_local std::string g_create_error;
+
+// ---------------------------------------------------------------- thermodynamics (host, FP64)
+// Peng-Robinson EOS, Eq. (eos): p = rho R T/(1 - b rho) - a phi(T) rho^2/(1 + 2 b rho - b^2 rho^2).
+struct PengRobinson {
+  double a, b, R, kappa, Tc;
+
+  double phi(double T) const {
+    double s = 1.0 + kappa * (1.0 - std::sqrt(T / Tc));
+    return s * s;
+  }
+  double p(double rho, double T) const {
+    return rho * R * T / (1.0 - b * rho) - a * phi(T) * rho * rho / (1.0 + 2.0 * b * rho - b * b * rho * rho);
+  }
+  double dp_drho(double rho, double T) const {
+    double D = 1.0 + 2.0 * b * rho - b * b * rho * rho;
+    double dD = 2.0 * b - 2.0 * b * b * rho;
+    double x = 1.0 - b * rho;
+    return R * T / (x * x) - a * phi(T) * (2.0 * rho * D - rho * rho * dD) / (D * D);
+  }
+  // Antiderivative of p with respect to the specific volume v = 1/rho:
+  // int RT/(v-b) dv = RT ln(v-b);  int dv/((v+b)^2 - 2b^2) = ln((v+b-sqrt2 b)/(v+b+sqrt2 b)) / (2 sqrt2 b).
+  double p_dv(double v, double T) const {
+    const double s2 = std::sqrt(2.0);
+    return R * T * std::log(v - b) - a * phi(T) / (2.0 * s2 * b) * std::log((v + b - s2 * b) / (v + b + s2 * b));
+  }
+  // Density where p = target on a monotonic branch [lo, hi] (bisection to the last bit).
+  double branch_root(double target, double lo, double hi, double T) const {
+    double flo = p(lo, T) - target;
+    for (int it = 0; it < 200; ++it) {
+      double mid = 0.5 * (lo + hi);
+      if (mid <= lo || mid >= hi) break;
+      double fm = p(mid, T) - target;
+      if ((fm < 0.0) == (flo < 0.0)) {
+        lo = mid;
+        flo = fm;
+      } else {
+        hi = mid;
+      }
+    }
+    return 0.5 * (lo + hi);
+  }
+  // Maxwell's equal-area rule: p(rho_v) = p(rho_l) = p_s and int_{v_l}^{v_v} p dv = p_s (v_v - v_l).
+  bool maxwell(double T, double& rho_v, double& rho_l, double& p_s) const {
+    const int n = 4000;
+    const double top = 1.0 / b;
+    double roots[2];
+    int nr = 0;
+    double prev = dp_drho(0.5 / n * top, T);
+    for (int k = 1; k < n && nr < 2; ++k) {
+      double r1 = (k + 0.5) / n * top;
+      double cur = dp_drho(r1, T);
+      if ((cur < 0.0) != (prev < 0.0)) {
+        double lo = (k - 0.5) / n * top, hi = r1, flo = prev;
+        for (int it = 0; it < 200; ++it) {
+          double mid = 0.5 * (lo + hi);
+          if (mid <= lo || mid >= hi) break;
+          double fm = dp_drho(mid, T);
+          if ((fm < 0.0) == (flo < 0.0)) {
+            lo = mid;
+            flo = fm;
+          } else {
+            hi = mid;
+          }
+        }
+        roots[nr++] = 0.5 * (lo + hi);
+      }
+      prev = cur;
+    }
+    if (nr != 2) return false;
+    const double ra = roots[0], rb = roots[1];
+    const double p_hi = p(ra, T);
+    double p_lo = p(rb, T);
+    if (p_lo < 1e-10 * p_hi) p_lo = 1e-10 * p_hi;
+    auto area = [&](double ps, double& rv, double& rl) {
+      rv = branch_root(ps, 0.0, ra, T);
+      rl = branch_root(ps, rb, (1.0 - 1e-12) * top, T);
+      double vv = 1.0 / rv, vl = 1.0 / rl;
+      return (p_dv(vv, T) - p_dv(vl, T)) - ps * (vv - vl);
+    };
+    double lo = p_lo + 1e-14 * (p_hi - p_lo), hi = p_hi - 1e-14 * (p_hi - p_lo), rv, rl;
+    double alo = area(lo, rv, rl);
+    for (int it = 0; it < 200; ++it) {
+      double mid = 0.5 * (lo + hi);
+      if (mid <= lo || mid >= hi) break;
+      double am = area(mid, rv, rl);
+      if ((am < 0.0) == (alo < 0.0)) {
+        lo = mid;
+        alo = am;
+      } else {
+        hi = mid;
+      }
+    }
+    p_s = 0.5 * (lo + hi);
+    area(p_s, rho_v, rho_l);
+    return rho_v > 0.0 && rho_l > rho_v;
+  }
+};
+
+// ---------------------------------------------------------------- helpers
+lbm_status fail(lbm_ctx* ctx, lbm_status st, const char* fmt, ...);
+
+}  // namespace
+
+struct lbm_ctx {
+  lbm::Geo geo{};
+  lbm::Phys ph{};
+  lbm::Dev dev{};
+  lbm_domain dom{};
+  lbm_cylinder cyl{};
+  lbm_params prm{};
+  lbm_allocator alloc{};
+  bool has_alloc = false;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  int cur = 0;
+  int64_t steps = 0;
+  int64_t launches = 0;
+  bool f64 = false;
+  double Tc = 0, pc = 0, p_sat = 0, lambda_v = 0;
+  std::vector<void*> blocks;
+  size_t bytes = 0;
+  std::string err = "no error";
+  // per-launch timing
+  struct Pending {
+    int kernel;
+    cudaEvent_t e0, e1;
+  };
+  bool prof = false;
+  std::vector<Pending> pending;
+  std::vector<cudaEvent_t> pool;
+  double prof_ms[lbm::kNumKernels] = {};
+  int64_t prof_n[lbm::kNumKernels] = {};
+  cudaEvent_t open_ev = nullptr;
+};
+
+namespace {
+
+lbm_status fail(lbm_ctx* ctx, lbm_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  std::vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  if (ctx) ctx->err = buf;
+  else g_create_error = buf;
+  return st;
+}
+
+#define LBM_CUDA(ctx, call)                                                                          \
+  do {                                                                                               \
+    cudaError_t e_ = (call);                                                                         \
+    if (e_ != cudaSuccess) return fail((ctx), LBM_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+void* dalloc(lbm_ctx* c, size_t bytes) {
+  bytes = (bytes + 255) & ~size_t(255);
+  void* p = nullptr;
+  if (c->has_alloc) {
+    p = c->alloc.alloc(bytes, c->alloc.user);
+  } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    p = nullptr;
+  }
+  if (p) {
+    c->blocks.push_back(p);
+    c->bytes += bytes;
+  }
+  return p;
+}
+
+void dfree_all(lbm_ctx* c) {
+  for (void* p : c->blocks) {
+    if (c->has_alloc) c->alloc.free(p, c->alloc.user);
+    else cudaFree(p);
+  }
+  c->blocks.clear();
+  c->bytes = 0;
+}
+
+void hook_before(void* self, int k) {
+  lbm_ctx* c = static_cast<lbm_ctx*>(self);
+  cudaEvent_t e;
+  if (!c->pool.empty()) {
+    e = c->pool.back();
+    c->pool.pop_back();
+  } else {
+    cudaEventCreate(&e);
+  }
+  cudaEventRecord(e, c->stream);
+  c->open_ev = e;
+  (void)k;
+}
+
+void hook_after(void* self, int k) {
+  lbm_ctx* c = static_cast<lbm_ctx*>(self);
+  cudaEvent_t e;
+  if (!c->pool.empty()) {
+    e = c->pool.back();
+    c->pool.pop_back();
+  } else {
+    cudaEventCreate(&e);
+  }
+  cudaEventRecord(e, c->stream);
+  c->pending.push_back({k, c->open_ev, e});
+}
+
+lbm_status check_status(lbm_ctx* c) {
+  int st = 0;
+  LBM_CUDA(c, cudaMemcpyAsync(&st, c->dev.status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+  if (st & 1) return fail(c, LBM_EUNSTABLE, "non-finite or non-positive density or velocity in the collision");
+  if (st & 2) return fail(c, LBM_EUNSTABLE, "pseudopotential radicand <= 0 (Eq. potential) at some node");
+  return LBM_OK;
+}
+
+int do_export(lbm_ctx* c, int which, double* dst) {
+  return c->f64 ? lbm::export_f64(c->geo, c->dev, c->cur, which, dst, c->stream)
+                : lbm::export_f32(c->geo, c->dev, c->cur, which, dst, c->stream);
+}
+int do_import(lbm_ctx* c, int which, const double* src) {
+  return c->f64 ? lbm::import_f64(c->geo, c->dev, c->cur, which, src, c->stream)
+                : lbm::import_f32(c->geo, c->dev, c->cur, which, src, c->stream);
+}
+
+}  // namespace
+
+extern "C" {
+
+lbm_status lbm_create(const lbm_domain* domain, const lbm_cylinder* cyl, const lbm_params* params,
+                      const lbm_init* init, const lbm_allocator* alloc, void* cuda_stream, lbm_ctx** out) {
+  g_create_error = "no error";
+  if (!domain || !cyl || !params || !out) return fail(nullptr, LBM_EINVAL, "NULL domain, cylinder, params or out");
+  *out = nullptr;
+  const lbm_domain& D = *domain;
+  const lbm_params& P = *params;
+  if (D.nx < 5 || D.ny < 5) return fail(nullptr, LBM_EINVAL, "nx and ny must be >= 5 (got %d x %d)", D.nx, D.ny);
+  if ((long long)D.nx * D.ny > (1ll << 31)) return fail(nullptr, LBM_EINVAL, "lattice too large");
+  if (P.compute_f64 && P.storage != LBM_STORE_F64)
+    return fail(nullptr, LBM_EINVAL, "compute_f64 = 1 needs storage = LBM_STORE_F64");
+  if (!P.compute_f64 && P.storage != LBM_STORE_F32)
+    return fail(nullptr, LBM_EINVAL, "FP32 compute needs storage = LBM_STORE_F32");
+  if (!(P.a > 0 && P.b > 0 && P.R > 0)) return fail(nullptr, LBM_EINVAL, "EOS constants a, b, R must be > 0");
+  if (P.G > 0) return fail(nullptr, LBM_EINVAL, "G must be <= 0 (Eq. potential needs G < 0; 0 = single phase)");
+  if (!(P.Tr_sat > 0 && P.Tr_sat < 1)) return fail(nullptr, LBM_EINVAL, "Tr_sat must lie in (0, 1)");
+  if (!(P.c_v > 0 && P.Pr_l > 0 && P.Pr_v > 0 && P.nu_ratio > 0))
+    return fail(nullptr, LBM_EINVAL, "c_v, Pr_l, Pr_v and nu_ratio must be > 0");
+  const bool has_cyl = cyl->D > 0;
+  if (has_cyl) {
+    const double r = 0.5 * cyl->D;
+    if (!D.periodic_x && (cyl->xc - r < 3.0 || cyl->xc + r > D.nx - 4.0))
+      return fail(nullptr, LBM_EINVAL, "cylinder must stay 3 nodes away from the inlet and outlet");
+    if (2.0 * r + 4.0 > D.ny) return fail(nullptr, LBM_EINVAL, "cylinder does not fit across the channel");
+  }
+
+  lbm_ctx* c = new lbm_ctx();
+  c->dom = D;
+  c->cyl = *cyl;
+  c->prm = P;
+  c->f64 = P.compute_f64 != 0;
+  c->stream = static_cast<cudaStream_t>(cuda_stream);
+  if (alloc && alloc->alloc && alloc->free) {
+    c->alloc = *alloc;
+    c->has_alloc = true;
+  }
+  cudaGetDevice(&c->device);
+
+  // derived constants, Sec. II.C and Sec. IV.A
+  PengRobinson eos;
+  eos.a = P.a;
+  eos.b = P.b;
+  eos.R = P.R;
+  eos.kappa = 0.37464 + 1.54226 * P.acentric - 0.26992 * P.acentric * P.acentric;
+  eos.Tc = 0.0778 * P.a / (0.4572 * P.b * P.R);
+  c->Tc = eos.Tc;
+  c->pc = 0.0778 * P.R * eos.Tc / P.b;
+  const double T_sat = P.Tr_sat * eos.Tc;
+  const double T_wall = T_sat + cyl->superheat_Tc * eos.Tc;
+  double rho_v, rho_l, p_s;
+  if (!eos.maxwell(T_sat, rho_v, rho_l, p_s)) {
+    delete c;
+    return fail(nullptr, LBM_EINVAL, "no liquid-vapour coexistence at T_sat = %g", T_sat);
+  }
+  c->p_sat = p_s;
+  lbm::Phys& ph = c->ph;
+  ph.a = P.a;
+  ph.b = P.b;
+  ph.R = P.R;
+  ph.kappa = eos.kappa;
+  ph.Tc = eos.Tc;
+  ph.G = P.G;
+  ph.sigma = P.sigma;
+  ph.T_sat = T_sat;
+  ph.T_wall = T_wall;
+  ph.rho_l = rho_l;
+  ph.rho_v = rho_v;
+  ph.rho_s = cyl->rho_solid > 0 ? cyl->rho_solid : rho_l;
+  ph.nu_l = P.nu_l > 0 ? P.nu_l : (P.Re > 0 ? P.u_in * cyl->D / P.Re : 0.0);
+  ph.nu_v = ph.nu_l / P.nu_ratio;
+  ph.alpha_l = ph.nu_l / P.Pr_l;
+  ph.alpha_v = ph.nu_v / P.Pr_v;
+  ph.c_v = P.c_v;
+  ph.g = P.g >= 0 ? P.g : (has_cyl ? P.u_in * P.u_in / (16.0 * cyl->D) : 0.0);
+  ph.u_in = P.u_in;
+  ph.U_out = P.outlet_U >= 0 ? P.outlet_U : P.u_in;
+  c->lambda_v = rho_v * P.c_v * ph.alpha_v;
+  for (double nu : {ph.nu_l, ph.nu_v}) {
+    const double omega = 1.0 / (nu * 3.0 + 0.5);
+    if (!(nu > 0) || !(omega > 0 && omega < 2)) {
+      delete c;
+      return fail(nullptr, LBM_EINVAL, "relaxation rate outside (0, 2): nu_l = %g, nu_v = %g", ph.nu_l, ph.nu_v);
+    }
+  }
+  if (P.G != 0) {
+    const double cs2 = 1.0 / 3.0;
+    for (double T : {T_sat, T_wall})
+      for (int k = 0; k <= 64; ++k) {
+        const double r = rho_v + (rho_l - rho_v) * k / 64.0;
+        if (!((eos.p(r, T) - r * cs2) / (P.G * cs2) > 0)) {
+          delete c;
+          return fail(nullptr, LBM_EINVAL, "psi radicand <= 0 at rho = %g, T = %g (Eq. potential)", r, T);
+        }
+      }
+  }
+
+  // geometry
+  lbm::Geo& g = c->geo;
+  g.nx = D.nx;
+  g.ny = D.ny;
+  g.pitch = (D.nx + 31) / 32 * 32;
+  g.periodic_x = D.periodic_x ? 1 : 0;
+  g.plane = (long long)g.ny * g.pitch;
+  g.xc = cyl->xc;
+  g.yc = cyl->yc;
+  g.r = has_cyl ? 0.5 * cyl->D : -1.0;
+  const long long plane = g.plane;
+  std::vector<uint8_t> mask(plane, 0);
+  auto solid_at = [&](int x, int y) {
+    if (!has_cyl) return false;
+    double dx = x - g.xc, dy = y - g.yc;
+    return dx * dx + dy * dy <= g.r * g.r;
+  };
+  for (int y = 0; y < g.ny; ++y)
+    for (int x = 0; x < g.nx; ++x)
+      if (solid_at(x, y)) mask[(long long)y * g.pitch + x] = lbm::kSolid;
+  std::vector<int> bnode;
+  std::vector<double> bnx, bny;
+  static const int CX[9] = {0, 1, -1, 0, 0, 1, -1, 1, -1};
+  static const int CY[9] = {0, 0, 0, 1, -1, 1, -1, -1, 1};
+  for (int y = 0; y < g.ny; ++y)
+    for (int x = 0; x < g.nx; ++x) {
+      const long long id = (long long)y * g.pitch + x;
+      if (mask[id] & lbm::kSolid) continue;
+      bool near = false;
+      for (int i = 1; i < 9 && !near; ++i) {
+        int sx = x - CX[i], sy = (y - CY[i] + g.ny) % g.ny;
+        if (g.periodic_x) sx = (sx + g.nx) % g.nx;
+        if (sx < 0 || sx >= g.nx) continue;
+        near = (mask[(long long)sy * g.pitch + sx] & lbm::kSolid) != 0;
+      }
+      if (near) {
+        mask[id] |= lbm::kNearWall;
+        double dx = x - g.xc, dy = y - g.yc, rr = std::sqrt(dx * dx + dy * dy);
+        bnode.push_back((int)id);
+        bnx.push_back(dx / rr);
+        bny.push_back(dy / rr);
+      }
+    }
+
+  // device memory
+  const size_t es = c->f64 ? sizeof(double) : sizeof(float);
+  const size_t N = (size_t)plane;
+  lbm::Dev& d = c->dev;
+  d.f[0] = dalloc(c, 9 * N * es);
+  d.f[1] = dalloc(c, 9 * N * es);
+  d.T = dalloc(c, N * es);
+  d.T1 = dalloc(c, N * es);
+  d.psi = dalloc(c, N * es);
+  d.rho = dalloc(c, N * es);
+  d.ux = dalloc(c, N * es);
+  d.uy = dalloc(c, N * es);
+  d.side = dalloc(c, 3 * (size_t)g.ny * es);
+  uint8_t* dmask = static_cast<uint8_t*>(dalloc(c, N));
+  d.mask = dmask;
+  d.nb = (int)bnode.size();
+  int* dbn = static_cast<int*>(dalloc(c, sizeof(int) * (bnode.size() + 1)));
+  double* dbv = static_cast<double*>(dalloc(c, sizeof(double) * (2 * bnode.size() + 1)));
+  d.bnode = dbn;
+  d.bn = dbv;
+  d.hf = static_cast<double*>(dalloc(c, 4 * sizeof(double)));
+  d.status = static_cast<int*>(dalloc(c, sizeof(int)));
+  d.stage = static_cast<double*>(dalloc(c, sizeof(double) * (size_t)g.nx * g.ny * 5));
+  if (!d.f[0] || !d.f[1] || !d.T || !d.T1 || !d.psi || !d.rho || !d.ux || !d.uy || !d.side || !dmask || !dbn ||
+      !dbv || !d.hf || !d.status || !d.stage) {
+    dfree_all(c);
+    delete c;
+    return fail(nullptr, LBM_ENOMEM, "device allocation failed");
+  }
+  std::vector<double> bnv(bnx);
+  bnv.insert(bnv.end(), bny.begin(), bny.end());
+  cudaError_t e = cudaSuccess;
+  auto chk = [&](cudaError_t r) {
+    if (e == cudaSuccess && r != cudaSuccess) e = r;
+  };
+  for (void* p : {d.T1, d.psi, d.side}) chk(cudaMemsetAsync(p, 0, p == d.side ? 3 * g.ny * es : N * es, c->stream));
+  chk(cudaMemsetAsync(d.hf, 0, 4 * sizeof(double), c->stream));
+  chk(cudaMemsetAsync(d.status, 0, sizeof(int), c->stream));
+  chk(cudaMemcpyAsync(dmask, mask.data(), N, cudaMemcpyHostToDevice, c->stream));
+  if (!bnode.empty()) {
+    chk(cudaMemcpyAsync(dbn, bnode.data(), sizeof(int) * bnode.size(), cudaMemcpyHostToDevice, c->stream));
+    chk(cudaMemcpyAsync(dbv, bnv.data(), sizeof(double) * bnv.size(), cudaMemcpyHostToDevice, c->stream));
+  }
+  // optional initial fields, staged through the export buffer (5 dense planes)
+  const size_t M = (size_t)g.nx * g.ny;
+  const double* src[5] = {init ? init->rho : nullptr, init ? init->drho : nullptr, init ? init->ux : nullptr,
+                          init ? init->uy : nullptr, init ? init->T : nullptr};
+  const double* dsrc[5] = {};
+  for (int k = 0; k < 5; ++k)
+    if (src[k]) {
+      chk(cudaMemcpyAsync(d.stage + k * M, src[k], M * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+      dsrc[k] = d.stage + k * M;
+    }
+  const int ok = c->f64 ? lbm::init_f64(g, ph, d, dsrc[0], dsrc[1], dsrc[2], dsrc[3], dsrc[4], P.seed, P.noise_amp,
+                                        c->stream)
+                        : lbm::init_f32(g, ph, d, dsrc[0], dsrc[1], dsrc[2], dsrc[3], dsrc[4], P.seed, P.noise_amp,
+                                        c->stream);
+  if (ok < 0) chk(cudaGetLastError());
+  chk(cudaMemcpyAsync(d.f[1], d.f[0], 9 * N * es, cudaMemcpyDeviceToDevice, c->stream));
+  chk(cudaStreamSynchronize(c->stream));
+  if (e != cudaSuccess) {
+    std::string m = cudaGetErrorString(e);
+    dfree_all(c);
+    delete c;
+    return fail(nullptr, LBM_ECUDA, "initialisation failed: %s", m.c_str());
+  }
+  c->launches = 1;
+  *out = c;
+  return LBM_OK;
+}
+
+lbm_status lbm_step(lbm_ctx* c, int64_t n) {
+  if (!c) return LBM_EINVAL;
+  if (n < 0) return fail(c, LBM_EINVAL, "negative step count");
+  lbm::LaunchHook hook{hook_before, hook_after, c};
+  const lbm::LaunchHook* hk = c->prof ? &hook : nullptr;
+  for (int64_t s = 0; s < n; ++s) {
+    const int forcing = c->steps >= c->prm.warmup_steps;
+    const int k = c->f64 ? lbm::step_f64(c->geo, c->ph, c->dev, c->cur, forcing, c->prm.energy, c->stream, hk)
+                         : lbm::step_f32(c->geo, c->ph, c->dev, c->cur, forcing, c->prm.energy, c->stream, hk);
+    if (k < 0) return fail(c, LBM_ECUDA, "kernel launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+    c->launches += k;
+    c->cur ^= 1;
+    c->steps++;
+  }
+  return LBM_OK;
+}
+
+lbm_status lbm_sync(lbm_ctx* c) {
+  if (!c) return LBM_EINVAL;
+  return check_status(c);
+}
+
+lbm_status lbm_wall_heat_flux(lbm_ctx* c, double* q_now, double* q_mean, double* q_std, double* nu_mean,
+                              int64_t* n_samples) {
+  if (!c) return LBM_EINVAL;
+  double hf[4];
+  LBM_CUDA(c, cudaMemcpyAsync(hf, c->dev.hf, sizeof(hf), cudaMemcpyDeviceToHost, c->stream));
+  lbm_status st = check_status(c);
+  if (st != LBM_OK) return st;
+  const double cnt = hf[3];
+  const double mean = cnt > 0 ? hf[1] / cnt : 0.0;
+  double var = cnt > 0 ? hf[2] / cnt - mean * mean : 0.0;
+  if (var < 0) var = 0;
+  const double dT = c->ph.T_wall - c->ph.T_sat;
+  if (q_now) *q_now = hf[0];
+  if (q_mean) *q_mean = mean;
+  if (q_std) *q_std = std::sqrt(var);
+  if (nu_mean) *nu_mean = (cnt > 0 && dT > 0) ? mean * c->cyl.D / (c->lambda_v * dT) : 0.0;
+  if (n_samples) *n_samples = (int64_t)cnt;
+  return LBM_OK;
+}
+
+lbm_status lbm_reset_heat_flux(lbm_ctx* c) {
+  if (!c) return LBM_EINVAL;
+  LBM_CUDA(c, cudaMemsetAsync(c->dev.hf, 0, 4 * sizeof(double), c->stream));
+  return LBM_OK;
+}
+
+lbm_status lbm_fields(lbm_ctx* c, uint32_t mask, void* dst, size_t bytes, int dst_on_device) {
+  if (!c || !dst) return LBM_EINVAL;
+  const size_t M = (size_t)c->geo.nx * c->geo.ny;
+  int planes = 0;
+  for (int b = 0; b < 6; ++b) planes += (mask >> b) & 1u;
+  if (mask >> 6) return fail(c, LBM_EINVAL, "unknown field bits 0x%x", mask);
+  if (bytes < planes * M * sizeof(double)) return fail(c, LBM_EINVAL, "dst too small for %d planes", planes);
+  double* out = static_cast<double*>(dst);
+  for (int b = 0; b < 6; ++b) {
+    if (!((mask >> b) & 1u)) continue;
+    if (do_export(c, b, c->dev.stage) < 0) return fail(c, LBM_ECUDA, "export kernel failed");
+    c->launches++;
+    LBM_CUDA(c, cudaMemcpyAsync(out, c->dev.stage, M * sizeof(double),
+                                dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
+    out += M;
+  }
+  return check_status(c);
+}
+
+lbm_status lbm_get_state(lbm_ctx* c, double* f, double* T, double* side, int64_t* steps) {
+  if (!c) return LBM_EINVAL;
+  const size_t M = (size_t)c->geo.nx * c->geo.ny;
+  if (f)
+    for (int i = 0; i < 9; ++i) {
+      if (do_export(c, 10 + i, c->dev.stage) < 0) return fail(c, LBM_ECUDA, "export kernel failed");
+      LBM_CUDA(c, cudaMemcpyAsync(f + i * M, c->dev.stage, M * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+      LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+    }
+  if (T) {
+    if (do_export(c, 3, c->dev.stage) < 0) return fail(c, LBM_ECUDA, "export kernel failed");
+    LBM_CUDA(c, cudaMemcpyAsync(T, c->dev.stage, M * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  }
+  if (side)
+    for (int j = 0; j < 3; ++j) {
+      if (do_export(c, 20 + j, c->dev.stage) < 0) return fail(c, LBM_ECUDA, "export kernel failed");
+      LBM_CUDA(c, cudaMemcpyAsync(side + j * c->geo.ny, c->dev.stage, c->geo.ny * sizeof(double),
+                                  cudaMemcpyDeviceToHost, c->stream));
+      LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+    }
+  if (steps) *steps = c->steps;
+  return check_status(c);
+}
+
+lbm_status lbm_set_state(lbm_ctx* c, const double* f, const double* T, const double* side, int64_t steps) {
+  if (!c) return LBM_EINVAL;
+  const size_t M = (size_t)c->geo.nx * c->geo.ny;
+  if (f)
+    for (int i = 0; i < 9; ++i) {
+      LBM_CUDA(c, cudaMemcpyAsync(c->dev.stage, f + i * M, M * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+      if (do_import(c, 10 + i, c->dev.stage) < 0) return fail(c, LBM_ECUDA, "import kernel failed");
+      LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+    }
+  if (T) {
+    LBM_CUDA(c, cudaMemcpyAsync(c->dev.stage, T, M * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    if (do_import(c, 3, c->dev.stage) < 0) return fail(c, LBM_ECUDA, "import kernel failed");
+    LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+  }
+  if (side)
+    for (int j = 0; j < 3; ++j) {
+      LBM_CUDA(c, cudaMemcpyAsync(c->dev.stage, side + j * c->geo.ny, c->geo.ny * sizeof(double),
+                                  cudaMemcpyHostToDevice, c->stream));
+      if (do_import(c, 20 + j, c->dev.stage) < 0) return fail(c, LBM_ECUDA, "import kernel failed");
+      LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+    }
+  if (steps >= 0) c->steps = steps;
+  return check_status(c);
+}
+
+lbm_status lbm_info(lbm_ctx* c, lbm_info_t* info) {
+  if (!c || !info) return LBM_EINVAL;
+  info->Tc = c->Tc;
+  info->pc = c->pc;
+  info->T_sat = c->ph.T_sat;
+  info->T_wall = c->ph.T_wall;
+  info->rho_l = c->ph.rho_l;
+  info->rho_v = c->ph.rho_v;
+  info->p_sat = c->p_sat;
+  info->nu_l = c->ph.nu_l;
+  info->nu_v = c->ph.nu_v;
+  info->alpha_l = c->ph.alpha_l;
+  info->alpha_v = c->ph.alpha_v;
+  info->lambda_v = c->lambda_v;
+  info->g = c->ph.g;
+  info->outlet_U = c->ph.U_out;
+  info->steps = c->steps;
+  info->n_boundary = c->dev.nb;
+  info->kernel_launches = c->launches;
+  info->device_bytes = (int64_t)c->bytes;
+  return LBM_OK;
+}
+
+lbm_status lbm_profile(lbm_ctx* c, int enable) {
+  if (!c) return LBM_EINVAL;
+  if (enable && !c->prof) {
+    LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+    for (auto& p : c->pending) {
+      c->pool.push_back(p.e0);
+      c->pool.push_back(p.e1);
+    }
+    c->pending.clear();
+    for (int k = 0; k < lbm::kNumKernels; ++k) {
+      c->prof_ms[k] = 0;
+      c->prof_n[k] = 0;
+    }
+  }
+  c->prof = enable != 0;
+  return LBM_OK;
+}
+
+lbm_status lbm_profile_read(lbm_ctx* c, const char** names, int64_t* launches, double* total_ms, int32_t max_kernels,
+                            int32_t* n_kernels) {
+  if (!c) return LBM_EINVAL;
+  LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+  for (auto& p : c->pending) {
+    float ms = 0;
+    if (cudaEventElapsedTime(&ms, p.e0, p.e1) == cudaSuccess) {
+      c->prof_ms[p.kernel] += ms;
+      c->prof_n[p.kernel] += 1;
+    }
+    c->pool.push_back(p.e0);
+    c->pool.push_back(p.e1);
+  }
+  c->pending.clear();
+  for (int k = 0; k < lbm::kNumKernels && k < max_kernels; ++k) {
+    if (names) names[k] = lbm::kKernelNames[k];
+    if (launches) launches[k] = c->prof_n[k];
+    if (total_ms) total_ms[k] = c->prof_ms[k];
+  }
+  if (n_kernels) *n_kernels = lbm::kNumKernels;
+  return LBM_OK;
+}
+
+const char* lbm_last_error(const lbm_ctx* c) { return c ? c->err.c_str() : g_create_error.c_str(); }
+
+void lbm_destroy(lbm_ctx* c) {
+  if (!c) return;
+  cudaStreamSynchronize(c->stream);
+  for (auto& p : c->pending) {
+    cudaEventDestroy(p.e0);
+    cudaEventDestroy(p.e1);
+  }
+  for (auto e : c->pool) cudaEventDestroy(e);
+  dfree_all(c);
+  delete c;
+}
+
+}  // extern "C"

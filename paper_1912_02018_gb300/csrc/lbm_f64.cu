@@ -1,0 +1,23 @@
+// FP64 instantiation of the step kernels: double populations and double arithmetic.
+// Built with --fmad=false so that every product and sum is rounded separately, in the
+// order the kernels spell out (the paper's equations term by term).
+#include "lbm_kernels.cuh"
+
+namespace lbm {
+
+int step_f64(const Geo& g, const Phys& ph, const Dev& d, int cur, int forcing, int energy, cudaStream_t s,
+             const LaunchHook* hook) {
+  return step_impl<double, double>(g, ph, d, cur, forcing, energy, s, hook);
+}
+int export_f64(const Geo& g, const Dev& d, int cur, int which, double* dst, cudaStream_t s) {
+  return export_impl<double, double>(g, d, cur, which, dst, s);
+}
+int import_f64(const Geo& g, const Dev& d, int cur, int which, const double* src, cudaStream_t s) {
+  return import_impl<double, double>(g, d, cur, which, src, s);
+}
+int init_f64(const Geo& g, const Phys& ph, const Dev& d, const double* rho0, const double* drho, const double* ux0,
+             const double* uy0, const double* T0, unsigned long long seed, double amp, cudaStream_t s) {
+  return init_impl<double, double>(g, ph, d, rho0, drho, ux0, uy0, T0, seed, amp, s);
+}
+
+}  // namespace lbm

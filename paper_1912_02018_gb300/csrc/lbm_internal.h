@@ -1,0 +1,81 @@
+// Internal interface between the C-ABI host layer (lbm_api.cu) and the kernels
+// (lbm_kernels.cuh, instantiated in lbm_f64.cu and lbm_f32.cu).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace lbm {
+
+// Node-type bits of the uint8 mask.
+constexpr uint8_t kSolid = 1;     // inside the cylinder
+constexpr uint8_t kNearWall = 2;  // fluid node with a D2Q9 neighbour inside the cylinder
+
+// Lattice geometry.  Arrays are [ny][pitch], pitch >= nx a multiple of 32 elements.
+struct Geo {
+  int nx, ny, pitch, periodic_x;
+  long long plane;  // elements per population plane = ny * pitch
+  double xc, yc, r; // cylinder centre and radius (r <= 0: none)
+};
+
+// Physical constants (all derived on the host in double).
+struct Phys {
+  double a, b, R, kappa, Tc, G, sigma;
+  double T_sat, T_wall;
+  double rho_l, rho_v, rho_s;
+  double nu_l, nu_v, alpha_l, alpha_v, c_v;
+  double g, u_in, U_out;
+};
+
+// Device buffers of one context (type-erased; element type is the storage / compute type).
+struct Dev {
+  void* f[2];        // populations, 9 planes each
+  void* T;           // temperature
+  void* T1;          // Runge-Kutta stage buffer
+  void* psi;         // pseudopotential of the current step
+  void* rho;         // density of the last collision
+  void* ux;          // velocity of the last collision
+  void* uy;
+  void* side;        // [3][ny] last streamed f_2, f_6, f_8 at the outlet column
+  const uint8_t* mask;
+  const int* bnode;  // boundary fluid nodes (y * pitch + x)
+  const double* bn;  // their outward normals, [2][nb]
+  int nb;
+  double* hf;        // heat-flux accumulators: last, sum, sum of squares, count
+  int* status;       // latched fault bits
+  double* stage;     // nx*ny doubles for exports/imports
+};
+
+// Kernel identifiers for per-launch timing.
+enum KernelId { kKRhoPsi = 0, kKCollide, kKHeatFlux, kKTStage1, kKTStage2, kKExport, kKImport, kNumKernels };
+extern const char* const kKernelNames[kNumKernels];
+
+// Per-launch hook: called before and after each kernel launch of a step.
+struct LaunchHook {
+  void (*before)(void* self, int kernel);
+  void (*after)(void* self, int kernel);
+  void* self;
+};
+
+// Step launchers (one per precision build).  cur: index of the buffer holding f*.
+// Returns the number of kernels launched, or -1 on a launch error.
+int step_f64(const Geo& g, const Phys& ph, const Dev& d, int cur, int forcing, int energy, cudaStream_t s,
+             const LaunchHook* hook);
+int step_f32(const Geo& g, const Phys& ph, const Dev& d, int cur, int forcing, int energy, cudaStream_t s,
+             const LaunchHook* hook);
+
+// Field export: copy a typed [ny][pitch] field (which: 0 rho, 1 ux, 2 uy, 3 T, 4 psi, 5 solid,
+// 10+i population plane i of buffer cur, 20+j outlet side row j) into a dense double buffer.
+int export_f64(const Geo& g, const Dev& d, int cur, int which, double* dst, cudaStream_t s);
+int export_f32(const Geo& g, const Dev& d, int cur, int which, double* dst, cudaStream_t s);
+// Field import: the reverse, for T (3), population planes (10+i) and side rows (20+j).
+int import_f64(const Geo& g, const Dev& d, int cur, int which, const double* src, cudaStream_t s);
+int import_f32(const Geo& g, const Dev& d, int cur, int which, const double* src, cudaStream_t s);
+// Initial state: populations at the Hermite equilibrium of (rho0 + drho, ux0, uy0), T = T0;
+// array arguments are dense [ny][nx] device doubles or NULL (see lbm_init in lbm.h).
+int init_f64(const Geo& g, const Phys& ph, const Dev& d, const double* rho0, const double* drho, const double* ux0,
+             const double* uy0, const double* T0, unsigned long long seed, double amp, cudaStream_t s);
+int init_f32(const Geo& g, const Phys& ph, const Dev& d, const double* rho0, const double* drho, const double* ux0,
+             const double* uy0, const double* T0, unsigned long long seed, double amp, cudaStream_t s);
+
+}  // namespace lbm

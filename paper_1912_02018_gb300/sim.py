@@ -1,0 +1,188 @@
+"""Python face of the C ABI: one simulation handle (argument marshalling only).
+
+Every step of the boiling update runs in the CUDA kernels behind liblbm.so; this
+module converts arguments, hands PyTorch's allocator and current stream to the
+library, and copies results into numpy / torch arrays.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from . import _native as N
+
+_PARAM_DEFAULTS = dict(a=2.0 / 49.0, b=2.0 / 21.0, R=1.0, acentric=0.344, G=-1.0, sigma=0.38, Tr_sat=0.86,
+                       Re=30.0, u_in=0.05, nu_l=0.0, nu_ratio=1.0, Pr_l=0.862, Pr_v=1.5, c_v=11.0, g=-1.0,
+                       outlet_U=-1.0, warmup=0, energy=1, seed=0, noise_amp=1e-4)
+
+
+def _dense(a, n):
+    if a is None:
+        return None
+    a = np.ascontiguousarray(a, dtype=np.float64).reshape(-1)
+    if a.size != n:
+        raise ValueError(f"initial field has {a.size} values, expected {n}")
+    return a
+
+
+class Sim:
+    """One boiling-on-a-cylinder simulation on the current CUDA device.
+
+    nx, ny, periodic_x             lattice (flow along +x; periodic in y)
+    D, xc, yc, superheat_Tc, rho_s  cylinder (D <= 0: none)
+    f64                            FP64 arithmetic and storage (else FP32)
+    init                           optional dict of [ny][nx] arrays: rho, drho, ux, uy, T
+    other keywords                 fields of lbm_params (see include/lbm.h)
+    torch_alloc                    device memory from PyTorch's caching allocator
+    """
+
+    def __init__(self, nx, ny, D=0.0, xc=0.0, yc=0.0, periodic_x=0, superheat_Tc=0.05, rho_s=0.0, f64=False,
+                 init=None, stream=None, torch_alloc=True, **params):
+        import torch
+
+        self._torch = torch
+        L = N.lib()
+        self.nx, self.ny, self.D = int(nx), int(ny), float(D)
+        kw = dict(_PARAM_DEFAULTS)
+        unknown = set(params) - set(kw)
+        if unknown:
+            raise TypeError(f"unknown parameters {sorted(unknown)}")
+        kw.update(params)
+        self.params = kw
+        dom = N.Domain(self.nx, self.ny, int(periodic_x), 0)
+        cyl = N.Cylinder(float(xc), float(yc), float(D), float(superheat_Tc), float(rho_s))
+        prm = N.Params(a=kw["a"], b=kw["b"], R=kw["R"], acentric=kw["acentric"], G=kw["G"], sigma=kw["sigma"],
+                       Tr_sat=kw["Tr_sat"], Re=kw["Re"], u_in=kw["u_in"], nu_l=kw["nu_l"],
+                       nu_ratio=kw["nu_ratio"], Pr_l=kw["Pr_l"], Pr_v=kw["Pr_v"], c_v=kw["c_v"], g=kw["g"],
+                       outlet_U=kw["outlet_U"], warmup_steps=int(kw["warmup"]), energy=int(kw["energy"]),
+                       storage=N.LBM_STORE_F64 if f64 else N.LBM_STORE_F32, compute_f64=1 if f64 else 0,
+                       reserved=0, seed=int(kw["seed"]), noise_amp=kw["noise_amp"])
+        n = self.nx * self.ny
+        init = init or {}
+        keep = {k: _dense(init.get(k), n) for k in ("rho", "drho", "ux", "uy", "T")}
+        ini = N.Init(*[keep[k].ctypes.data if keep[k] is not None else None
+                       for k in ("rho", "drho", "ux", "uy", "T")])
+        self.device = torch.cuda.current_device()
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self._blocks = {}
+        alloc_p = None
+        if torch_alloc:
+            dev = torch.device("cuda", self.device)
+
+            def _alloc(nbytes, user):
+                t = torch.empty(int(nbytes), dtype=torch.uint8, device=dev)
+                self._blocks[t.data_ptr()] = t
+                return t.data_ptr()
+
+            def _free(ptr, user):
+                self._blocks.pop(ptr, None)
+
+            self._alloc_cb = (N.ALLOC_FN(_alloc), N.FREE_FN(_free))
+            self._allocator = N.Allocator(self._alloc_cb[0], self._alloc_cb[1], None)
+            alloc_p = C.byref(self._allocator)
+        h = C.c_void_p()
+        N.check(L.lbm_create(C.byref(dom), C.byref(cyl), C.byref(prm), C.byref(ini), alloc_p,
+                             C.c_void_p(self.stream.cuda_stream), C.byref(h)))
+        self.h = h
+
+    @classmethod
+    def from_case(cls, case, f64=False, **kw):
+        """Build from an object with the attributes of a workload description (nx, ny, D, ...)."""
+        names = [k for k in _PARAM_DEFAULTS if hasattr(case, k) and k not in kw]
+        params = {k: getattr(case, k) for k in names}
+        if hasattr(case, "U_out") and "outlet_U" not in kw:
+            params["outlet_U"] = case.U_out
+        rho_s = getattr(case, "rho_s", 0.0)
+        return cls(case.nx, case.ny, D=case.D, xc=case.xc, yc=case.yc, periodic_x=case.periodic_x,
+                   superheat_Tc=case.superheat_Tc, rho_s=rho_s, f64=f64, **params, **kw)
+
+    # ------------------------------------------------------------------ lifecycle
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            N.lib().lbm_destroy(self.h)
+            self.h = None
+            self._blocks.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _chk(self, st):
+        N.check(st, self.h)
+
+    # ------------------------------------------------------------------ stepping
+    def step(self, n: int = 1):
+        self._chk(N.lib().lbm_step(self.h, int(n)))
+        return self
+
+    def sync(self):
+        self._chk(N.lib().lbm_sync(self.h))
+        return self
+
+    # ------------------------------------------------------------------ outputs
+    def heat_flux(self) -> dict:
+        v = [C.c_double() for _ in range(4)]
+        cnt = C.c_int64()
+        self._chk(N.lib().lbm_wall_heat_flux(self.h, *[C.byref(x) for x in v], C.byref(cnt)))
+        return {"q_now": v[0].value, "q_mean": v[1].value, "q_std": v[2].value, "nu_mean": v[3].value,
+                "count": cnt.value}
+
+    def reset_heat_flux(self):
+        self._chk(N.lib().lbm_reset_heat_flux(self.h))
+
+    def fields(self, names=("rho", "ux", "uy", "T", "psi")) -> dict:
+        mask = 0
+        for k in names:
+            mask |= N.FIELD_BITS[k]
+        order = [k for k in N.FIELD_BITS if mask & N.FIELD_BITS[k]]
+        out = np.empty((len(order), self.ny, self.nx))
+        self._chk(N.lib().lbm_fields(self.h, mask, out.ctypes.data, out.nbytes, 0))
+        return {k: out[i] for i, k in enumerate(order)}
+
+    def fields_device(self, names=("rho", "T")):
+        """Fields as a CUDA float64 tensor [len(names), ny, nx] (device-to-device copy)."""
+        torch = self._torch
+        mask = 0
+        for k in names:
+            mask |= N.FIELD_BITS[k]
+        order = [k for k in N.FIELD_BITS if mask & N.FIELD_BITS[k]]
+        out = torch.empty((len(order), self.ny, self.nx), dtype=torch.float64, device=f"cuda:{self.device}")
+        self._chk(N.lib().lbm_fields(self.h, mask, out.data_ptr(), out.numel() * 8, 1))
+        return out, order
+
+    def get_state(self):
+        n = self.nx * self.ny
+        f = np.empty((9, self.ny, self.nx))
+        T = np.empty((self.ny, self.nx))
+        side = np.empty((3, self.ny))
+        steps = C.c_int64()
+        self._chk(N.lib().lbm_get_state(self.h, f.ctypes.data, T.ctypes.data, side.ctypes.data, C.byref(steps)))
+        assert f.size == 9 * n
+        return f, T, side, steps.value
+
+    def set_state(self, f=None, T=None, side=None, steps=-1):
+        n = self.nx * self.ny
+        keep = [_dense(f, 9 * n), _dense(T, n), _dense(side, 3 * self.ny)]
+        ptrs = [a.ctypes.data if a is not None else None for a in keep]
+        self._chk(N.lib().lbm_set_state(self.h, *ptrs, int(steps)))
+
+    def info(self) -> dict:
+        inf = N.Info()
+        self._chk(N.lib().lbm_info(self.h, C.byref(inf)))
+        return {k: getattr(inf, k) for k, _ in N.Info._fields_}
+
+    # ------------------------------------------------------------------ timing
+    def profile(self, enable=True):
+        self._chk(N.lib().lbm_profile(self.h, 1 if enable else 0))
+
+    def profile_read(self) -> dict:
+        k = 16
+        names = (C.c_char_p * k)()
+        launches = (C.c_int64 * k)()
+        ms = (C.c_double * k)()
+        nk = C.c_int32()
+        self._chk(N.lib().lbm_profile_read(self.h, names, launches, ms, k, C.byref(nk)))
+        return {names[i].decode(): (launches[i], ms[i]) for i in range(nk.value) if names[i]}

@@ -1,0 +1,202 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Bars (from the method's precision targets): the FP64 build within 1e-12 relative on
+every field; FP32 within 1e-5 relative on rho and T after 200 steps.  The relative
+error of a field is max |gpu - oracle| / max |oracle| over fluid nodes.
+"""
+import numpy as np
+import pytest
+
+import synthetic_inputs as si
+from oracle import Oracle
+
+pytestmark = pytest.mark.gpu
+
+FIELDS = ("rho", "ux", "uy", "T", "psi")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+
+    from oracle import build as ob
+    from paper_1912_02018_gb300 import build
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    build()
+    ob.build()
+    torch.cuda.set_device(0)
+
+
+def Sim():
+    from paper_1912_02018_gb300 import Sim as S
+
+    return S
+
+
+def rel(a, b, fluid):
+    a, b = a[fluid], b[fluid]
+    den = np.abs(b).max()
+    return np.abs(a - b).max() / (den if den > 0 else 1.0)
+
+
+def pair(case, steps, f64, init=None):
+    init = dict(init or {})
+    if "drho" not in init and "rho" not in init:
+        init["drho"] = case.drho()
+    sim = Sim().from_case(case, f64=f64, init=init)
+    sim.step(steps)
+    ref = Oracle(case, **init).step(steps)
+    return sim, ref
+
+
+def assert_fields(sim, ref, tol, names=FIELDS):
+    got = sim.fields()
+    fluid = ref.field("solid") == 0
+    errs = {k: rel(got[k], ref.field(k), fluid) for k in names}
+    tols = tol if isinstance(tol, dict) else {k: tol for k in names}
+    bad = {k: v for k, v in errs.items() if not v <= tols[k]}
+    assert not bad, f"relative errors {errs}"
+    return errs
+
+
+def test_fp64_parity_1000_steps_plain_method_case():
+    case = si.SMALL  # 128x64, D=16 at (32,32), superheat 0.05 Tc, Re=30
+    sim, ref = pair(case, 1000, True)
+    assert_fields(sim, ref, 1e-12)
+    f, T, side, n = sim.get_state()
+    fluid = ref.field("solid") == 0
+    fr = ref.populations()
+    assert n == 1000
+    assert np.abs(f[:, fluid] - fr[:, fluid]).max() / np.abs(fr).max() < 1e-12
+    assert np.abs(side - ref.side()).max() / np.abs(ref.side()).max() < 1e-12
+    hg, hr = sim.heat_flux(), ref.heat_flux()
+    assert hg["count"] == hr["count"] == 1000
+    assert abs(hg["q_mean"] - hr["q_mean"]) <= 1e-12 * abs(hr["q_mean"])
+    assert abs(hg["q_now"] - hr["q_now"]) <= 1e-12 * abs(hr["q_now"])
+    assert abs(hg["nu_mean"] - hr["nu_mean"]) <= 1e-11 * abs(hr["nu_mean"])
+
+
+def test_fp32_parity_200_steps_plain_method_case():
+    case = si.SMALL
+    sim, ref = pair(case, 200, False)
+    errs = assert_fields(sim, ref, {"rho": 1e-5, "T": 1e-5}, names=("rho", "T"))
+    fluid = ref.field("solid") == 0
+    got = sim.fields()
+    for k in ("ux", "uy", "psi"):
+        errs[k] = rel(got[k], ref.field(k), fluid)
+    assert errs["ux"] < 1e-3 and errs["uy"] < 1e-3 and errs["psi"] < 1e-5, errs
+    hg, hr = sim.heat_flux(), ref.heat_flux()
+    assert abs(hg["q_mean"] - hr["q_mean"]) <= 1e-3 * abs(hr["q_mean"])
+
+
+def _two_phase_periodic():
+    c = si.Case(nx=40, ny=24, D=0.0, xc=0.0, yc=0.0, periodic_x=1, g=3e-5, u_in=0.0, nu_l=0.1,
+                superheat_Tc=0.0, noise_amp=0.0, name="periodic_two_phase")
+    rho = 3.4 + 0.6 * si.uniform_pm1(11, 40 * 24).reshape(24, 40)
+    return c, {"rho": rho, "ux": np.zeros((24, 40)), "uy": np.zeros((24, 40))}
+
+
+EDGE_CASES = {
+    "ragged_37x13_no_cylinder": (si.Case(nx=37, ny=13, D=0.0, xc=0.0, yc=0.0, Re=30.0, nu_l=0.04), None),
+    "minimal_5x5": (si.Case(nx=5, ny=5, D=0.0, xc=0.0, yc=0.0, nu_l=0.05), None),
+    "off_grid_cylinder_70x27": (si.Case(nx=70, ny=27, D=9.4, xc=20.3, yc=11.7, Re=40.0, superheat_Tc=0.08), None),
+    "periodic_two_phase": _two_phase_periodic(),
+    "single_phase_G0": (si.SMALL.replace(G=0.0, sigma=0.0), None),
+    "warmup_30": (si.SMALL.replace(warmup=30), None),
+    "viscosity_ratio_2": (si.SMALL.replace(nu_ratio=2.0, Pr_v=1.0), None),
+    "no_energy": (si.SMALL.replace(energy=0), None),
+}
+
+
+@pytest.mark.parametrize("name", sorted(EDGE_CASES))
+def test_fp64_parity_edge_cases(name):
+    case, init = EDGE_CASES[name]
+    sim, ref = pair(case, 60, True, init=init)
+    assert_fields(sim, ref, 1e-12)
+    hg, hr = sim.heat_flux(), ref.heat_flux()
+    assert hg["count"] == hr["count"]
+    if hr["count"]:
+        assert abs(hg["q_mean"] - hr["q_mean"]) <= 1e-12 * max(abs(hr["q_mean"]), 1e-300)
+
+
+@pytest.mark.parametrize("name", ["ragged_37x13_no_cylinder", "off_grid_cylinder_70x27", "periodic_two_phase"])
+def test_fp32_parity_edge_cases(name):
+    case, init = EDGE_CASES[name]
+    sim, ref = pair(case, 60, False, init=init)
+    assert_fields(sim, ref, {"rho": 1e-5, "T": 1e-5}, names=("rho", "T"))
+
+
+@pytest.mark.parametrize("case", [si.PAPER_SHAPED.replace(warmup=0), si.PRECISION.replace(warmup=0)],
+                         ids=lambda c: c.name)
+def test_fp32_full_size_first_steps_match_oracle(case):
+    # the benchmark's workloads at full size, two steps from the seeded state, every node
+    sim, ref = pair(case, 2, False)
+    assert_fields(sim, ref, {"rho": 1e-6, "T": 1e-6, "psi": 1e-6}, names=("rho", "T", "psi"))
+    fluid = ref.field("solid") == 0
+    got = sim.fields(("ux", "uy"))
+    umax = np.abs(ref.field("ux")[fluid]).max()
+    for k in ("ux", "uy"):
+        assert np.abs(got[k][fluid] - ref.field(k)[fluid]).max() < 1e-5 * umax
+
+
+def test_fp32_rest_state_stays_exactly_at_rest_at_full_size():
+    c = si.Case(nx=1536, ny=768, D=0.0, xc=0.0, yc=0.0, periodic_x=1, g=0.0, u_in=0.0, nu_l=0.02, noise_amp=0.0)
+    sim = Sim().from_case(c, f64=False, init={"ux": np.zeros((768, 1536)), "uy": np.zeros((768, 1536))})
+    sim.step(20)
+    f = sim.fields(("ux", "uy", "T"))
+    assert np.all(f["ux"] == 0) and np.all(f["uy"] == 0)
+    assert np.ptp(f["T"]) == 0
+
+
+def test_fp64_mass_conservation_periodic():
+    case, init = _two_phase_periodic()
+    sim = Sim().from_case(case, f64=True, init=init)
+    m0 = init["rho"].sum()
+    for _ in range(4):
+        sim.step(50)
+        assert abs(sim.fields(("rho",))["rho"].sum() - m0) / m0 < 1e-13
+
+
+def test_checkpoint_restart_is_bit_exact():
+    case = si.SMALL
+    drho = case.drho()
+    a = Sim().from_case(case, f64=True, init={"drho": drho}).step(30)
+    f, T, side, n = a.get_state()
+    a.step(20)
+    b = Sim().from_case(case, f64=True, init={"drho": drho})
+    b.set_state(f, T, side, n)
+    b.step(20)
+    fa, fb = a.fields(), b.fields()
+    for k in FIELDS:
+        assert np.array_equal(fa[k], fb[k]), k
+
+
+def test_torch_allocator_and_cudamalloc_agree():
+    case = si.SMALL
+    init = {"drho": case.drho()}
+    a = Sim().from_case(case, f64=False, init=init, torch_alloc=True).step(25)
+    b = Sim().from_case(case, f64=False, init=init, torch_alloc=False).step(25)
+    for k, v in a.fields().items():
+        assert np.array_equal(v, b.fields()[k]), k
+
+
+def test_library_default_noise_matches_seeded_input_generator():
+    case = si.SMALL.replace(seed=5, noise_amp=3e-4)
+    a = Sim().from_case(case, f64=True)  # the library draws SplitMix64(seed) itself
+    b = Sim().from_case(case, f64=True, init={"drho": case.drho()})
+    assert np.array_equal(a.fields(("rho",))["rho"], b.fields(("rho",))["rho"])
+
+
+def test_profile_counts_launches():
+    case = si.SMALL
+    sim = Sim().from_case(case, f64=False)
+    sim.profile(True)
+    sim.step(10)
+    prof = sim.profile_read()
+    assert prof["k_collide"][0] == 10 and prof["k_rho_psi"][0] == 10
+    assert prof["k_T_stage1"][0] == 10 and prof["k_heat_flux"][0] == 10
+    assert all(v[1] >= 0 for v in prof.values())
+    info = sim.info()
+    assert info["steps"] == 10 and info["kernel_launches"] >= 50
