@@ -548,6 +548,7 @@ static void pull_all(orc_t *o)
 
 static void heat_flux_sample(orc_t *o)
 {
+    if (o->nb == 0) return; /* no cylinder surface, no sample (Sec. IV.B) */
     double s = 0.0;
     for (int b = 0; b < o->nb; ++b) {
         int id = o->bnode[b], x = id % o->p.nx, y = id / o->p.nx;
@@ -555,7 +556,7 @@ static void heat_flux_sample(orc_t *o)
         iso_grad(o, o->T, x, y, &gx, &gy);
         s += -o->lam[id] * (gx * o->bnx[b] + gy * o->bny[b]);
     }
-    double q = o->nb > 0 ? s / o->nb : 0.0;
+    double q = s / o->nb;
     o->q_now = q;
     o->q_sum += q;
     o->q_sumsq += q * q;
