@@ -49,10 +49,8 @@ WORKLOADS = {
 # Algorithmic bytes per lattice update of each kernel (FP32 storage and compute): the
 # values a kernel must read and write by its contract, each once.
 ALG_BYTES = {
-    "k_rho_psi": 9 * 4 + 4 + 4,          # f in, T in, psi out
-    "k_collide": 9 * 4 + 4 + 9 * 4 + 12,  # f in, psi in, f* out, rho/ux/uy out
-    "k_T_stage1": 4 * 4 + 4,             # T, rho, ux, uy in; T1 out
-    "k_T_stage2": 5 * 4 + 4,             # T1, T, rho, ux, uy in; T out
+    "k_flow": 9 * 4 + 4 + 9 * 4 + 4 * 4,  # f, T in; f*, rho, ux, uy, psi out
+    "k_energy": 4 * 4 + 4,               # T, rho, ux, uy in; T out
 }
 STEP_ALG_BYTES = 9 * 4 * 2 + 4 * 2        # the whole step: populations and T in and out
 KERNEL_SRC = os.path.join(ROOT, "paper_1912_02018_gb300", "csrc", "lbm_kernels.cuh")

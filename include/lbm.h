@@ -58,9 +58,10 @@ typedef enum {
     LBM_ESTATE = -6     /* call not valid in the context's current state */
 } lbm_status;
 
-/* Population storage.  Arithmetic is FP64 when compute_f64 is set, FP32 otherwise;
- * the pseudopotential (Eq. potential) is always evaluated in FP64 and the wall
- * heat flux is always accumulated in FP64. */
+/* Population storage.  Arithmetic is FP64 when compute_f64 is set, FP32 otherwise.
+ * In the FP32 build the pseudopotential (Eq. potential) is evaluated with FP64-class
+ * accuracy by default (see lbm_params.psi_mode); the wall heat flux is always
+ * accumulated in FP64. */
 typedef enum { LBM_STORE_F64 = 0, LBM_STORE_F32 = 1 } lbm_storage;
 
 typedef struct {
@@ -94,7 +95,8 @@ typedef struct {
     int32_t energy;       /* 1: solve Eq. (energy); 0: keep T fixed */
     int32_t storage;      /* lbm_storage; must be LBM_STORE_F64 when compute_f64 = 1 */
     int32_t compute_f64;  /* 1: FP64 arithmetic throughout (the parity build) */
-    int32_t reserved;
+    int32_t psi_mode;     /* FP32 build only: how psi of Eq. (potential) is evaluated from FP32 rho, T:
+                             0 double-float (FP32 pairs, ~2^-44 relative), 1 IEEE FP64, 2 FP32 */
     uint64_t seed;        /* SplitMix64 stream for the default density perturbation */
     double noise_amp;     /* amplitude of that perturbation (uniform in +/- noise_amp) */
 } lbm_params;

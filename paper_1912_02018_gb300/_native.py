@@ -37,7 +37,7 @@ class Params(C.Structure):
                 ("u_in", C.c_double), ("nu_l", C.c_double), ("nu_ratio", C.c_double), ("Pr_l", C.c_double),
                 ("Pr_v", C.c_double), ("c_v", C.c_double), ("g", C.c_double), ("outlet_U", C.c_double),
                 ("warmup_steps", C.c_int64), ("energy", C.c_int32), ("storage", C.c_int32),
-                ("compute_f64", C.c_int32), ("reserved", C.c_int32), ("seed", C.c_uint64),
+                ("compute_f64", C.c_int32), ("psi_mode", C.c_int32), ("seed", C.c_uint64),
                 ("noise_amp", C.c_double)]
 
 

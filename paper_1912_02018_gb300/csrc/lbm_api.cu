@@ -16,8 +16,7 @@
 #include "lbm_internal.h"
 
 namespace lbm {
-const char* const kKernelNames[kNumKernels] = {"k_rho_psi", "k_collide", "k_heat_flux", "k_T_stage1",
-                                               "k_T_stage2", "k_export", "k_import"};
+const char* const kKernelNames[kNumKernels] = {"k_flow", "k_energy", "k_hf_reduce", "k_export", "k_import"};
 }  // namespace lbm
 
 namespace {
@@ -137,7 +136,8 @@ struct lbm_ctx {
   bool has_alloc = false;
   cudaStream_t stream = nullptr;
   int device = 0;
-  int cur = 0;
+  int cur = 0;   // buffer index of f* and the outlet side values
+  int tcur = 0;  // buffer index of T
   int64_t steps = 0;
   int64_t launches = 0;
   bool f64 = false;
@@ -239,12 +239,12 @@ lbm_status check_status(lbm_ctx* c) {
 }
 
 int do_export(lbm_ctx* c, int which, double* dst) {
-  return c->f64 ? lbm::export_f64(c->geo, c->dev, c->cur, which, dst, c->stream)
-                : lbm::export_f32(c->geo, c->dev, c->cur, which, dst, c->stream);
+  return c->f64 ? lbm::export_f64(c->geo, c->dev, c->cur, c->tcur, which, dst, c->stream)
+                : lbm::export_f32(c->geo, c->dev, c->cur, c->tcur, which, dst, c->stream);
 }
 int do_import(lbm_ctx* c, int which, const double* src) {
-  return c->f64 ? lbm::import_f64(c->geo, c->dev, c->cur, which, src, c->stream)
-                : lbm::import_f32(c->geo, c->dev, c->cur, which, src, c->stream);
+  return c->f64 ? lbm::import_f64(c->geo, c->dev, c->cur, c->tcur, which, src, c->stream)
+                : lbm::import_f32(c->geo, c->dev, c->cur, c->tcur, which, src, c->stream);
 }
 
 }  // namespace
@@ -264,6 +264,7 @@ lbm_status lbm_create(const lbm_domain* domain, const lbm_cylinder* cyl, const l
     return fail(nullptr, LBM_EINVAL, "compute_f64 = 1 needs storage = LBM_STORE_F64");
   if (!P.compute_f64 && P.storage != LBM_STORE_F32)
     return fail(nullptr, LBM_EINVAL, "FP32 compute needs storage = LBM_STORE_F32");
+  if (P.psi_mode < 0 || P.psi_mode > 2) return fail(nullptr, LBM_EINVAL, "psi_mode must be 0, 1 or 2");
   if (!(P.a > 0 && P.b > 0 && P.R > 0)) return fail(nullptr, LBM_EINVAL, "EOS constants a, b, R must be > 0");
   if (P.G > 0) return fail(nullptr, LBM_EINVAL, "G must be <= 0 (Eq. potential needs G < 0; 0 = single phase)");
   if (!(P.Tr_sat > 0 && P.Tr_sat < 1)) return fail(nullptr, LBM_EINVAL, "Tr_sat must lie in (0, 1)");
@@ -328,6 +329,19 @@ lbm_status lbm_create(const lbm_domain* domain, const lbm_cylinder* cyl, const l
   ph.u_in = P.u_in;
   ph.U_out = P.outlet_U >= 0 ? P.outlet_U : P.u_in;
   c->lambda_v = rho_v * P.c_v * ph.alpha_v;
+  auto split = [](double v) {
+    lbm::F2 r;
+    r.hi = (float)v;
+    r.lo = (float)(v - (double)r.hi);
+    return r;
+  };
+  ph.a2 = split(P.a);
+  ph.b2 = split(P.b);
+  ph.R2 = split(P.R);
+  ph.kappa2 = split(eos.kappa);
+  ph.invTc2 = split(1.0 / eos.Tc);
+  ph.cs22 = split(1.0 / 3.0);
+  ph.k2 = split(P.G != 0 ? 2.0 / (P.G * (1.0 / 3.0)) : 0.0);
   for (double nu : {ph.nu_l, ph.nu_v}) {
     const double omega = 1.0 / (nu * 3.0 + 0.5);
     if (!(nu > 0) || !(omega > 0 && omega < 2)) {
@@ -397,13 +411,15 @@ lbm_status lbm_create(const lbm_domain* domain, const lbm_cylinder* cyl, const l
   lbm::Dev& d = c->dev;
   d.f[0] = dalloc(c, 9 * N * es);
   d.f[1] = dalloc(c, 9 * N * es);
-  d.T = dalloc(c, N * es);
-  d.T1 = dalloc(c, N * es);
+  d.T[0] = dalloc(c, N * es);
+  d.T[1] = dalloc(c, N * es);
   d.psi = dalloc(c, N * es);
   d.rho = dalloc(c, N * es);
   d.ux = dalloc(c, N * es);
   d.uy = dalloc(c, N * es);
-  d.side = dalloc(c, 3 * (size_t)g.ny * es);
+  d.side[0] = dalloc(c, 3 * (size_t)g.ny * es);
+  d.side[1] = dalloc(c, 3 * (size_t)g.ny * es);
+  d.partial = static_cast<double*>(dalloc(c, sizeof(double) * lbm::energy_blocks(g.nx, g.ny)));
   uint8_t* dmask = static_cast<uint8_t*>(dalloc(c, N));
   d.mask = dmask;
   d.nb = (int)bnode.size();
@@ -414,8 +430,8 @@ lbm_status lbm_create(const lbm_domain* domain, const lbm_cylinder* cyl, const l
   d.hf = static_cast<double*>(dalloc(c, 4 * sizeof(double)));
   d.status = static_cast<int*>(dalloc(c, sizeof(int)));
   d.stage = static_cast<double*>(dalloc(c, sizeof(double) * (size_t)g.nx * g.ny * 5));
-  if (!d.f[0] || !d.f[1] || !d.T || !d.T1 || !d.psi || !d.rho || !d.ux || !d.uy || !d.side || !dmask || !dbn ||
-      !dbv || !d.hf || !d.status || !d.stage) {
+  if (!d.f[0] || !d.f[1] || !d.T[0] || !d.T[1] || !d.psi || !d.rho || !d.ux || !d.uy || !d.side[0] ||
+      !d.side[1] || !d.partial || !dmask || !dbn || !dbv || !d.hf || !d.status || !d.stage) {
     dfree_all(c);
     delete c;
     return fail(nullptr, LBM_ENOMEM, "device allocation failed");
@@ -426,7 +442,8 @@ lbm_status lbm_create(const lbm_domain* domain, const lbm_cylinder* cyl, const l
   auto chk = [&](cudaError_t r) {
     if (e == cudaSuccess && r != cudaSuccess) e = r;
   };
-  for (void* p : {d.T1, d.psi, d.side}) chk(cudaMemsetAsync(p, 0, p == d.side ? 3 * g.ny * es : N * es, c->stream));
+  chk(cudaMemsetAsync(d.psi, 0, N * es, c->stream));
+  for (void* p : {d.side[0], d.side[1]}) chk(cudaMemsetAsync(p, 0, 3 * g.ny * es, c->stream));
   chk(cudaMemsetAsync(d.hf, 0, 4 * sizeof(double), c->stream));
   chk(cudaMemsetAsync(d.status, 0, sizeof(int), c->stream));
   chk(cudaMemcpyAsync(dmask, mask.data(), N, cudaMemcpyHostToDevice, c->stream));
@@ -450,6 +467,8 @@ lbm_status lbm_create(const lbm_domain* domain, const lbm_cylinder* cyl, const l
                                         c->stream);
   if (ok < 0) chk(cudaGetLastError());
   chk(cudaMemcpyAsync(d.f[1], d.f[0], 9 * N * es, cudaMemcpyDeviceToDevice, c->stream));
+  chk(cudaMemcpyAsync(d.T[1], d.T[0], N * es, cudaMemcpyDeviceToDevice, c->stream));
+  chk(cudaMemcpyAsync(d.side[1], d.side[0], 3 * g.ny * es, cudaMemcpyDeviceToDevice, c->stream));
   chk(cudaStreamSynchronize(c->stream));
   if (e != cudaSuccess) {
     std::string m = cudaGetErrorString(e);
@@ -469,11 +488,15 @@ lbm_status lbm_step(lbm_ctx* c, int64_t n) {
   const lbm::LaunchHook* hk = c->prof ? &hook : nullptr;
   for (int64_t s = 0; s < n; ++s) {
     const int forcing = c->steps >= c->prm.warmup_steps;
-    const int k = c->f64 ? lbm::step_f64(c->geo, c->ph, c->dev, c->cur, forcing, c->prm.energy, c->stream, hk)
-                         : lbm::step_f32(c->geo, c->ph, c->dev, c->cur, forcing, c->prm.energy, c->stream, hk);
+    int flipped = 0;
+    const int k = c->f64 ? lbm::step_f64(c->geo, c->ph, c->dev, c->cur, c->tcur, forcing, c->prm.energy,
+                                         c->prm.psi_mode, c->stream, hk, &flipped)
+                         : lbm::step_f32(c->geo, c->ph, c->dev, c->cur, c->tcur, forcing, c->prm.energy,
+                                         c->prm.psi_mode, c->stream, hk, &flipped);
     if (k < 0) return fail(c, LBM_ECUDA, "kernel launch failed: %s", cudaGetErrorString(cudaGetLastError()));
     c->launches += k;
     c->cur ^= 1;
+    c->tcur ^= flipped;
     c->steps++;
   }
   return LBM_OK;

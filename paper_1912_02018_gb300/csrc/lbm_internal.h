@@ -18,6 +18,11 @@ struct Geo {
   double xc, yc, r; // cylinder centre and radius (r <= 0: none)
 };
 
+// A double-float value hi + lo (two FP32 words, |lo| <= ulp(hi)/2).
+struct F2 {
+  float hi, lo;
+};
+
 // Physical constants (all derived on the host in double).
 struct Phys {
   double a, b, R, kappa, Tc, G, sigma;
@@ -25,29 +30,42 @@ struct Phys {
   double rho_l, rho_v, rho_s;
   double nu_l, nu_v, alpha_l, alpha_v, c_v;
   double g, u_in, U_out;
+  // double-float copies of the EOS constants for the FP32 build's psi:
+  // a, b, R, kappa, 1/Tc, cs^2 = 1/3 and k = 2/(G cs^2)
+  F2 a2, b2, R2, kappa2, invTc2, cs22, k2;
 };
+
+// psi evaluation of the FP32 build (Eq. potential with Eq. eos); values of lbm_params.psi_mode.
+enum PsiMode { kPsiDF = 0, kPsiF64 = 1, kPsiF32 = 2 };
 
 // Device buffers of one context (type-erased; element type is the storage / compute type).
 struct Dev {
-  void* f[2];        // populations, 9 planes each
-  void* T;           // temperature
-  void* T1;          // Runge-Kutta stage buffer
+  void* f[2];        // populations, 9 planes each (ping-pong)
+  void* T[2];        // temperature (ping-pong)
   void* psi;         // pseudopotential of the current step
   void* rho;         // density of the last collision
   void* ux;          // velocity of the last collision
   void* uy;
-  void* side;        // [3][ny] last streamed f_2, f_6, f_8 at the outlet column
+  void* side[2];     // [3][ny] last streamed f_2, f_6, f_8 at the outlet column (ping-pong with f)
   const uint8_t* mask;
   const int* bnode;  // boundary fluid nodes (y * pitch + x)
   const double* bn;  // their outward normals, [2][nb]
   int nb;
   double* hf;        // heat-flux accumulators: last, sum, sum of squares, count
+  double* partial;   // one heat-flux partial sum per energy-kernel block
   int* status;       // latched fault bits
   double* stage;     // nx*ny doubles for exports/imports
 };
 
 // Kernel identifiers for per-launch timing.
-enum KernelId { kKRhoPsi = 0, kKCollide, kKHeatFlux, kKTStage1, kKTStage2, kKExport, kKImport, kNumKernels };
+enum KernelId { kKFlow = 0, kKEnergy, kKHeatFlux, kKExport, kKImport, kNumKernels };
+
+// Tile shapes (threads per block = tile nodes).
+constexpr int kFlowTX = 32, kFlowTY = 16;
+constexpr int kEnergyTX = 32, kEnergyTY = 16;
+inline int energy_blocks(int nx, int ny) {
+  return ((nx + kEnergyTX - 1) / kEnergyTX) * ((ny + kEnergyTY - 1) / kEnergyTY);
+}
 extern const char* const kKernelNames[kNumKernels];
 
 // Per-launch hook: called before and after each kernel launch of a step.
@@ -57,20 +75,23 @@ struct LaunchHook {
   void* self;
 };
 
-// Step launchers (one per precision build).  cur: index of the buffer holding f*.
+// Step launchers (one per precision build).  cur: index of the buffers holding f* and the
+// outlet side values; tcur: index of the temperature buffer.  The step writes f*, side into
+// [cur ^ 1] and, when it runs the energy equation, T into [tcur ^ 1] (*t_flipped = 1).
 // Returns the number of kernels launched, or -1 on a launch error.
-int step_f64(const Geo& g, const Phys& ph, const Dev& d, int cur, int forcing, int energy, cudaStream_t s,
-             const LaunchHook* hook);
-int step_f32(const Geo& g, const Phys& ph, const Dev& d, int cur, int forcing, int energy, cudaStream_t s,
-             const LaunchHook* hook);
+int step_f64(const Geo& g, const Phys& ph, const Dev& d, int cur, int tcur, int forcing, int energy, int psi_mode,
+             cudaStream_t s, const LaunchHook* hook, int* t_flipped);
+int step_f32(const Geo& g, const Phys& ph, const Dev& d, int cur, int tcur, int forcing, int energy, int psi_mode,
+             cudaStream_t s, const LaunchHook* hook, int* t_flipped);
 
 // Field export: copy a typed [ny][pitch] field (which: 0 rho, 1 ux, 2 uy, 3 T, 4 psi, 5 solid,
-// 10+i population plane i of buffer cur, 20+j outlet side row j) into a dense double buffer.
-int export_f64(const Geo& g, const Dev& d, int cur, int which, double* dst, cudaStream_t s);
-int export_f32(const Geo& g, const Dev& d, int cur, int which, double* dst, cudaStream_t s);
+// 10+i population plane i of buffer cur, 20+j outlet side row j of buffer cur) into a dense
+// double buffer.  T is taken from buffer tcur.
+int export_f64(const Geo& g, const Dev& d, int cur, int tcur, int which, double* dst, cudaStream_t s);
+int export_f32(const Geo& g, const Dev& d, int cur, int tcur, int which, double* dst, cudaStream_t s);
 // Field import: the reverse, for T (3), population planes (10+i) and side rows (20+j).
-int import_f64(const Geo& g, const Dev& d, int cur, int which, const double* src, cudaStream_t s);
-int import_f32(const Geo& g, const Dev& d, int cur, int which, const double* src, cudaStream_t s);
+int import_f64(const Geo& g, const Dev& d, int cur, int tcur, int which, const double* src, cudaStream_t s);
+int import_f32(const Geo& g, const Dev& d, int cur, int tcur, int which, const double* src, cudaStream_t s);
 // Initial state: populations at the Hermite equilibrium of (rho0 + drho, ux0, uy0), T = T0;
 // array arguments are dense [ny][nx] device doubles or NULL (see lbm_init in lbm.h).
 int init_f64(const Geo& g, const Phys& ph, const Dev& d, const double* rho0, const double* drho, const double* ux0,

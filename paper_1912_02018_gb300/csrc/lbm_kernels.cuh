@@ -2,13 +2,15 @@
 // templated on the compute type C (double or float) and population storage type S.
 //
 // Layout: structure of arrays, every field [ny][pitch] with x fastest; populations are
-// 9 such planes.  One thread per node, 32x8 thread blocks.  Each kernel is a single
-// pass over HBM:
-//   k_rho_psi   pull f (with boundary substitutions) -> rho -> psi(rho, T) in FP64
-//   k_collide   pull f again, interaction force from the psi stencil, CM collision,
-//               store f* (the other buffer), rho, u
-//   k_heat_flux wall heat flux over the boundary-node list (FP64 accumulation)
-//   k_T_stage   one Heun stage of the temperature equation
+// 9 such planes, ping-ponged between two buffers.  A step is two kernels plus a
+// one-block reduction:
+//   k_flow    per 32x16 tile: pull f with boundary substitutions, rho, psi(rho, T) on the
+//             tile and a 2-node halo (halo nodes re-pulled, psi kept in shared memory),
+//             interaction force, gravity, CM collision; writes f*, rho, u, psi.
+//   k_energy  per 32x16 tile: T, rho, u, lambda(rho) on a 4-node halo in shared memory,
+//             Heun stage 1 on a 2-node halo, stage 2 on the tile; writes T^{n+1} and a
+//             per-block partial of the wall heat flux (FP64).
+//   k_hf_reduce  fixed-order sum of the partials into the running heat-flux statistics.
 // The operation order inside each node follows the paper's equations term by term so
 // that the FP64 build (compiled without FMA contraction) rounds like a plain reference.
 #pragma once
@@ -20,9 +22,6 @@
 namespace lbm {
 namespace kern {
 
-constexpr int kBX = 32;
-constexpr int kBY = 8;
-
 // ---------------------------------------------------------------- lattice tables
 // D2Q9 velocities, Eq. (velVec).
 __device__ __forceinline__ constexpr int cxv(int i) {
@@ -31,9 +30,7 @@ __device__ __forceinline__ constexpr int cxv(int i) {
 __device__ __forceinline__ constexpr int cyv(int i) {
   return i == 3 || i == 5 || i == 8 ? 1 : (i == 4 || i == 6 || i == 7 ? -1 : 0);
 }
-__device__ __forceinline__ constexpr int oppv(int i) {
-  return i == 0 ? 0 : (i % 2 == 1 ? i + 1 : i - 1);
-}
+__device__ __forceinline__ constexpr int oppv(int i) { return i == 0 ? 0 : (i % 2 == 1 ? i + 1 : i - 1); }
 // The 24-neighbour stencil of Eq. (interForce) as 12 pairs (e, -e), with w(|e|^2).
 __device__ __forceinline__ constexpr int exv(int k) {
   return k == 0 ? 1 : k == 1 ? 2 : k == 2 ? -2 : k == 3 ? -1 : k == 4 ? 0 : k == 5 ? 1 : k == 6 ? 2
@@ -50,25 +47,83 @@ __device__ __forceinline__ constexpr double wiso(int k) {
 }
 
 // ---------------------------------------------------------------- addressing
-__device__ __forceinline__ int wrap_y(const Geo& g, int y) {  // offsets |dy| <= 2 < ny
-  return y < 0 ? y + g.ny : (y >= g.ny ? y - g.ny : y);
+// Node coordinate of an arbitrary lattice position for stencil reads: periodic in y; in x
+// periodic, or the nearest boundary column (zero-gradient ghost) at the inlet and outlet.
+__device__ __forceinline__ int map_y(const Geo& g, int y) {
+  y %= g.ny;
+  return y < 0 ? y + g.ny : y;
 }
-// x for a stencil read: periodic, or the nearest boundary column (zero-gradient ghost).
-__device__ __forceinline__ int stencil_x(const Geo& g, int x) {
-  if (g.periodic_x) return x < 0 ? x + g.nx : (x >= g.nx ? x - g.nx : x);
+__device__ __forceinline__ int map_x(const Geo& g, int x) {
+  if (g.periodic_x) {
+    x %= g.nx;
+    return x < 0 ? x + g.nx : x;
+  }
   return x < 0 ? 0 : (x >= g.nx ? g.nx - 1 : x);
 }
-template <typename C>
-__device__ __forceinline__ C at(const Geo& g, const C* __restrict__ fld, int x, int y) {
-  return fld[(long long)wrap_y(g, y) * g.pitch + stencil_x(g, x)];
+__device__ __forceinline__ int wrap_y(const Geo& g, int y) {  // offsets |dy| <= 2 < ny
+  return y < 0 ? y + g.ny : (y >= g.ny ? y - g.ny : y);
 }
 template <typename C, typename S>
 __device__ __forceinline__ C ldf(const Geo& g, const S* __restrict__ f, int i, int y, int x) {
   return static_cast<C>(f[i * g.plane + (long long)y * g.pitch + x]);
 }
 
+// ---------------------------------------------------------------- double-float arithmetic
+// Error-free transformations (Knuth's TwoSum, Dekker's FastTwoSum, FMA-based TwoProd) and
+// double-word operations after Joldes, Muller and Popescu, "Tight and rigorous error bounds
+// for basic building blocks of double-word arithmetic" (ACM TOMS 2017): about 2^-44
+// relative accuracy on the FP32 pipes.
+struct DF {
+  float hi, lo;
+};
+__device__ __forceinline__ DF two_sum(float a, float b) {
+  float s = __fadd_rn(a, b);
+  float bb = __fsub_rn(s, a);
+  float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return {s, e};
+}
+__device__ __forceinline__ DF fast_two_sum(float a, float b) {
+  float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ DF two_prod(float a, float b) {
+  float p = __fmul_rn(a, b);
+  return {p, __fmaf_rn(a, b, -p)};
+}
+__device__ __forceinline__ DF df_add(DF a, DF b) {
+  DF s = two_sum(a.hi, b.hi);
+  DF t = two_sum(a.lo, b.lo);
+  DF v = fast_two_sum(s.hi, __fadd_rn(s.lo, t.hi));
+  return fast_two_sum(v.hi, __fadd_rn(t.lo, v.lo));
+}
+__device__ __forceinline__ DF df_neg(DF a) { return {-a.hi, -a.lo}; }
+__device__ __forceinline__ DF df_sub(DF a, DF b) { return df_add(a, df_neg(b)); }
+__device__ __forceinline__ DF df_mul(DF a, DF b) {
+  DF c = two_prod(a.hi, b.hi);
+  float t = __fmaf_rn(a.lo, b.hi, __fmul_rn(a.hi, b.lo));
+  return fast_two_sum(c.hi, __fadd_rn(c.lo, t));
+}
+__device__ __forceinline__ DF df_mulf(DF a, float b) {
+  DF c = two_prod(a.hi, b);
+  return fast_two_sum(c.hi, __fmaf_rn(a.lo, b, c.lo));
+}
+__device__ __forceinline__ DF df_div(DF a, DF b) {
+  float q1 = __fdividef(a.hi, b.hi);
+  DF r = df_sub(a, df_mulf(b, q1));
+  float q2 = __fdividef(r.hi, b.hi);
+  DF q = fast_two_sum(q1, q2);
+  r = df_sub(a, df_mul(b, q));
+  return df_add(q, {__fdividef(r.hi, b.hi), 0.0f});
+}
+__device__ __forceinline__ DF df_sqrt(DF a) {
+  float s = __fsqrt_rn(a.hi);
+  DF r = df_sub(a, two_prod(s, s));
+  return fast_two_sum(s, __fdividef(r.hi, __fmul_rn(2.0f, s)));
+}
+__device__ __forceinline__ DF df_of(F2 v) { return {v.hi, v.lo}; }
+
 // ---------------------------------------------------------------- thermodynamics
-// Peng-Robinson EOS, Eq. (eos), and psi of Eq. (potential); FP64 in every build.
+// Peng-Robinson EOS, Eq. (eos), and psi of Eq. (potential) in IEEE FP64.
 __device__ __forceinline__ double psi_eos(const Phys& ph, double rho, double T, double& rad) {
   const double cs2 = 1.0 / 3.0;
   double s = 1.0 + ph.kappa * (1.0 - sqrt(T / ph.Tc));
@@ -78,6 +133,51 @@ __device__ __forceinline__ double psi_eos(const Phys& ph, double rho, double T, 
   double p = rep - att;
   rad = 2.0 * (p - rho * cs2) / (ph.G * cs2);
   return sqrt(rad);
+}
+// The same in double-float arithmetic (inputs and result FP32).
+__device__ __forceinline__ float psi_eos_df(const Phys& ph, float rho, float T, float& rad_hi) {
+  const DF one = {1.0f, 0.0f};
+  DF sq = df_sqrt(df_mulf(df_of(ph.invTc2), T));
+  DF s = df_add(one, df_mul(df_of(ph.kappa2), df_sub(one, sq)));
+  DF phi = df_mul(s, s);
+  DF brho = df_mulf(df_of(ph.b2), rho);
+  DF rep = df_div(df_mulf(df_mulf(df_of(ph.R2), T), rho), df_sub(one, brho));
+  DF den = df_sub(df_add(one, DF{2.0f * brho.hi, 2.0f * brho.lo}), df_mul(brho, brho));
+  DF att = df_div(df_mulf(df_mulf(df_mul(df_of(ph.a2), phi), rho), rho), den);
+  DF q = df_sub(df_sub(rep, att), df_mulf(df_of(ph.cs22), rho));
+  DF rad = df_mul(q, df_of(ph.k2));
+  rad_hi = rad.hi;
+  DF r = df_sqrt(rad);
+  return __fadd_rn(r.hi, r.lo);
+}
+// The same in plain FP32.
+__device__ __forceinline__ float psi_eos_f32(const Phys& ph, float rho, float T, float& rad) {
+  float s = 1.0f + ph.kappa2.hi * (1.0f - sqrtf(T * ph.invTc2.hi));
+  float phi = s * s;
+  float b = ph.b2.hi;
+  float rep = rho * ph.R2.hi * T / (1.0f - b * rho);
+  float att = ph.a2.hi * phi * rho * rho / (1.0f + 2.0f * b * rho - b * b * rho * rho);
+  rad = (rep - att - rho * ph.cs22.hi) * ph.k2.hi;
+  return sqrtf(rad);
+}
+template <typename C, int PSI>
+__device__ __forceinline__ C psi_of(const Phys& ph, C rho, C T, int* status) {
+  if constexpr (PSI == kPsiDF) {
+    float rad;
+    float p = psi_eos_df(ph, (float)rho, (float)T, rad);
+    if (!(rad > 0.0f)) atomicOr(status, 2);
+    return (C)p;
+  } else if constexpr (PSI == kPsiF32) {
+    float rad;
+    float p = psi_eos_f32(ph, (float)rho, (float)T, rad);
+    if (!(rad > 0.0f)) atomicOr(status, 2);
+    return (C)p;
+  } else {
+    double rad;
+    double p = psi_eos(ph, (double)rho, (double)T, rad);
+    if (!(rad > 0.0)) atomicOr(status, 2);
+    return (C)p;
+  }
 }
 // (dp/dT) at fixed rho, the derivative of Eq. (eos).
 template <typename C>
@@ -106,17 +206,18 @@ __device__ __forceinline__ C lam_of(const Phys& ph, C rho) {
   return rho * C(ph.c_v) * alpha;
 }
 
-// ---------------------------------------------------------------- stencils (Sec. II.C)
+// ---------------------------------------------------------------- stencils on tiles (Sec. II.C)
+// p points at the stencil centre of a row-major tile with row stride s.
 // Isotropic gradient sum_k w_k phi(x+e_k) e_k over +/- pairs.
 template <typename C, bool kX = true, bool kY = true>
-__device__ __forceinline__ void iso_grad(const Geo& g, const C* __restrict__ fld, int x, int y, C& gx, C& gy) {
+__device__ __forceinline__ void grad_t(const C* p, int s, C& gx, C& gy) {
   C sx = C(0), sy = C(0);
 #pragma unroll
   for (int k = 0; k < 12; ++k) {
     const int ex = exv(k), ey = eyv(k);
-    const C w = C(wiso(k));
     if ((kX && ex != 0) || (kY && ey != 0)) {
-      C d = at(g, fld, x + ex, y + ey) - at(g, fld, x - ex, y - ey);
+      const C w = C(wiso(k));
+      C d = p[ey * s + ex] - p[-ey * s - ex];
       if (kX && ex != 0) sx = sx + w * d * C(ex);
       if (kY && ey != 0) sy = sy + w * d * C(ey);
     }
@@ -126,66 +227,46 @@ __device__ __forceinline__ void iso_grad(const Geo& g, const C* __restrict__ fld
 }
 // Isotropic Laplacian 2 sum_k w_k (phi(x+e_k) - phi(x)) over +/- pairs.
 template <typename C>
-__device__ __forceinline__ C iso_lap(const Geo& g, const C* __restrict__ fld, int x, int y) {
-  C c = at(g, fld, x, y), s = C(0);
+__device__ __forceinline__ C lap_t(const C* p, int s) {
+  const C c = p[0];
+  C acc = C(0);
 #pragma unroll
   for (int k = 0; k < 12; ++k) {
     const int ex = exv(k), ey = eyv(k);
-    C d = (at(g, fld, x + ex, y + ey) + at(g, fld, x - ex, y - ey)) - C(2) * c;
-    s = s + C(wiso(k)) * d;
+    C d = (p[ey * s + ex] + p[-ey * s - ex]) - C(2) * c;
+    acc = acc + C(wiso(k)) * d;
   }
-  return C(2) * s;
+  return C(2) * acc;
 }
-// Isotropic gradient of lambda(rho), lambda evaluated at each stencil point.
+// Third-order upwind derivative along the direction with element step st, biased against v.
 template <typename C>
-__device__ __forceinline__ void iso_grad_lambda(const Geo& g, const Phys& ph, const C* __restrict__ rho, int x, int y,
-                                                C& gx, C& gy) {
-  C sx = C(0), sy = C(0);
-#pragma unroll
-  for (int k = 0; k < 12; ++k) {
-    const int ex = exv(k), ey = eyv(k);
-    const C w = C(wiso(k));
-    C d = lam_of(ph, at(g, rho, x + ex, y + ey)) - lam_of(ph, at(g, rho, x - ex, y - ey));
-    if (ex != 0) sx = sx + w * d * C(ex);
-    if (ey != 0) sy = sy + w * d * C(ey);
-  }
-  gx = sx;
-  gy = sy;
-}
-// Third-order upwind derivative along (dx, dy), biased against the sign of v.
-template <typename C>
-__device__ __forceinline__ C upwind3(const Geo& g, const C* __restrict__ fld, int x, int y, int dx, int dy, C v) {
-  C c = at(g, fld, x, y);
+__device__ __forceinline__ C upwind3_t(const C* p, int st, C v) {
+  const C c = p[0];
   if (v >= C(0)) {
-    C m2 = at(g, fld, x - 2 * dx, y - 2 * dy) - c;
-    C m1 = at(g, fld, x - dx, y - dy) - c;
-    C p1 = at(g, fld, x + dx, y + dy) - c;
+    C m2 = p[-2 * st] - c, m1 = p[-st] - c, p1 = p[st] - c;
     return (m2 - C(6) * m1 + C(2) * p1) / C(6);
-  } else {
-    C m1 = at(g, fld, x - dx, y - dy) - c;
-    C p1 = at(g, fld, x + dx, y + dy) - c;
-    C p2 = at(g, fld, x + 2 * dx, y + 2 * dy) - c;
-    return (-C(2) * m1 + C(6) * p1 - p2) / C(6);
   }
+  C m1 = p[-st] - c, p1 = p[st] - c, p2 = p[2 * st] - c;
+  return (-C(2) * m1 + C(6) * p1 - p2) / C(6);
 }
-
-// Right-hand side of Eq. (energy) with rho and u frozen.
+// Right-hand side of Eq. (energy) with rho and u frozen:
+// -u.grad T + (lambda lap T + grad lambda.grad T)/(rho c_v) - T (dp/dT)_rho div u / (rho c_v).
+// t: temperature stencil centre (row stride ts); lam, u, v, r: centres in tiles of stride as.
 template <typename C>
-__device__ C energy_rhs(const Geo& g, const Phys& ph, const C* __restrict__ T, const C* __restrict__ rho,
-                        const C* __restrict__ ux, const C* __restrict__ uy, int x, int y) {
-  const long long id = (long long)y * g.pitch + x;
-  const C r = rho[id], u = ux[id], v = uy[id], Tc = T[id];
-  C conv = u * upwind3(g, T, x, y, 1, 0, u) + v * upwind3(g, T, x, y, 0, 1, v);
+__device__ __forceinline__ C energy_rhs_t(const Phys& ph, const C* t, int ts, const C* lam, const C* u, const C* v,
+                                          const C* r, int as) {
+  const C r0 = r[0], u0 = u[0], v0 = v[0], T0 = t[0];
+  C conv = u0 * upwind3_t(t, 1, u0) + v0 * upwind3_t(t, ts, v0);
   C gx, gy, lx, ly, dxux, dyuy, unused;
-  iso_grad(g, T, x, y, gx, gy);
-  C lap = iso_lap(g, T, x, y);
-  iso_grad_lambda(g, ph, rho, x, y, lx, ly);
-  iso_grad<C, true, false>(g, ux, x, y, dxux, unused);
-  iso_grad<C, false, true>(g, uy, x, y, unused, dyuy);
+  grad_t(t, ts, gx, gy);
+  C lap = lap_t(t, ts);
+  grad_t(lam, as, lx, ly);
+  grad_t<C, true, false>(u, as, dxux, unused);
+  grad_t<C, false, true>(v, as, unused, dyuy);
   C divu = dxux + dyuy;
-  C diff = lam_of(ph, r) * lap + (lx * gx + ly * gy);
-  C work = Tc * dpdT_eos(ph, r, Tc) * divu;
-  return -conv + diff / (r * C(ph.c_v)) - work / (r * C(ph.c_v));
+  C diff = lam[0] * lap + (lx * gx + ly * gy);
+  C work = T0 * dpdT_eos(ph, r0, T0) * divu;
+  return -conv + diff / (r0 * C(ph.c_v)) - work / (r0 * C(ph.c_v));
 }
 
 // ---------------------------------------------------------------- streaming (Sec. IV.A BCs)
@@ -198,10 +279,13 @@ __device__ __forceinline__ double link_fraction(const Geo& g, int x, int y, int 
   return (-B - sqrt(B * B - A * C0)) / A;
 }
 
-// Pull with substitutions for nodes next to the wall, the inlet or the outlet.
-template <typename C, typename S, bool kWriteSide>
+// Pull with substitutions for nodes next to the wall, the inlet or the outlet: linear
+// interpolated bounce-back on the cylinder, Zou-He inlet, convective outlet.
+// side_out != nullptr: store the outlet's new streamed values there.
+template <typename C, typename S>
 __device__ __noinline__ void pull_slow(const Geo g, const Phys ph, const S* __restrict__ f,
-                                       const uint8_t* __restrict__ mask, C* side, int x, int y, C* fo) {
+                                       const uint8_t* __restrict__ mask, const C* __restrict__ side_in,
+                                       C* __restrict__ side_out, int x, int y, C* fo) {
   for (int i = 0; i < 9; ++i) {
     const int cx = cxv(i), cy = cyv(i);
     int sx = x - cx;
@@ -241,24 +325,23 @@ __device__ __noinline__ void pull_slow(const Geo g, const Phys ph, const S* __re
   if (x == g.nx - 1) {
     // convective outlet: f(t+1) = (f(t) + U f_{nx-2}(t+1)) / (1 + U) for f2, f6, f8
     const C U = C(ph.U_out);
-#pragma unroll
     for (int j = 0; j < 3; ++j) {
       const int i = j == 0 ? 2 : (j == 1 ? 6 : 8);
       const C inner = ldf<C>(g, f, i, wrap_y(g, y - cyv(i)), g.nx - 1);
-      const C v = (side[j * g.ny + y] + U * inner) / (C(1) + U);
+      const C v = (side_in[j * g.ny + y] + U * inner) / (C(1) + U);
       fo[i] = v;
-      if (kWriteSide) side[j * g.ny + y] = v;
+      if (side_out) side_out[j * g.ny + y] = v;
     }
   }
 }
 
-template <typename C, typename S, bool kWriteSide>
+template <typename C, typename S>
 __device__ __forceinline__ void pull_node(const Geo& g, const Phys& ph, const S* __restrict__ f,
-                                          const uint8_t* __restrict__ mask, C* side, int x, int y, uint8_t m,
-                                          C fo[9]) {
+                                          const uint8_t* __restrict__ mask, const C* __restrict__ side_in,
+                                          C* __restrict__ side_out, int x, int y, uint8_t m, C fo[9]) {
   const bool edge = !g.periodic_x && (x == 0 || x == g.nx - 1);
   if ((m & kNearWall) || edge) {
-    pull_slow<C, S, kWriteSide>(g, ph, f, mask, side, x, y, fo);
+    pull_slow<C, S>(g, ph, f, mask, side_in, side_out, x, y, fo);
     return;
   }
   const int ym = y == 0 ? g.ny - 1 : y - 1;
@@ -277,6 +360,26 @@ __device__ __forceinline__ void pull_node(const Geo& g, const Phys& ph, const S*
   fo[6] = ldf<C>(g, f, 6, yp, xp);
   fo[7] = ldf<C>(g, f, 7, yp, xm);
   fo[8] = ldf<C>(g, f, 8, ym, xp);
+}
+
+// psi at node (x, y): pull, rho = sum f, Eq. (potential); solid nodes use rho_s.
+template <typename C, typename S, int PSI>
+__device__ __forceinline__ C psi_node(const Geo& g, const Phys& ph, const S* __restrict__ f,
+                                      const C* __restrict__ T, const uint8_t* __restrict__ mask,
+                                      const C* __restrict__ side_in, int x, int y, int* status) {
+  const long long id = (long long)y * g.pitch + x;
+  const uint8_t m = mask[id];
+  C rho;
+  if (m & kSolid) {
+    rho = C(ph.rho_s);
+  } else {
+    C fo[9];
+    pull_node<C, S>(g, ph, f, mask, side_in, nullptr, x, y, m, fo);
+    rho = fo[0];
+#pragma unroll
+    for (int i = 1; i < 9; ++i) rho = rho + fo[i];
+  }
+  return psi_of<C, PSI>(ph, rho, T[id], status);
 }
 
 // ---------------------------------------------------------------- CM collision (Sec. II.A-B)
@@ -340,63 +443,65 @@ __device__ __forceinline__ void collide(const C f[9], C rho, C Fx, C Fy, C Fmx, 
   fs[8] = ((-q * ms5 + q * ms6) - q * ms7) + q * ms8;
 }
 
-// ---------------------------------------------------------------- kernels
-template <typename C, typename S>
-__global__ void __launch_bounds__(kBX* kBY) k_rho_psi(Geo g, Phys ph, const S* __restrict__ f,
-                                                      const C* __restrict__ T, const uint8_t* __restrict__ mask,
-                                                      C* side, C* __restrict__ psi, int* status) {
-  const int x = blockIdx.x * kBX + threadIdx.x;
-  const int y = blockIdx.y * kBY + threadIdx.y;
-  if (x >= g.nx || y >= g.ny) return;
+// ---------------------------------------------------------------- k_flow
+template <typename C, typename S, int PSI>
+__global__ void __launch_bounds__(kFlowTX* kFlowTY)
+    k_flow(Geo g, Phys ph, const S* __restrict__ f, S* __restrict__ fn, const C* __restrict__ T,
+           const uint8_t* __restrict__ mask, const C* __restrict__ side_in, C* __restrict__ side_out,
+           C* __restrict__ rho_o, C* __restrict__ ux_o, C* __restrict__ uy_o, C* __restrict__ psi_o, int forcing,
+           int* status) {
+  constexpr int HX = kFlowTX + 4, HY = kFlowTY + 4;
+  __shared__ C s_psi[HY * HX];
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int x0 = blockIdx.x * kFlowTX, y0 = blockIdx.y * kFlowTY;
+  const int x = x0 + tx, y = y0 + ty;
+  const bool inside = x < g.nx && y < g.ny;
+  const bool multiphase = ph.G != 0.0;
   const long long id = (long long)y * g.pitch + x;
-  const uint8_t m = mask[id];
-  double r;
-  if (m & kSolid) {
-    r = ph.rho_s;
-  } else {
-    C fo[9];
-    pull_node<C, S, false>(g, ph, f, mask, side, x, y, m, fo);
-    C s = fo[0];
+  C fo[9];
+  C rho = C(0);
+  uint8_t m = kSolid;
+  if (inside) {
+    m = mask[id];
+    if (!(m & kSolid)) {
+      pull_node<C, S>(g, ph, f, mask, side_in, side_out, x, y, m, fo);
+      rho = fo[0];
 #pragma unroll
-    for (int i = 1; i < 9; ++i) s = s + fo[i];
-    r = (double)s;
+      for (int i = 1; i < 9; ++i) rho = rho + fo[i];
+    } else {
+      rho = C(ph.rho_s);
+    }
   }
-  double rad;
-  const double p = psi_eos(ph, r, (double)T[id], rad);
-  if (!(rad > 0.0)) atomicOr(status, 2);
-  psi[id] = (C)p;
-}
-
-template <typename C, typename S>
-__global__ void __launch_bounds__(kBX* kBY) k_collide(Geo g, Phys ph, const S* __restrict__ f, S* __restrict__ fn,
-                                                      const C* __restrict__ psi, const uint8_t* __restrict__ mask,
-                                                      C* side, C* __restrict__ rho_o, C* __restrict__ ux_o,
-                                                      C* __restrict__ uy_o, int forcing, int* status) {
-  const int x = blockIdx.x * kBX + threadIdx.x;
-  const int y = blockIdx.y * kBY + threadIdx.y;
-  if (x >= g.nx || y >= g.ny) return;
-  const long long id = (long long)y * g.pitch + x;
-  const uint8_t m = mask[id];
+  C psi0 = C(0);
+  if (multiphase) {
+    if (inside) {
+      psi0 = psi_of<C, PSI>(ph, rho, T[id], status);
+      s_psi[(ty + 2) * HX + tx + 2] = psi0;
+    }
+    // halo (and positions past the domain edge): psi at the mapped node
+    for (int p = ty * kFlowTX + tx; p < HX * HY; p += kFlowTX * kFlowTY) {
+      const int hx = p % HX, hy = p / HX;
+      const int gx = x0 + hx - 2, gy = y0 + hy - 2;
+      const bool own = hx >= 2 && hx < kFlowTX + 2 && hy >= 2 && hy < kFlowTY + 2 && gx < g.nx && gy < g.ny;
+      if (!own) s_psi[p] = psi_node<C, S, PSI>(g, ph, f, T, mask, side_in, map_x(g, gx), map_y(g, gy), status);
+    }
+    __syncthreads();
+  }
+  if (!inside) return;
   if (m & kSolid) {
     rho_o[id] = C(ph.rho_s);
     ux_o[id] = C(0);
     uy_o[id] = C(0);
+    psi_o[id] = psi0;
     return;
   }
-  C fo[9];
-  pull_node<C, S, true>(g, ph, f, mask, side, x, y, m, fo);
-  C rho = fo[0];
-#pragma unroll
-  for (int i = 1; i < 9; ++i) rho = rho + fo[i];
-  const bool multiphase = ph.G != 0.0;
   const C cs2 = C(1.0 / 3.0);
-  C Fmx = C(0), Fmy = C(0), Fx = C(0), Fy = C(0), p0 = C(0);
-  if (multiphase) p0 = psi[id];
+  C Fmx = C(0), Fmy = C(0), Fx = C(0), Fy = C(0);
   if (forcing && multiphase) {
     C sx, sy;
-    iso_grad(g, psi, x, y, sx, sy);
-    Fmx = -C(ph.G) * cs2 * p0 * sx;
-    Fmy = -C(ph.G) * cs2 * p0 * sy;
+    grad_t(&s_psi[(ty + 2) * HX + tx + 2], HX, sx, sy);
+    Fmx = -C(ph.G) * cs2 * psi0 * sx;
+    Fmy = -C(ph.G) * cs2 * psi0 * sy;
   }
   if (forcing) {
     Fx = Fmx - (rho - C(ph.rho_l)) * C(ph.g);
@@ -405,67 +510,119 @@ __global__ void __launch_bounds__(kBX* kBY) k_collide(Geo g, Phys ph, const S* _
   const C omega = C(1) / (nu_of(ph, rho) / cs2 + C(0.5));
   const C sig = (forcing && multiphase) ? C(ph.sigma) : C(0);
   C fs[9], ux, uy;
-  collide(fo, rho, Fx, Fy, Fmx, Fmy, p0, omega, sig, fs, ux, uy);
+  collide(fo, rho, Fx, Fy, Fmx, Fmy, psi0, omega, sig, fs, ux, uy);
 #pragma unroll
   for (int i = 0; i < 9; ++i) fn[i * g.plane + id] = static_cast<S>(fs[i]);
   rho_o[id] = rho;
   ux_o[id] = ux;
   uy_o[id] = uy;
+  psi_o[id] = psi0;
   if (!(rho > C(0)) || !(ux == ux) || !(uy == uy)) atomicOr(status, 1);
 }
 
-template <typename C>
-__global__ void __launch_bounds__(256) k_heat_flux(Geo g, Phys ph, const C* __restrict__ T, const C* __restrict__ rho,
-                                                    const int* __restrict__ bnode, const double* __restrict__ bn,
-                                                    int nb, double* hf) {
-  double acc = 0.0;
-  for (int b = threadIdx.x; b < nb; b += blockDim.x) {
-    const int id = bnode[b];
-    const int y = id / g.pitch, x = id - y * g.pitch;
-    C gx, gy;
-    iso_grad(g, T, x, y, gx, gy);
-    const double lam = (double)lam_of(ph, rho[id]);
-    acc += -lam * ((double)gx * bn[b] + (double)gy * bn[nb + b]);
-  }
-  // fixed-shape tree: warp shuffles, then warp 0 over the 8 warp sums
+// ---------------------------------------------------------------- k_energy
+// Fixed-shape block sum (warp shuffles, then the first warp over the warp sums).
+template <int NT>
+__device__ __forceinline__ double block_sum(double v, double* red) {
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-  __shared__ double ws[8];
-  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = acc;
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  if ((tid & 31) == 0) red[tid >> 5] = v;
   __syncthreads();
-  if (threadIdx.x < 32) {
-    double v = threadIdx.x < (blockDim.x >> 5) ? ws[threadIdx.x] : 0.0;
+  double s = 0.0;
+  if (tid < 32) {
+    s = tid < NT / 32 ? red[tid] : 0.0;
 #pragma unroll
-    for (int o = 4; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    if (threadIdx.x == 0) {
-      const double q = nb > 0 ? v / nb : 0.0;
-      hf[0] = q;
-      hf[1] += q;
-      hf[2] += q * q;
-      hf[3] += 1.0;
-    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
   }
+  return s;  // valid in thread 0
 }
 
 template <typename C>
-__global__ void __launch_bounds__(kBX* kBY) k_T_stage(Geo g, Phys ph, const C* __restrict__ Tin, const C* Tbase,
-                                                      C* Tout, const C* __restrict__ rho, const C* __restrict__ ux,
-                                                      const C* __restrict__ uy, const uint8_t* __restrict__ mask,
-                                                      int stage) {
-  const int x = blockIdx.x * kBX + threadIdx.x;
-  const int y = blockIdx.y * kBY + threadIdx.y;
-  if (x >= g.nx || y >= g.ny) return;
-  const long long id = (long long)y * g.pitch + x;
-  C out;
-  if (mask[id] & kSolid) {
-    out = C(ph.T_wall);
-  } else if (!g.periodic_x && x == 0) {
-    out = C(ph.T_sat);
-  } else {
-    const C L = energy_rhs(g, ph, Tin, rho, ux, uy, x, y);
-    out = stage == 1 ? Tin[id] + L : ((Tbase[id] + Tin[id]) + L) * C(0.5);
+__global__ void __launch_bounds__(kEnergyTX* kEnergyTY)
+    k_energy(Geo g, Phys ph, const C* __restrict__ Tin, C* __restrict__ Tout, const C* __restrict__ rho,
+             const C* __restrict__ ux, const C* __restrict__ uy, const uint8_t* __restrict__ mask,
+             double* __restrict__ partial, int do_hf) {
+  constexpr int H = 4, AX = kEnergyTX + 2 * H, AY = kEnergyTY + 2 * H;  // inputs: tile + 4
+  constexpr int BX = kEnergyTX + 4, BY = kEnergyTY + 4;                 // stage 1: tile + 2
+  constexpr int NT = kEnergyTX * kEnergyTY;
+  __shared__ C sT[AY * AX], sL[AY * AX], sU[AY * AX], sV[AY * AX], sR[AY * AX];
+  __shared__ C sT1[BY * BX];
+  __shared__ uint8_t sM[AY * AX];
+  __shared__ double red[NT / 32];
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * kEnergyTX + tx;
+  const int x0 = blockIdx.x * kEnergyTX, y0 = blockIdx.y * kEnergyTY;
+  for (int p = tid; p < AX * AY; p += NT) {
+    const int gx = x0 + p % AX - H, gy = y0 + p / AX - H;
+    const long long nid = (long long)map_y(g, gy) * g.pitch + map_x(g, gx);
+    const C r = rho[nid];
+    sT[p] = Tin[nid];
+    sR[p] = r;
+    sL[p] = lam_of(ph, r);
+    sU[p] = ux[nid];
+    sV[p] = uy[nid];
+    sM[p] = mask[nid];
   }
-  Tout[id] = out;
+  __syncthreads();
+  // stage 1: T1 = T + L(T) on the tile and a 2-node halo
+  for (int p = tid; p < BX * BY; p += NT) {
+    const int bx = p % BX, by = p / BX;
+    const int gx = x0 + bx - 2;
+    if (!g.periodic_x && (gx < 0 || gx >= g.nx)) continue;  // filled from the edge column below
+    const int a = (by + 2) * AX + bx + 2;
+    C t1;
+    if (sM[a] & kSolid) t1 = C(ph.T_wall);
+    else if (!g.periodic_x && gx == 0) t1 = C(ph.T_sat);
+    else t1 = sT[a] + energy_rhs_t(ph, &sT[a], AX, &sL[a], &sU[a], &sV[a], &sR[a], AX);
+    sT1[p] = t1;
+  }
+  __syncthreads();
+  if (!g.periodic_x && (x0 < 2 || x0 + kEnergyTX + 2 > g.nx)) {
+    for (int p = tid; p < BX * BY; p += NT) {
+      const int bx = p % BX, by = p / BX;
+      const int gx = x0 + bx - 2;
+      if (gx < 0 || gx >= g.nx) sT1[p] = sT1[by * BX + (map_x(g, gx) - x0 + 2)];
+    }
+    __syncthreads();
+  }
+  const int x = x0 + tx, y = y0 + ty;
+  const bool inside = x < g.nx && y < g.ny;
+  const int a = (ty + H) * AX + tx + H, b = (ty + 2) * BX + tx + 2;
+  double q = 0.0;
+  if (inside) {
+    C out;
+    if (sM[a] & kSolid) out = C(ph.T_wall);
+    else if (!g.periodic_x && x == 0) out = C(ph.T_sat);
+    else out = ((sT[a] + sT1[b]) + energy_rhs_t(ph, &sT1[b], BX, &sL[a], &sU[a], &sV[a], &sR[a], AX)) * C(0.5);
+    Tout[(long long)y * g.pitch + x] = out;
+    if (do_hf && (sM[a] & kNearWall)) {
+      // wall heat flux -lambda grad T . n at this boundary node, from T^n (Sec. IV.B)
+      C gx, gy;
+      grad_t(&sT[a], AX, gx, gy);
+      const double dx = x - g.xc, dy = y - g.yc, rr = sqrt(dx * dx + dy * dy);
+      const double nxv = dx / rr, nyv = dy / rr;
+      q = -(double)sL[a] * ((double)gx * nxv + (double)gy * nyv);
+    }
+  }
+  if (do_hf) {
+    const double s = block_sum<NT>(q, red);
+    if (tid == 0) partial[blockIdx.y * gridDim.x + blockIdx.x] = s;
+  }
+}
+
+// One block: fixed-order sum of the per-block partials, then the running statistics.
+__global__ void __launch_bounds__(256) k_hf_reduce(const double* __restrict__ partial, int nblocks, int nb, double* hf) {
+  __shared__ double red[8];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < nblocks; i += 256) s += partial[i];
+  s = block_sum<256>(s, red);
+  if (threadIdx.x == 0) {
+    const double qv = s / nb;
+    hf[0] = qv;
+    hf[1] += qv;
+    hf[2] += qv * qv;
+    hf[3] += 1.0;
+  }
 }
 
 // ---------------------------------------------------------------- init / export / import
@@ -499,12 +656,12 @@ __device__ __forceinline__ double splitmix_pm1(unsigned long long seed, unsigned
 
 // in: optional dense [ny][nx] double arrays (rho, drho, ux, uy, T), any NULL.
 template <typename C, typename S>
-__global__ void __launch_bounds__(kBX* kBY) k_init(Geo g, Phys ph, const double* rho0, const double* drho,
-                                                   const double* ux0, const double* uy0, const double* T0,
-                                                   unsigned long long seed, double noise_amp, S* f, C* T, C* rho_o,
-                                                   C* ux_o, C* uy_o, C* side, const uint8_t* __restrict__ mask) {
-  const int x = blockIdx.x * kBX + threadIdx.x;
-  const int y = blockIdx.y * kBY + threadIdx.y;
+__global__ void __launch_bounds__(256) k_init(Geo g, Phys ph, const double* rho0, const double* drho,
+                                             const double* ux0, const double* uy0, const double* T0,
+                                             unsigned long long seed, double noise_amp, S* f, C* T, C* rho_o,
+                                             C* ux_o, C* uy_o, C* side, const uint8_t* __restrict__ mask) {
+  const int x = blockIdx.x * 32 + threadIdx.x;
+  const int y = blockIdx.y * 8 + threadIdx.y;
   if (x >= g.nx || y >= g.ny) return;
   const long long id = (long long)y * g.pitch + x;
   const long long k = (long long)y * g.nx + x;
@@ -561,53 +718,58 @@ __global__ void k_import(Geo g, E* __restrict__ dst, long long dst_pitch, int ro
 }  // namespace kern
 
 // ---------------------------------------------------------------- launchers
-template <typename C, typename S>
-int step_impl(const Geo& g, const Phys& ph, const Dev& d, int cur, int forcing, int energy, cudaStream_t s,
-              const LaunchHook* hook) {
+template <typename C, typename S, int PSI>
+int step_impl(const Geo& g, const Phys& ph, const Dev& d, int cur, int tcur, int forcing, int energy, cudaStream_t s,
+              const LaunchHook* hook, int* t_flipped) {
   using namespace kern;
-  const dim3 blk(kBX, kBY), grd((g.nx + kBX - 1) / kBX, (g.ny + kBY - 1) / kBY);
   const S* f = static_cast<const S*>(d.f[cur]);
   S* fn = static_cast<S*>(d.f[cur ^ 1]);
-  C* T = static_cast<C*>(d.T);
-  C* T1 = static_cast<C*>(d.T1);
-  C* psi = static_cast<C*>(d.psi);
+  const C* T = static_cast<const C*>(d.T[tcur]);
+  C* Tn = static_cast<C*>(d.T[tcur ^ 1]);
   C* rho = static_cast<C*>(d.rho);
   C* ux = static_cast<C*>(d.ux);
   C* uy = static_cast<C*>(d.uy);
-  C* side = static_cast<C*>(d.side);
+  C* psi = static_cast<C*>(d.psi);
+  const C* side_in = static_cast<const C*>(d.side[cur]);
+  C* side_out = static_cast<C*>(d.side[cur ^ 1]);
   int n = 0;
-  auto pre = [&](int k) { if (hook) hook->before(hook->self, k); };
-  auto post = [&](int k) { if (hook) hook->after(hook->self, k); ++n; };
-  if (ph.G != 0.0) {
-    pre(kKRhoPsi);
-    k_rho_psi<C, S><<<grd, blk, 0, s>>>(g, ph, f, T, d.mask, side, psi, d.status);
-    post(kKRhoPsi);
+  auto pre = [&](int k) {
+    if (hook) hook->before(hook->self, k);
+  };
+  auto post = [&](int k) {
+    if (hook) hook->after(hook->self, k);
+    ++n;
+  };
+  {
+    const dim3 blk(kFlowTX, kFlowTY), grd((g.nx + kFlowTX - 1) / kFlowTX, (g.ny + kFlowTY - 1) / kFlowTY);
+    pre(kKFlow);
+    k_flow<C, S, PSI><<<grd, blk, 0, s>>>(g, ph, f, fn, T, d.mask, side_in, side_out, rho, ux, uy, psi, forcing,
+                                          d.status);
+    post(kKFlow);
   }
-  pre(kKCollide);
-  k_collide<C, S><<<grd, blk, 0, s>>>(g, ph, f, fn, psi, d.mask, side, rho, ux, uy, forcing, d.status);
-  post(kKCollide);
+  *t_flipped = 0;
   if (energy && forcing) {
-    if (d.nb > 0) {
+    const int do_hf = d.nb > 0;
+    const dim3 blk(kEnergyTX, kEnergyTY), grd((g.nx + kEnergyTX - 1) / kEnergyTX, (g.ny + kEnergyTY - 1) / kEnergyTY);
+    pre(kKEnergy);
+    k_energy<C><<<grd, blk, 0, s>>>(g, ph, T, Tn, rho, ux, uy, d.mask, d.partial, do_hf);
+    post(kKEnergy);
+    if (do_hf) {
       pre(kKHeatFlux);
-      k_heat_flux<C><<<1, 256, 0, s>>>(g, ph, T, rho, d.bnode, d.bn, d.nb, d.hf);
+      k_hf_reduce<<<1, 256, 0, s>>>(d.partial, (int)(grd.x * grd.y), d.nb, d.hf);
       post(kKHeatFlux);
     }
-    pre(kKTStage1);
-    k_T_stage<C><<<grd, blk, 0, s>>>(g, ph, T, T, T1, rho, ux, uy, d.mask, 1);
-    post(kKTStage1);
-    pre(kKTStage2);
-    k_T_stage<C><<<grd, blk, 0, s>>>(g, ph, T1, T, T, rho, ux, uy, d.mask, 2);
-    post(kKTStage2);
+    *t_flipped = 1;
   }
   return cudaPeekAtLastError() == cudaSuccess ? n : -1;
 }
 
 template <typename C, typename S>
-int export_impl(const Geo& g, const Dev& d, int cur, int which, double* dst, cudaStream_t s) {
+int export_impl(const Geo& g, const Dev& d, int cur, int tcur, int which, double* dst, cudaStream_t s) {
   using namespace kern;
   const dim3 blk(256);
   if (which >= 20 && which < 23) {
-    const C* src = static_cast<const C*>(d.side) + (which - 20) * g.ny;
+    const C* src = static_cast<const C*>(d.side[cur]) + (which - 20) * g.ny;
     k_export<C><<<dim3((g.ny + 255) / 256, 1), blk, 0, s>>>(g, src, g.ny, 1, dst, g.ny);
   } else if (which >= 10 && which < 19) {
     const S* src = static_cast<const S*>(d.f[cur]) + (which - 10) * g.plane;
@@ -615,24 +777,25 @@ int export_impl(const Geo& g, const Dev& d, int cur, int which, double* dst, cud
   } else if (which == 5) {
     k_export_solid<<<dim3((g.nx + 255) / 256, g.ny), blk, 0, s>>>(g, d.mask, dst);
   } else {
-    const void* p = which == 0 ? d.rho : which == 1 ? d.ux : which == 2 ? d.uy : which == 3 ? d.T : d.psi;
+    const void* p = which == 0 ? d.rho : which == 1 ? d.ux : which == 2 ? d.uy : which == 3 ? d.T[tcur] : d.psi;
     k_export<C><<<dim3((g.nx + 255) / 256, g.ny), blk, 0, s>>>(g, static_cast<const C*>(p), g.pitch, g.ny, dst, g.nx);
   }
   return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 
 template <typename C, typename S>
-int import_impl(const Geo& g, const Dev& d, int cur, int which, const double* src, cudaStream_t s) {
+int import_impl(const Geo& g, const Dev& d, int cur, int tcur, int which, const double* src, cudaStream_t s) {
   using namespace kern;
   const dim3 blk(256);
   if (which >= 20 && which < 23) {
-    C* dst = static_cast<C*>(d.side) + (which - 20) * g.ny;
+    C* dst = static_cast<C*>(d.side[cur]) + (which - 20) * g.ny;
     k_import<C><<<dim3((g.ny + 255) / 256, 1), blk, 0, s>>>(g, dst, g.ny, 1, src, g.ny);
   } else if (which >= 10 && which < 19) {
     S* dst = static_cast<S*>(d.f[cur]) + (which - 10) * g.plane;
     k_import<S><<<dim3((g.nx + 255) / 256, g.ny), blk, 0, s>>>(g, dst, g.pitch, g.ny, src, g.nx);
   } else if (which == 3) {
-    k_import<C><<<dim3((g.nx + 255) / 256, g.ny), blk, 0, s>>>(g, static_cast<C*>(d.T), g.pitch, g.ny, src, g.nx);
+    k_import<C><<<dim3((g.nx + 255) / 256, g.ny), blk, 0, s>>>(g, static_cast<C*>(d.T[tcur]), g.pitch, g.ny, src,
+                                                                 g.nx);
   } else {
     return -1;
   }
@@ -643,10 +806,10 @@ template <typename C, typename S>
 int init_impl(const Geo& g, const Phys& ph, const Dev& d, const double* rho0, const double* drho, const double* ux0,
               const double* uy0, const double* T0, unsigned long long seed, double amp, cudaStream_t s) {
   using namespace kern;
-  const dim3 blk(kBX, kBY), grd((g.nx + kBX - 1) / kBX, (g.ny + kBY - 1) / kBY);
+  const dim3 blk(32, 8), grd((g.nx + 31) / 32, (g.ny + 7) / 8);
   k_init<C, S><<<grd, blk, 0, s>>>(g, ph, rho0, drho, ux0, uy0, T0, seed, amp, static_cast<S*>(d.f[0]),
-                                   static_cast<C*>(d.T), static_cast<C*>(d.rho), static_cast<C*>(d.ux),
-                                   static_cast<C*>(d.uy), static_cast<C*>(d.side), d.mask);
+                                   static_cast<C*>(d.T[0]), static_cast<C*>(d.rho), static_cast<C*>(d.ux),
+                                   static_cast<C*>(d.uy), static_cast<C*>(d.side[0]), d.mask);
   return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 

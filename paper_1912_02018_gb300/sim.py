@@ -14,7 +14,7 @@ from . import _native as N
 
 _PARAM_DEFAULTS = dict(a=2.0 / 49.0, b=2.0 / 21.0, R=1.0, acentric=0.344, G=-1.0, sigma=0.38, Tr_sat=0.86,
                        Re=30.0, u_in=0.05, nu_l=0.0, nu_ratio=1.0, Pr_l=0.862, Pr_v=1.5, c_v=11.0, g=-1.0,
-                       outlet_U=-1.0, warmup=0, energy=1, seed=0, noise_amp=1e-4)
+                       outlet_U=-1.0, warmup=0, energy=1, seed=0, noise_amp=1e-4, psi_mode=0)
 
 
 def _dense(a, n):
@@ -57,7 +57,7 @@ class Sim:
                        nu_ratio=kw["nu_ratio"], Pr_l=kw["Pr_l"], Pr_v=kw["Pr_v"], c_v=kw["c_v"], g=kw["g"],
                        outlet_U=kw["outlet_U"], warmup_steps=int(kw["warmup"]), energy=int(kw["energy"]),
                        storage=N.LBM_STORE_F64 if f64 else N.LBM_STORE_F32, compute_f64=1 if f64 else 0,
-                       reserved=0, seed=int(kw["seed"]), noise_amp=kw["noise_amp"])
+                       psi_mode=int(kw["psi_mode"]), seed=int(kw["seed"]), noise_amp=kw["noise_amp"])
         n = self.nx * self.ny
         init = init or {}
         keep = {k: _dense(init.get(k), n) for k in ("rho", "drho", "ux", "uy", "T")}

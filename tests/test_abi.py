@@ -55,12 +55,12 @@ def _good():
     cyl = N.Cylinder(32.0, 32.0, 16.0, 0.05, 0.0)
     prm = N.Params(a=2 / 49, b=2 / 21, R=1.0, acentric=0.344, G=-1.0, sigma=0.38, Tr_sat=0.86, Re=30.0,
                    u_in=0.05, nu_l=0.0, nu_ratio=1.0, Pr_l=0.862, Pr_v=1.5, c_v=11.0, g=-1.0, outlet_U=-1.0,
-                   warmup_steps=0, energy=1, storage=N.LBM_STORE_F32, compute_f64=0, reserved=0, seed=0,
+                   warmup_steps=0, energy=1, storage=N.LBM_STORE_F32, compute_f64=0, psi_mode=0, seed=0,
                    noise_amp=1e-4)
     return dom, cyl, prm
 
 
-@pytest.mark.parametrize("what", ["small", "storage", "G", "Tr", "cyl_inlet", "cyl_wide", "nu"])
+@pytest.mark.parametrize("what", ["small", "storage", "G", "Tr", "cyl_inlet", "cyl_wide", "nu", "psi_mode"])
 def test_invalid_parameters_are_rejected_on_the_host(lib, what):
     dom, cyl, prm = _good()
     if what == "small":
@@ -75,6 +75,8 @@ def test_invalid_parameters_are_rejected_on_the_host(lib, what):
         cyl.xc = 8.0
     elif what == "cyl_wide":
         cyl.D = 62.0
+    elif what == "psi_mode":
+        prm.psi_mode = 3
     elif what == "nu":
         prm.Re = 0.0  # nu_l = 0 and no Reynolds number: no valid relaxation rate
     st, h = _create(lib, dom, cyl, prm)

@@ -190,6 +190,20 @@ def test_torch_allocator_and_cudamalloc_agree():
         assert np.array_equal(v, b.fields()[k]), k
 
 
+@pytest.mark.parametrize("psi_mode", [0, 1, 2], ids=["double_float", "ieee_fp64", "fp32"])
+def test_fp32_psi_modes_match_oracle(psi_mode):
+    case = si.SMALL
+    init = {"drho": case.drho()}
+    sim = Sim().from_case(case, f64=False, init=init, psi_mode=psi_mode).step(50)
+    ref = Oracle(case, **init).step(50)
+    fluid = ref.field("solid") == 0
+    got = sim.fields(("psi", "rho", "T"))
+    # psi is stored in FP32: the double-float and FP64 evaluations round to within 2 ulp-scale of the oracle
+    tol = 1e-6 if psi_mode != 2 else 1e-5
+    assert rel(got["psi"], ref.field("psi"), fluid) < tol
+    assert rel(got["rho"], ref.field("rho"), fluid) < 1e-5
+
+
 def test_library_default_noise_matches_seeded_input_generator():
     case = si.SMALL.replace(seed=5, noise_amp=3e-4)
     a = Sim().from_case(case, f64=True)  # the library draws SplitMix64(seed) itself
@@ -203,8 +217,7 @@ def test_profile_counts_launches():
     sim.profile(True)
     sim.step(10)
     prof = sim.profile_read()
-    assert prof["k_collide"][0] == 10 and prof["k_rho_psi"][0] == 10
-    assert prof["k_T_stage1"][0] == 10 and prof["k_heat_flux"][0] == 10
+    assert prof["k_flow"][0] == 10 and prof["k_energy"][0] == 10 and prof["k_hf_reduce"][0] == 10
     assert all(v[1] >= 0 for v in prof.values())
     info = sim.info()
-    assert info["steps"] == 10 and info["kernel_launches"] >= 50
+    assert info["steps"] == 10 and info["kernel_launches"] >= 30
