@@ -611,7 +611,7 @@ __global__ void __launch_bounds__(kEnergyTX* kEnergyTY)
 }
 
 // One block: fixed-order sum of the per-block partials, then the running statistics.
-__global__ void __launch_bounds__(256) k_hf_reduce(const double* __restrict__ partial, int nblocks, int nb, double* hf) {
+static __global__ void __launch_bounds__(256) k_hf_reduce(const double* __restrict__ partial, int nblocks, int nb, double* hf) {
   __shared__ double red[8];
   double s = 0.0;
   for (int i = threadIdx.x; i < nblocks; i += 256) s += partial[i];
