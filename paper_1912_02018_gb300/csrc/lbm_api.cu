@@ -307,7 +307,8 @@ lbm_status lbm_create(const lbm_domain* domain, const lbm_cylinder* cyl, const l
     return fail(nullptr, LBM_EINVAL, "no liquid-vapour coexistence at T_sat = %g", T_sat);
   }
   c->p_sat = p_s;
-  lbm::Phys& ph = c->ph;
+  lbm::Phys& phys = c->ph;
+  lbm::PhysC<double>& ph = phys.d;
   ph.a = P.a;
   ph.b = P.b;
   ph.R = P.R;
@@ -329,19 +330,27 @@ lbm_status lbm_create(const lbm_domain* domain, const lbm_cylinder* cyl, const l
   ph.u_in = P.u_in;
   ph.U_out = P.outlet_U >= 0 ? P.outlet_U : P.u_in;
   c->lambda_v = rho_v * P.c_v * ph.alpha_v;
+  {
+    lbm::PhysC<float>& pf = phys.f;
+    pf.a = (float)ph.a, pf.b = (float)ph.b, pf.R = (float)ph.R, pf.kappa = (float)ph.kappa, pf.Tc = (float)ph.Tc;
+    pf.G = (float)ph.G, pf.sigma = (float)ph.sigma, pf.T_sat = (float)ph.T_sat, pf.T_wall = (float)ph.T_wall;
+    pf.rho_l = (float)ph.rho_l, pf.rho_v = (float)ph.rho_v, pf.rho_s = (float)ph.rho_s;
+    pf.nu_l = (float)ph.nu_l, pf.nu_v = (float)ph.nu_v, pf.alpha_l = (float)ph.alpha_l, pf.alpha_v = (float)ph.alpha_v;
+    pf.c_v = (float)ph.c_v, pf.g = (float)ph.g, pf.u_in = (float)ph.u_in, pf.U_out = (float)ph.U_out;
+  }
   auto split = [](double v) {
     lbm::F2 r;
     r.hi = (float)v;
     r.lo = (float)(v - (double)r.hi);
     return r;
   };
-  ph.a2 = split(P.a);
-  ph.b2 = split(P.b);
-  ph.R2 = split(P.R);
-  ph.kappa2 = split(eos.kappa);
-  ph.invTc2 = split(1.0 / eos.Tc);
-  ph.cs22 = split(1.0 / 3.0);
-  ph.k2 = split(P.G != 0 ? 2.0 / (P.G * (1.0 / 3.0)) : 0.0);
+  phys.a2 = split(P.a);
+  phys.b2 = split(P.b);
+  phys.R2 = split(P.R);
+  phys.kappa2 = split(eos.kappa);
+  phys.invTc2 = split(1.0 / eos.Tc);
+  phys.cs22 = split(1.0 / 3.0);
+  phys.k2 = split(P.G != 0 ? 2.0 / (P.G * (1.0 / 3.0)) : 0.0);
   for (double nu : {ph.nu_l, ph.nu_v}) {
     const double omega = 1.0 / (nu * 3.0 + 0.5);
     if (!(nu > 0) || !(omega > 0 && omega < 2)) {
@@ -461,9 +470,9 @@ lbm_status lbm_create(const lbm_domain* domain, const lbm_cylinder* cyl, const l
       chk(cudaMemcpyAsync(d.stage + k * M, src[k], M * sizeof(double), cudaMemcpyHostToDevice, c->stream));
       dsrc[k] = d.stage + k * M;
     }
-  const int ok = c->f64 ? lbm::init_f64(g, ph, d, dsrc[0], dsrc[1], dsrc[2], dsrc[3], dsrc[4], P.seed, P.noise_amp,
+  const int ok = c->f64 ? lbm::init_f64(g, phys, d, dsrc[0], dsrc[1], dsrc[2], dsrc[3], dsrc[4], P.seed, P.noise_amp,
                                         c->stream)
-                        : lbm::init_f32(g, ph, d, dsrc[0], dsrc[1], dsrc[2], dsrc[3], dsrc[4], P.seed, P.noise_amp,
+                        : lbm::init_f32(g, phys, d, dsrc[0], dsrc[1], dsrc[2], dsrc[3], dsrc[4], P.seed, P.noise_amp,
                                         c->stream);
   if (ok < 0) chk(cudaGetLastError());
   chk(cudaMemcpyAsync(d.f[1], d.f[0], 9 * N * es, cudaMemcpyDeviceToDevice, c->stream));
@@ -518,7 +527,7 @@ lbm_status lbm_wall_heat_flux(lbm_ctx* c, double* q_now, double* q_mean, double*
   const double mean = cnt > 0 ? hf[1] / cnt : 0.0;
   double var = cnt > 0 ? hf[2] / cnt - mean * mean : 0.0;
   if (var < 0) var = 0;
-  const double dT = c->ph.T_wall - c->ph.T_sat;
+  const double dT = c->ph.d.T_wall - c->ph.d.T_sat;
   if (q_now) *q_now = hf[0];
   if (q_mean) *q_mean = mean;
   if (q_std) *q_std = std::sqrt(var);
@@ -605,18 +614,18 @@ lbm_status lbm_info(lbm_ctx* c, lbm_info_t* info) {
   if (!c || !info) return LBM_EINVAL;
   info->Tc = c->Tc;
   info->pc = c->pc;
-  info->T_sat = c->ph.T_sat;
-  info->T_wall = c->ph.T_wall;
-  info->rho_l = c->ph.rho_l;
-  info->rho_v = c->ph.rho_v;
+  info->T_sat = c->ph.d.T_sat;
+  info->T_wall = c->ph.d.T_wall;
+  info->rho_l = c->ph.d.rho_l;
+  info->rho_v = c->ph.d.rho_v;
   info->p_sat = c->p_sat;
-  info->nu_l = c->ph.nu_l;
-  info->nu_v = c->ph.nu_v;
-  info->alpha_l = c->ph.alpha_l;
-  info->alpha_v = c->ph.alpha_v;
+  info->nu_l = c->ph.d.nu_l;
+  info->nu_v = c->ph.d.nu_v;
+  info->alpha_l = c->ph.d.alpha_l;
+  info->alpha_v = c->ph.d.alpha_v;
   info->lambda_v = c->lambda_v;
-  info->g = c->ph.g;
-  info->outlet_U = c->ph.U_out;
+  info->g = c->ph.d.g;
+  info->outlet_U = c->ph.d.U_out;
   info->steps = c->steps;
   info->n_boundary = c->dev.nb;
   info->kernel_launches = c->launches;

@@ -23,15 +23,23 @@ struct F2 {
   float hi, lo;
 };
 
-// Physical constants (all derived on the host in double).
+// Physical constants in one precision.
+template <typename C>
+struct PhysC {
+  C a, b, R, kappa, Tc, G, sigma;
+  C T_sat, T_wall;
+  C rho_l, rho_v, rho_s;
+  C nu_l, nu_v, alpha_l, alpha_v, c_v;
+  C g, u_in, U_out;
+};
+
+// Physical constants, derived on the host in double and rounded once to float there, so
+// that no kernel converts a double to a float (on GB300 that conversion runs on the FP64
+// pipe).  The double-float copies serve the FP32 build's psi: a, b, R, kappa, 1/Tc,
+// cs^2 = 1/3 and k = 2/(G cs^2).
 struct Phys {
-  double a, b, R, kappa, Tc, G, sigma;
-  double T_sat, T_wall;
-  double rho_l, rho_v, rho_s;
-  double nu_l, nu_v, alpha_l, alpha_v, c_v;
-  double g, u_in, U_out;
-  // double-float copies of the EOS constants for the FP32 build's psi:
-  // a, b, R, kappa, 1/Tc, cs^2 = 1/3 and k = 2/(G cs^2)
+  PhysC<double> d;
+  PhysC<float> f;
   F2 a2, b2, R2, kappa2, invTc2, cs22, k2;
 };
 

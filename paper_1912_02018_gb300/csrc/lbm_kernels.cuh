@@ -46,19 +46,37 @@ __device__ __forceinline__ constexpr double wiso(int k) {
        : 1.0 / 5040.0;
 }
 
+// Constants in the compute precision.
+template <typename C>
+__device__ __forceinline__ const PhysC<C>& pc(const Phys& ph);
+template <>
+__device__ __forceinline__ const PhysC<double>& pc<double>(const Phys& ph) {
+  return ph.d;
+}
+template <>
+__device__ __forceinline__ const PhysC<float>& pc<float>(const Phys& ph) {
+  return ph.f;
+}
+
 // ---------------------------------------------------------------- addressing
 // Node coordinate of an arbitrary lattice position for stencil reads: periodic in y; in x
 // periodic, or the nearest boundary column (zero-gradient ghost) at the inlet and outlet.
 __device__ __forceinline__ int map_y(const Geo& g, int y) {
-  y %= g.ny;
+  if (y >= 0 && y < g.ny) return y;
+  if (y < 0 && y + g.ny >= 0) return y + g.ny;
+  if (y >= g.ny && y - g.ny < g.ny) return y - g.ny;
+  y %= g.ny;  // only for lattices smaller than a tile
   return y < 0 ? y + g.ny : y;
 }
 __device__ __forceinline__ int map_x(const Geo& g, int x) {
+  if (x >= 0 && x < g.nx) return x;
   if (g.periodic_x) {
+    if (x < 0 && x + g.nx >= 0) return x + g.nx;
+    if (x >= g.nx && x - g.nx < g.nx) return x - g.nx;
     x %= g.nx;
     return x < 0 ? x + g.nx : x;
   }
-  return x < 0 ? 0 : (x >= g.nx ? g.nx - 1 : x);
+  return x < 0 ? 0 : g.nx - 1;
 }
 __device__ __forceinline__ int wrap_y(const Geo& g, int y) {  // offsets |dy| <= 2 < ny
   return y < 0 ? y + g.ny : (y >= g.ny ? y - g.ny : y);
@@ -126,12 +144,13 @@ __device__ __forceinline__ DF df_of(F2 v) { return {v.hi, v.lo}; }
 // Peng-Robinson EOS, Eq. (eos), and psi of Eq. (potential) in IEEE FP64.
 __device__ __forceinline__ double psi_eos(const Phys& ph, double rho, double T, double& rad) {
   const double cs2 = 1.0 / 3.0;
-  double s = 1.0 + ph.kappa * (1.0 - sqrt(T / ph.Tc));
+  const PhysC<double>& k = ph.d;
+  double s = 1.0 + k.kappa * (1.0 - sqrt(T / k.Tc));
   double phi = s * s;
-  double rep = rho * ph.R * T / (1.0 - ph.b * rho);
-  double att = ph.a * phi * rho * rho / (1.0 + 2.0 * ph.b * rho - ph.b * ph.b * rho * rho);
+  double rep = rho * k.R * T / (1.0 - k.b * rho);
+  double att = k.a * phi * rho * rho / (1.0 + 2.0 * k.b * rho - k.b * k.b * rho * rho);
   double p = rep - att;
-  rad = 2.0 * (p - rho * cs2) / (ph.G * cs2);
+  rad = 2.0 * (p - rho * cs2) / (k.G * cs2);
   return sqrt(rad);
 }
 // The same in double-float arithmetic (inputs and result FP32).
@@ -182,28 +201,28 @@ __device__ __forceinline__ C psi_of(const Phys& ph, C rho, C T, int* status) {
 // (dp/dT) at fixed rho, the derivative of Eq. (eos).
 template <typename C>
 __device__ __forceinline__ C dpdT_eos(const Phys& ph, C rho, C T) {
-  C s = C(1) + C(ph.kappa) * (C(1) - sqrt(T / C(ph.Tc)));
-  C dphi = -C(ph.kappa) * s / sqrt(T * C(ph.Tc));
-  C rep = rho * C(ph.R) / (C(1) - C(ph.b) * rho);
-  C att = C(ph.a) * dphi * rho * rho / (C(1) + C(2) * C(ph.b) * rho - C(ph.b) * C(ph.b) * rho * rho);
+  C s = C(1) + pc<C>(ph).kappa * (C(1) - sqrt(T / pc<C>(ph).Tc));
+  C dphi = -pc<C>(ph).kappa * s / sqrt(T * pc<C>(ph).Tc);
+  C rep = rho * pc<C>(ph).R / (C(1) - pc<C>(ph).b * rho);
+  C att = pc<C>(ph).a * dphi * rho * rho / (C(1) + C(2) * pc<C>(ph).b * rho - pc<C>(ph).b * pc<C>(ph).b * rho * rho);
   return rep - att;
 }
 // Phase fraction for the transport properties, and nu(rho), lambda(rho).
 template <typename C>
 __device__ __forceinline__ C phase_frac(const Phys& ph, C rho) {
-  if (!(ph.rho_l > ph.rho_v)) return C(1);
-  C f = (rho - C(ph.rho_v)) / (C(ph.rho_l) - C(ph.rho_v));
+  if (!(pc<C>(ph).rho_l > pc<C>(ph).rho_v)) return C(1);
+  C f = (rho - pc<C>(ph).rho_v) / (pc<C>(ph).rho_l - pc<C>(ph).rho_v);
   f = f < C(0) ? C(0) : f;
   return f > C(1) ? C(1) : f;
 }
 template <typename C>
 __device__ __forceinline__ C nu_of(const Phys& ph, C rho) {
-  return C(ph.nu_v) + phase_frac(ph, rho) * (C(ph.nu_l) - C(ph.nu_v));
+  return pc<C>(ph).nu_v + phase_frac(ph, rho) * (pc<C>(ph).nu_l - pc<C>(ph).nu_v);
 }
 template <typename C>
 __device__ __forceinline__ C lam_of(const Phys& ph, C rho) {
-  C alpha = C(ph.alpha_v) + phase_frac(ph, rho) * (C(ph.alpha_l) - C(ph.alpha_v));
-  return rho * C(ph.c_v) * alpha;
+  C alpha = pc<C>(ph).alpha_v + phase_frac(ph, rho) * (pc<C>(ph).alpha_l - pc<C>(ph).alpha_v);
+  return rho * pc<C>(ph).c_v * alpha;
 }
 
 // ---------------------------------------------------------------- stencils on tiles (Sec. II.C)
@@ -266,7 +285,7 @@ __device__ __forceinline__ C energy_rhs_t(const Phys& ph, const C* t, int ts, co
   C divu = dxux + dyuy;
   C diff = lam[0] * lap + (lx * gx + ly * gy);
   C work = T0 * dpdT_eos(ph, r0, T0) * divu;
-  return -conv + diff / (r0 * C(ph.c_v)) - work / (r0 * C(ph.c_v));
+  return -conv + diff / (r0 * pc<C>(ph).c_v) - work / (r0 * pc<C>(ph).c_v);
 }
 
 // ---------------------------------------------------------------- streaming (Sec. IV.A BCs)
@@ -316,7 +335,7 @@ __device__ __noinline__ void pull_slow(const Geo g, const Phys ph, const S* __re
   if (g.periodic_x) return;
   if (x == 0) {
     // Zou-He velocity inlet, u = (u_in, 0): unknowns f1, f5, f7
-    const C u = C(ph.u_in);
+    const C u = pc<C>(ph).u_in;
     const C rho = (fo[0] + fo[3] + fo[4] + C(2) * (fo[2] + fo[6] + fo[8])) / (C(1) - u);
     fo[1] = fo[2] + C(2.0 / 3.0) * rho * u;
     fo[5] = fo[6] - C(0.5) * (fo[3] - fo[4]) + rho * u / C(6);
@@ -324,7 +343,7 @@ __device__ __noinline__ void pull_slow(const Geo g, const Phys ph, const S* __re
   }
   if (x == g.nx - 1) {
     // convective outlet: f(t+1) = (f(t) + U f_{nx-2}(t+1)) / (1 + U) for f2, f6, f8
-    const C U = C(ph.U_out);
+    const C U = pc<C>(ph).U_out;
     for (int j = 0; j < 3; ++j) {
       const int i = j == 0 ? 2 : (j == 1 ? 6 : 8);
       const C inner = ldf<C>(g, f, i, wrap_y(g, y - cyv(i)), g.nx - 1);
@@ -371,7 +390,7 @@ __device__ __forceinline__ C psi_node(const Geo& g, const Phys& ph, const S* __r
   const uint8_t m = mask[id];
   C rho;
   if (m & kSolid) {
-    rho = C(ph.rho_s);
+    rho = pc<C>(ph).rho_s;
   } else {
     C fo[9];
     pull_node<C, S>(g, ph, f, mask, side_in, nullptr, x, y, m, fo);
@@ -456,7 +475,7 @@ __global__ void __launch_bounds__(kFlowTX* kFlowTY)
   const int x0 = blockIdx.x * kFlowTX, y0 = blockIdx.y * kFlowTY;
   const int x = x0 + tx, y = y0 + ty;
   const bool inside = x < g.nx && y < g.ny;
-  const bool multiphase = ph.G != 0.0;
+  const bool multiphase = pc<C>(ph).G != C(0);
   const long long id = (long long)y * g.pitch + x;
   C fo[9];
   C rho = C(0);
@@ -469,7 +488,7 @@ __global__ void __launch_bounds__(kFlowTX* kFlowTY)
 #pragma unroll
       for (int i = 1; i < 9; ++i) rho = rho + fo[i];
     } else {
-      rho = C(ph.rho_s);
+      rho = pc<C>(ph).rho_s;
     }
   }
   C psi0 = C(0);
@@ -489,7 +508,7 @@ __global__ void __launch_bounds__(kFlowTX* kFlowTY)
   }
   if (!inside) return;
   if (m & kSolid) {
-    rho_o[id] = C(ph.rho_s);
+    rho_o[id] = pc<C>(ph).rho_s;
     ux_o[id] = C(0);
     uy_o[id] = C(0);
     psi_o[id] = psi0;
@@ -500,15 +519,15 @@ __global__ void __launch_bounds__(kFlowTX* kFlowTY)
   if (forcing && multiphase) {
     C sx, sy;
     grad_t(&s_psi[(ty + 2) * HX + tx + 2], HX, sx, sy);
-    Fmx = -C(ph.G) * cs2 * psi0 * sx;
-    Fmy = -C(ph.G) * cs2 * psi0 * sy;
+    Fmx = -pc<C>(ph).G * cs2 * psi0 * sx;
+    Fmy = -pc<C>(ph).G * cs2 * psi0 * sy;
   }
   if (forcing) {
-    Fx = Fmx - (rho - C(ph.rho_l)) * C(ph.g);
+    Fx = Fmx - (rho - pc<C>(ph).rho_l) * pc<C>(ph).g;
     Fy = Fmy;
   }
   const C omega = C(1) / (nu_of(ph, rho) / cs2 + C(0.5));
-  const C sig = (forcing && multiphase) ? C(ph.sigma) : C(0);
+  const C sig = (forcing && multiphase) ? pc<C>(ph).sigma : C(0);
   C fs[9], ux, uy;
   collide(fo, rho, Fx, Fy, Fmx, Fmy, psi0, omega, sig, fs, ux, uy);
 #pragma unroll
@@ -571,8 +590,8 @@ __global__ void __launch_bounds__(kEnergyTX* kEnergyTY)
     if (!g.periodic_x && (gx < 0 || gx >= g.nx)) continue;  // filled from the edge column below
     const int a = (by + 2) * AX + bx + 2;
     C t1;
-    if (sM[a] & kSolid) t1 = C(ph.T_wall);
-    else if (!g.periodic_x && gx == 0) t1 = C(ph.T_sat);
+    if (sM[a] & kSolid) t1 = pc<C>(ph).T_wall;
+    else if (!g.periodic_x && gx == 0) t1 = pc<C>(ph).T_sat;
     else t1 = sT[a] + energy_rhs_t(ph, &sT[a], AX, &sL[a], &sU[a], &sV[a], &sR[a], AX);
     sT1[p] = t1;
   }
@@ -591,8 +610,8 @@ __global__ void __launch_bounds__(kEnergyTX* kEnergyTY)
   double q = 0.0;
   if (inside) {
     C out;
-    if (sM[a] & kSolid) out = C(ph.T_wall);
-    else if (!g.periodic_x && x == 0) out = C(ph.T_sat);
+    if (sM[a] & kSolid) out = pc<C>(ph).T_wall;
+    else if (!g.periodic_x && x == 0) out = pc<C>(ph).T_sat;
     else out = ((sT[a] + sT1[b]) + energy_rhs_t(ph, &sT1[b], BX, &sL[a], &sU[a], &sV[a], &sR[a], AX)) * C(0.5);
     Tout[(long long)y * g.pitch + x] = out;
     if (do_hf && (sM[a] & kNearWall)) {
@@ -665,15 +684,15 @@ __global__ void __launch_bounds__(256) k_init(Geo g, Phys ph, const double* rho0
   if (x >= g.nx || y >= g.ny) return;
   const long long id = (long long)y * g.pitch + x;
   const long long k = (long long)y * g.nx + x;
-  double r = rho0 ? rho0[k] : ph.rho_l;
+  double r = rho0 ? rho0[k] : ph.d.rho_l;
   r = r + (drho ? drho[k] : noise_amp * splitmix_pm1(seed, (unsigned long long)k));
-  double u = ux0 ? ux0[k] : ph.u_in, v = uy0 ? uy0[k] : 0.0;
-  double t = T0 ? T0[k] : ph.T_sat;
+  double u = ux0 ? ux0[k] : ph.d.u_in, v = uy0 ? uy0[k] : 0.0;
+  double t = T0 ? T0[k] : ph.d.T_sat;
   if (mask[id] & kSolid) {
-    r = ph.rho_s;
+    r = ph.d.rho_s;
     u = 0.0;
     v = 0.0;
-    t = ph.T_wall;
+    t = ph.d.T_wall;
   }
   double fe[9];
   feq_hermite(r, u, v, fe);
