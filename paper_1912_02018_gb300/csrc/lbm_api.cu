@@ -16,7 +16,7 @@
 #include "lbm_internal.h"
 
 namespace lbm {
-const char* const kKernelNames[kNumKernels] = {"k_flow", "k_energy", "k_hf_reduce", "k_export", "k_import"};
+const char* const kKernelNames[kNumKernels] = {"k_flow", "k_energy", "k_export", "k_import"};
 }  // namespace lbm
 
 namespace {
@@ -429,6 +429,7 @@ lbm_status lbm_create(const lbm_domain* domain, const lbm_cylinder* cyl, const l
   d.side[0] = dalloc(c, 3 * (size_t)g.ny * es);
   d.side[1] = dalloc(c, 3 * (size_t)g.ny * es);
   d.partial = static_cast<double*>(dalloc(c, sizeof(double) * lbm::energy_blocks(g.nx, g.ny)));
+  d.counter = static_cast<unsigned*>(dalloc(c, sizeof(unsigned)));
   uint8_t* dmask = static_cast<uint8_t*>(dalloc(c, N));
   d.mask = dmask;
   d.nb = (int)bnode.size();
@@ -440,7 +441,7 @@ lbm_status lbm_create(const lbm_domain* domain, const lbm_cylinder* cyl, const l
   d.status = static_cast<int*>(dalloc(c, sizeof(int)));
   d.stage = static_cast<double*>(dalloc(c, sizeof(double) * (size_t)g.nx * g.ny * 5));
   if (!d.f[0] || !d.f[1] || !d.T[0] || !d.T[1] || !d.psi || !d.rho || !d.ux || !d.uy || !d.side[0] ||
-      !d.side[1] || !d.partial || !dmask || !dbn || !dbv || !d.hf || !d.status || !d.stage) {
+      !d.side[1] || !d.partial || !d.counter || !dmask || !dbn || !dbv || !d.hf || !d.status || !d.stage) {
     dfree_all(c);
     delete c;
     return fail(nullptr, LBM_ENOMEM, "device allocation failed");
@@ -455,6 +456,7 @@ lbm_status lbm_create(const lbm_domain* domain, const lbm_cylinder* cyl, const l
   for (void* p : {d.side[0], d.side[1]}) chk(cudaMemsetAsync(p, 0, 3 * g.ny * es, c->stream));
   chk(cudaMemsetAsync(d.hf, 0, 4 * sizeof(double), c->stream));
   chk(cudaMemsetAsync(d.status, 0, sizeof(int), c->stream));
+  chk(cudaMemsetAsync(d.counter, 0, sizeof(unsigned), c->stream));
   chk(cudaMemcpyAsync(dmask, mask.data(), N, cudaMemcpyHostToDevice, c->stream));
   if (!bnode.empty()) {
     chk(cudaMemcpyAsync(dbn, bnode.data(), sizeof(int) * bnode.size(), cudaMemcpyHostToDevice, c->stream));

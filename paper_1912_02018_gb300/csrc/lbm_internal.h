@@ -61,12 +61,13 @@ struct Dev {
   int nb;
   double* hf;        // heat-flux accumulators: last, sum, sum of squares, count
   double* partial;   // one heat-flux partial sum per energy-kernel block
+  unsigned* counter; // blocks of the current energy launch that have finished (wraps to 0)
   int* status;       // latched fault bits
   double* stage;     // nx*ny doubles for exports/imports
 };
 
 // Kernel identifiers for per-launch timing.
-enum KernelId { kKFlow = 0, kKEnergy, kKHeatFlux, kKExport, kKImport, kNumKernels };
+enum KernelId { kKFlow = 0, kKEnergy, kKExport, kKImport, kNumKernels };
 
 // Tile shapes (threads per block = tile nodes).
 constexpr int kFlowTX = 32, kFlowTY = 16;

@@ -2,15 +2,14 @@
 // templated on the compute type C (double or float) and population storage type S.
 //
 // Layout: structure of arrays, every field [ny][pitch] with x fastest; populations are
-// 9 such planes, ping-ponged between two buffers.  A step is two kernels plus a
-// one-block reduction:
+// 9 such planes, ping-ponged between two buffers.  A step is two kernels:
 //   k_flow    per 32x16 tile: pull f with boundary substitutions, rho, psi(rho, T) on the
 //             tile and a 2-node halo (halo nodes re-pulled, psi kept in shared memory),
 //             interaction force, gravity, CM collision; writes f*, rho, u, psi.
 //   k_energy  per 32x16 tile: T, rho, u, lambda(rho) on a 4-node halo in shared memory,
-//             Heun stage 1 on a 2-node halo, stage 2 on the tile; writes T^{n+1} and a
-//             per-block partial of the wall heat flux (FP64).
-//   k_hf_reduce  fixed-order sum of the partials into the running heat-flux statistics.
+//             Heun stage 1 on a 2-node halo, stage 2 on the tile; writes T^{n+1}; blocks
+//             holding wall nodes sum the wall heat flux in FP64 and the last block to
+//             finish adds the per-block partials in block order.
 // The operation order inside each node follows the paper's equations term by term so
 // that the FP64 build (compiled without FMA contraction) rounds like a plain reference.
 #pragma once
@@ -153,18 +152,34 @@ __device__ __forceinline__ double psi_eos(const Phys& ph, double rho, double T, 
   rad = 2.0 * (p - rho * cs2) / (k.G * cs2);
   return sqrt(rad);
 }
-// The same in double-float arithmetic (inputs and result FP32).
+// The same in double-float arithmetic (inputs and result FP32), rearranged over one
+// denominator: with x = b rho and D = 1 + 2x - x^2,
+//   rad = k rho [R T D - a phi rho (1 - x) - (1 - x) D / 3] / ((1 - x) D),  k = 2/(G cs^2),
+// whose numerator has condition number ~2 over the liquid-vapour range, so the cheaper
+// double-word addition (Joldes et al., Alg. 5) keeps ~2^-44 relative accuracy.
+__device__ __forceinline__ DF df_add_s(DF a, DF b) {
+  DF s = two_sum(a.hi, b.hi);
+  return fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
+__device__ __forceinline__ DF df_sub_s(DF a, DF b) { return df_add_s(a, df_neg(b)); }
+__device__ __forceinline__ DF df_div_s(DF a, DF b) {
+  float q1 = __fdividef(a.hi, b.hi);
+  DF r = df_sub_s(a, df_mulf(b, q1));
+  return fast_two_sum(q1, __fdividef(r.hi, b.hi));
+}
 __device__ __forceinline__ float psi_eos_df(const Phys& ph, float rho, float T, float& rad_hi) {
-  const DF one = {1.0f, 0.0f};
+  const DF one = {1.0f, 0.0f}, third = {0.333333343f, -9.93410776e-09f};
   DF sq = df_sqrt(df_mulf(df_of(ph.invTc2), T));
-  DF s = df_add(one, df_mul(df_of(ph.kappa2), df_sub(one, sq)));
+  DF s = df_add_s(one, df_mul(df_of(ph.kappa2), df_sub_s(one, sq)));
   DF phi = df_mul(s, s);
-  DF brho = df_mulf(df_of(ph.b2), rho);
-  DF rep = df_div(df_mulf(df_mulf(df_of(ph.R2), T), rho), df_sub(one, brho));
-  DF den = df_sub(df_add(one, DF{2.0f * brho.hi, 2.0f * brho.lo}), df_mul(brho, brho));
-  DF att = df_div(df_mulf(df_mulf(df_mul(df_of(ph.a2), phi), rho), rho), den);
-  DF q = df_sub(df_sub(rep, att), df_mulf(df_of(ph.cs22), rho));
-  DF rad = df_mul(q, df_of(ph.k2));
+  DF x = df_mulf(df_of(ph.b2), rho);
+  DF omx = df_sub_s(one, x);
+  DF D = df_sub_s(df_add_s(one, DF{2.0f * x.hi, 2.0f * x.lo}), df_mul(x, x));
+  DF den = df_mul(omx, D);
+  DF A = df_mul(df_mulf(df_of(ph.R2), T), D);
+  DF B = df_mul(df_mulf(df_mul(df_of(ph.a2), phi), rho), omx);
+  DF num = df_sub_s(df_sub_s(A, B), df_mul(den, third));
+  DF rad = df_div_s(df_mulf(df_mul(df_of(ph.k2), num), rho), den);
   rad_hi = rad.hi;
   DF r = df_sqrt(rad);
   return __fadd_rn(r.hi, r.lo);
@@ -496,13 +511,29 @@ __global__ void __launch_bounds__(kFlowTX* kFlowTY)
     if (inside) {
       psi0 = psi_of<C, PSI>(ph, rho, T[id], status);
       s_psi[(ty + 2) * HX + tx + 2] = psi0;
+    } else {
+      s_psi[(ty + 2) * HX + tx + 2] =
+          psi_node<C, S, PSI>(g, ph, f, T, mask, side_in, map_x(g, x), map_y(g, y), status);
     }
-    // halo (and positions past the domain edge): psi at the mapped node
-    for (int p = ty * kFlowTX + tx; p < HX * HY; p += kFlowTX * kFlowTY) {
-      const int hx = p % HX, hy = p / HX;
-      const int gx = x0 + hx - 2, gy = y0 + hy - 2;
-      const bool own = hx >= 2 && hx < kFlowTX + 2 && hy >= 2 && hy < kFlowTY + 2 && gx < g.nx && gy < g.ny;
-      if (!own) s_psi[p] = psi_node<C, S, PSI>(g, ph, f, T, mask, side_in, map_x(g, gx), map_y(g, gy), status);
+    // the 2-node halo ring, enumerated contiguously so that whole warps share the work:
+    // two rows above, two rows below, then two columns on each side of the tile rows
+    constexpr int NH = 4 * HX + 4 * kFlowTY;
+    for (int j = ty * kFlowTX + tx; j < NH; j += kFlowTX * kFlowTY) {
+      int hx, hy;
+      if (j < 2 * HX) {
+        hy = j / HX;
+        hx = j - hy * HX;
+      } else if (j < 4 * HX) {
+        const int jj = j - 2 * HX;
+        hy = kFlowTY + 2 + jj / HX;
+        hx = jj % HX;
+      } else {
+        const int jj = j - 4 * HX, c4 = jj & 3;
+        hy = 2 + (jj >> 2);
+        hx = c4 < 2 ? c4 : kFlowTX + c4;
+      }
+      s_psi[hy * HX + hx] =
+          psi_node<C, S, PSI>(g, ph, f, T, mask, side_in, map_x(g, x0 + hx - 2), map_y(g, y0 + hy - 2), status);
     }
     __syncthreads();
   }
@@ -561,7 +592,7 @@ template <typename C>
 __global__ void __launch_bounds__(kEnergyTX* kEnergyTY)
     k_energy(Geo g, Phys ph, const C* __restrict__ Tin, C* __restrict__ Tout, const C* __restrict__ rho,
              const C* __restrict__ ux, const C* __restrict__ uy, const uint8_t* __restrict__ mask,
-             double* __restrict__ partial, int do_hf) {
+             double* partial, unsigned* counter, double* hf, int nb, int do_hf) {
   constexpr int H = 4, AX = kEnergyTX + 2 * H, AY = kEnergyTY + 2 * H;  // inputs: tile + 4
   constexpr int BX = kEnergyTX + 4, BY = kEnergyTY + 4;                 // stage 1: tile + 2
   constexpr int NT = kEnergyTX * kEnergyTY;
@@ -569,6 +600,7 @@ __global__ void __launch_bounds__(kEnergyTX* kEnergyTY)
   __shared__ C sT1[BY * BX];
   __shared__ uint8_t sM[AY * AX];
   __shared__ double red[NT / 32];
+  __shared__ int done_last;
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * kEnergyTX + tx;
   const int x0 = blockIdx.x * kEnergyTX, y0 = blockIdx.y * kEnergyTY;
   for (int p = tid; p < AX * AY; p += NT) {
@@ -624,23 +656,31 @@ __global__ void __launch_bounds__(kEnergyTX* kEnergyTY)
     }
   }
   if (do_hf) {
-    const double s = block_sum<NT>(q, red);
-    if (tid == 0) partial[blockIdx.y * gridDim.x + blockIdx.x] = s;
-  }
-}
-
-// One block: fixed-order sum of the per-block partials, then the running statistics.
-static __global__ void __launch_bounds__(256) k_hf_reduce(const double* __restrict__ partial, int nblocks, int nb, double* hf) {
-  __shared__ double red[8];
-  double s = 0.0;
-  for (int i = threadIdx.x; i < nblocks; i += 256) s += partial[i];
-  s = block_sum<256>(s, red);
-  if (threadIdx.x == 0) {
-    const double qv = s / nb;
-    hf[0] = qv;
-    hf[1] += qv;
-    hf[2] += qv * qv;
-    hf[3] += 1.0;
+    // FP64 block sum only where the tile touches the cylinder; the last block to finish
+    // adds all partials in block order and updates the running statistics
+    const int has = __syncthreads_or(q != 0.0 || (inside && (sM[a] & kNearWall)));
+    double s = 0.0;
+    if (has) s = block_sum<NT>(q, red);
+    const int nblocks = gridDim.x * gridDim.y;
+    if (tid == 0) {
+      partial[blockIdx.y * gridDim.x + blockIdx.x] = s;
+      __threadfence();
+      done_last = atomicInc(counter, nblocks - 1) == (unsigned)(nblocks - 1);
+    }
+    __syncthreads();
+    if (done_last) {
+      __threadfence();
+      double acc = 0.0;
+      for (int i = tid; i < nblocks; i += NT) acc += __ldcg(&partial[i]);
+      acc = block_sum<NT>(acc, red);
+      if (tid == 0) {
+        const double qv = acc / nb;
+        hf[0] = qv;
+        hf[1] += qv;
+        hf[2] += qv * qv;
+        hf[3] += 1.0;
+      }
+    }
   }
 }
 
@@ -771,13 +811,8 @@ int step_impl(const Geo& g, const Phys& ph, const Dev& d, int cur, int tcur, int
     const int do_hf = d.nb > 0;
     const dim3 blk(kEnergyTX, kEnergyTY), grd((g.nx + kEnergyTX - 1) / kEnergyTX, (g.ny + kEnergyTY - 1) / kEnergyTY);
     pre(kKEnergy);
-    k_energy<C><<<grd, blk, 0, s>>>(g, ph, T, Tn, rho, ux, uy, d.mask, d.partial, do_hf);
+    k_energy<C><<<grd, blk, 0, s>>>(g, ph, T, Tn, rho, ux, uy, d.mask, d.partial, d.counter, d.hf, d.nb, do_hf);
     post(kKEnergy);
-    if (do_hf) {
-      pre(kKHeatFlux);
-      k_hf_reduce<<<1, 256, 0, s>>>(d.partial, (int)(grd.x * grd.y), d.nb, d.hf);
-      post(kKHeatFlux);
-    }
     *t_flipped = 1;
   }
   return cudaPeekAtLastError() == cudaSuccess ? n : -1;

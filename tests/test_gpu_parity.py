@@ -217,7 +217,7 @@ def test_profile_counts_launches():
     sim.profile(True)
     sim.step(10)
     prof = sim.profile_read()
-    assert prof["k_flow"][0] == 10 and prof["k_energy"][0] == 10 and prof["k_hf_reduce"][0] == 10
+    assert prof["k_flow"][0] == 10 and prof["k_energy"][0] == 10
     assert all(v[1] >= 0 for v in prof.values())
     info = sim.info()
-    assert info["steps"] == 10 and info["kernel_launches"] >= 30
+    assert info["steps"] == 10 and info["kernel_launches"] >= 20
