@@ -180,7 +180,7 @@ def run_ours(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     case = WORKLOADS[args.workload]
     nodes = case.nx * case.ny
-    sim = Sim.from_case(case, f64=False)  # seeded state generated on the device
+    sim = Sim.from_case(case, f64=False, psi_mode=args.psi_mode)  # seeded state generated on the device
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     clocks = Clocks(local) if rank == 0 else None
@@ -264,7 +264,8 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": case.name, "nx": case.nx, "ny": case.ny, "D": case.D, "Re": case.Re,
-                   "superheat_Tc": case.superheat_Tc, "storage": "f32", "psi": "f64",
+                   "superheat_Tc": case.superheat_Tc, "storage": "f32",
+                   "psi": ["double-float (FP32 pairs)", "IEEE f64", "f32"][args.psi_mode],
                    "l2": "flushed (256 MB write) before every timed step", "parallelism": "replicas"},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "peak_kind": f"{peak_kind} copy bandwidth",
@@ -290,6 +291,8 @@ def main():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="paper_shaped")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--psi-mode", type=int, default=0, choices=(0, 1, 2),
+                    help="psi evaluation of the FP32 build: 0 double-float (default), 1 IEEE FP64, 2 FP32")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
