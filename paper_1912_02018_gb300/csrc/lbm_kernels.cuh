@@ -7,7 +7,8 @@
 //             tile and a 2-node halo (halo nodes re-pulled, psi kept in shared memory),
 //             interaction force, gravity, CM collision; writes f*, rho, u, psi.
 //   k_energy  per 32x16 tile: T, rho, u, lambda(rho) on a 4-node halo in shared memory,
-//             Heun stage 1 on a 2-node halo, stage 2 on the tile; writes T^{n+1}; blocks
+//             Heun stage 1 on a 2-node halo, stage 2 on the tile, two nodes per thread;
+//             writes T^{n+1}; blocks
 //             holding wall nodes sum the wall heat flux in FP64 and the last block to
 //             finish adds the per-block partials in block order.
 // The operation order inside each node follows the paper's equations term by term so
@@ -55,6 +56,17 @@ __device__ __forceinline__ const PhysC<double>& pc<double>(const Phys& ph) {
 template <>
 __device__ __forceinline__ const PhysC<float>& pc<float>(const Phys& ph) {
   return ph.f;
+}
+
+// Division in the compute precision: IEEE in the FP64 build (which must round like the
+// reference), the 2-ulp hardware approximation in the FP32 build.
+template <typename C>
+__device__ __forceinline__ C fdiv(C a, C b) {
+  return a / b;
+}
+template <>
+__device__ __forceinline__ float fdiv<float>(float a, float b) {
+  return __fdividef(a, b);
 }
 
 // ---------------------------------------------------------------- addressing
@@ -216,17 +228,18 @@ __device__ __forceinline__ C psi_of(const Phys& ph, C rho, C T, int* status) {
 // (dp/dT) at fixed rho, the derivative of Eq. (eos).
 template <typename C>
 __device__ __forceinline__ C dpdT_eos(const Phys& ph, C rho, C T) {
-  C s = C(1) + pc<C>(ph).kappa * (C(1) - sqrt(T / pc<C>(ph).Tc));
-  C dphi = -pc<C>(ph).kappa * s / sqrt(T * pc<C>(ph).Tc);
-  C rep = rho * pc<C>(ph).R / (C(1) - pc<C>(ph).b * rho);
-  C att = pc<C>(ph).a * dphi * rho * rho / (C(1) + C(2) * pc<C>(ph).b * rho - pc<C>(ph).b * pc<C>(ph).b * rho * rho);
+  C s = C(1) + pc<C>(ph).kappa * (C(1) - sqrt(fdiv(T, pc<C>(ph).Tc)));
+  C dphi = fdiv(-pc<C>(ph).kappa * s, sqrt(T * pc<C>(ph).Tc));
+  C rep = fdiv(rho * pc<C>(ph).R, C(1) - pc<C>(ph).b * rho);
+  C att = fdiv(pc<C>(ph).a * dphi * rho * rho,
+               C(1) + C(2) * pc<C>(ph).b * rho - pc<C>(ph).b * pc<C>(ph).b * rho * rho);
   return rep - att;
 }
 // Phase fraction for the transport properties, and nu(rho), lambda(rho).
 template <typename C>
 __device__ __forceinline__ C phase_frac(const Phys& ph, C rho) {
   if (!(pc<C>(ph).rho_l > pc<C>(ph).rho_v)) return C(1);
-  C f = (rho - pc<C>(ph).rho_v) / (pc<C>(ph).rho_l - pc<C>(ph).rho_v);
+  C f = fdiv(rho - pc<C>(ph).rho_v, pc<C>(ph).rho_l - pc<C>(ph).rho_v);
   f = f < C(0) ? C(0) : f;
   return f > C(1) ? C(1) : f;
 }
@@ -278,10 +291,10 @@ __device__ __forceinline__ C upwind3_t(const C* p, int st, C v) {
   const C c = p[0];
   if (v >= C(0)) {
     C m2 = p[-2 * st] - c, m1 = p[-st] - c, p1 = p[st] - c;
-    return (m2 - C(6) * m1 + C(2) * p1) / C(6);
+    return fdiv(m2 - C(6) * m1 + C(2) * p1, C(6));
   }
   C m1 = p[-st] - c, p1 = p[st] - c, p2 = p[2 * st] - c;
-  return (-C(2) * m1 + C(6) * p1 - p2) / C(6);
+  return fdiv(-C(2) * m1 + C(6) * p1 - p2, C(6));
 }
 // Right-hand side of Eq. (energy) with rho and u frozen:
 // -u.grad T + (lambda lap T + grad lambda.grad T)/(rho c_v) - T (dp/dT)_rho div u / (rho c_v).
@@ -300,7 +313,7 @@ __device__ __forceinline__ C energy_rhs_t(const Phys& ph, const C* t, int ts, co
   C divu = dxux + dyuy;
   C diff = lam[0] * lap + (lx * gx + ly * gy);
   C work = T0 * dpdT_eos(ph, r0, T0) * divu;
-  return -conv + diff / (r0 * pc<C>(ph).c_v) - work / (r0 * pc<C>(ph).c_v);
+  return -conv + fdiv(diff, r0 * pc<C>(ph).c_v) - fdiv(work, r0 * pc<C>(ph).c_v);
 }
 
 // ---------------------------------------------------------------- streaming (Sec. IV.A BCs)
@@ -317,9 +330,10 @@ __device__ __forceinline__ double link_fraction(const Geo& g, int x, int y, int 
 // interpolated bounce-back on the cylinder, Zou-He inlet, convective outlet.
 // side_out != nullptr: store the outlet's new streamed values there.
 template <typename C, typename S>
-__device__ __noinline__ void pull_slow(const Geo g, const Phys ph, const S* __restrict__ f,
-                                       const uint8_t* __restrict__ mask, const C* __restrict__ side_in,
-                                       C* __restrict__ side_out, int x, int y, C* fo) {
+__device__ __forceinline__ void pull_slow(const Geo& g, const Phys& ph, const S* __restrict__ f,
+                                          const uint8_t* __restrict__ mask, const C* __restrict__ side_in,
+                                          C* __restrict__ side_out, int x, int y, C fo[9]) {
+#pragma unroll
   for (int i = 0; i < 9; ++i) {
     const int cx = cxv(i), cy = cyv(i);
     int sx = x - cx;
@@ -340,7 +354,7 @@ __device__ __noinline__ void pull_slow(const Geo g, const Phys ph, const S* __re
         const bool ok = nxp >= 0 && nxp < g.nx && !(mask[(long long)nyp * g.pitch + nxp] & kSolid);
         v = ok ? C(2) * q * a + (C(1) - C(2) * q) * ldf<C>(g, f, io, nyp, nxp) : a;
       } else {
-        v = a / (C(2) * q) + (C(2) * q - C(1)) / (C(2) * q) * ldf<C>(g, f, i, y, x);
+        v = fdiv(a, C(2) * q) + fdiv(C(2) * q - C(1), C(2) * q) * ldf<C>(g, f, i, y, x);
       }
     } else {
       v = ldf<C>(g, f, i, sy, sx);
@@ -351,18 +365,19 @@ __device__ __noinline__ void pull_slow(const Geo g, const Phys ph, const S* __re
   if (x == 0) {
     // Zou-He velocity inlet, u = (u_in, 0): unknowns f1, f5, f7
     const C u = pc<C>(ph).u_in;
-    const C rho = (fo[0] + fo[3] + fo[4] + C(2) * (fo[2] + fo[6] + fo[8])) / (C(1) - u);
+    const C rho = fdiv(fo[0] + fo[3] + fo[4] + C(2) * (fo[2] + fo[6] + fo[8]), C(1) - u);
     fo[1] = fo[2] + C(2.0 / 3.0) * rho * u;
-    fo[5] = fo[6] - C(0.5) * (fo[3] - fo[4]) + rho * u / C(6);
-    fo[7] = fo[8] + C(0.5) * (fo[3] - fo[4]) + rho * u / C(6);
+    fo[5] = fo[6] - C(0.5) * (fo[3] - fo[4]) + fdiv(rho * u, C(6));
+    fo[7] = fo[8] + C(0.5) * (fo[3] - fo[4]) + fdiv(rho * u, C(6));
   }
   if (x == g.nx - 1) {
     // convective outlet: f(t+1) = (f(t) + U f_{nx-2}(t+1)) / (1 + U) for f2, f6, f8
     const C U = pc<C>(ph).U_out;
+#pragma unroll
     for (int j = 0; j < 3; ++j) {
       const int i = j == 0 ? 2 : (j == 1 ? 6 : 8);
       const C inner = ldf<C>(g, f, i, wrap_y(g, y - cyv(i)), g.nx - 1);
-      const C v = (side_in[j * g.ny + y] + U * inner) / (C(1) + U);
+      const C v = fdiv(side_in[j * g.ny + y] + U * inner, C(1) + U);
       fo[i] = v;
       if (side_out) side_out[j * g.ny + y] = v;
     }
@@ -427,8 +442,8 @@ __device__ __forceinline__ void collide(const C f[9], C rho, C Fx, C Fy, C Fmx, 
   const C m2 = ((((f[3] - f[4]) + f[5]) - f[6]) - f[7]) + f[8];
   const C m4 = ((f[1] + f[2]) - f[3]) - f[4];
   const C m5 = ((f[5] + f[6]) - f[7]) - f[8];
-  ux = (m1 + C(0.5) * Fx) / rho;
-  uy = (m2 + C(0.5) * Fy) / rho;
+  ux = fdiv(m1 + C(0.5) * Fx, rho);
+  uy = fdiv(m2 + C(0.5) * Fy, rho);
   const C u = ux, v = uy;
   // shift matrix N(u), App. A
   const C N10 = -u, N20 = -v;
@@ -442,17 +457,17 @@ __device__ __forceinline__ void collide(const C f[9], C rho, C Fx, C Fy, C Fmx, 
   const C k4 = ((N40 * rho + N41 * m1) + N42 * m2) + m4;
   const C k5 = ((N50 * rho + N51 * m1) + N52 * m2) + m5;
   // post-collision central moments
-  const C alpha = sigma != C(0) ? sigma / (psi * psi) : C(0);
+  const C alpha = sigma != C(0) ? fdiv(sigma, psi * psi) : C(0);
   const C Fm2 = Fmx * Fmx + Fmy * Fmy;
   const C ks0 = rho;
   const C ks1 = C(0.5) * Fx;
   const C ks2 = C(0.5) * Fy;
-  const C ks3 = C(2) * rho / C(3) + C(0.5) * (C(4) * alpha * Fm2);
+  const C ks3 = fdiv(C(2) * rho, C(3)) + C(0.5) * (C(4) * alpha * Fm2);
   const C ks4 = (C(1) - omega) * k4;
   const C ks5 = (C(1) - omega) * k5;
-  const C ks6 = C(0.5) * (Fy / C(3));
-  const C ks7 = C(0.5) * (Fx / C(3));
-  const C ks8 = rho / C(9) + C(0.5) * (C(4.0 / 3.0) * alpha * Fm2);
+  const C ks6 = C(0.5) * fdiv(Fy, C(3));
+  const C ks7 = C(0.5) * fdiv(Fx, C(3));
+  const C ks8 = fdiv(rho, C(9)) + C(0.5) * (C(4.0 / 3.0) * alpha * Fm2);
   // forward substitution N m* = k*
   const C ms0 = ks0;
   const C ms1 = ks1 - N10 * ms0;
@@ -557,7 +572,7 @@ __global__ void __launch_bounds__(kFlowTX* kFlowTY)
     Fx = Fmx - (rho - pc<C>(ph).rho_l) * pc<C>(ph).g;
     Fy = Fmy;
   }
-  const C omega = C(1) / (nu_of(ph, rho) / cs2 + C(0.5));
+  const C omega = fdiv(C(1), fdiv(nu_of(ph, rho), cs2) + C(0.5));
   const C sig = (forcing && multiphase) ? pc<C>(ph).sigma : C(0);
   C fs[9], ux, uy;
   collide(fo, rho, Fx, Fy, Fmx, Fmy, psi0, omega, sig, fs, ux, uy);
@@ -588,20 +603,134 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
   return s;  // valid in thread 0
 }
 
+// Two x-adjacent nodes per thread: a 5x6 window (rows -2..2, columns -2..3 around the
+// left node) is read from a shared tile with three aligned 2-vector loads per row; both
+// nodes' stencils are then evaluated from registers in the same term order as above.
 template <typename C>
-__global__ void __launch_bounds__(kEnergyTX* kEnergyTY)
+struct Vec2;
+template <>
+struct Vec2<float> {
+  using T = float2;
+};
+template <>
+struct Vec2<double> {
+  using T = double2;
+};
+template <typename C>
+__device__ __forceinline__ void load_window(const C* p, int s, C w[5][6]) {
+  using T2 = typename Vec2<C>::T;
+#pragma unroll
+  for (int r = 0; r < 5; ++r) {
+    const T2* q = reinterpret_cast<const T2*>(p + (r - 2) * s - 2);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const T2 v = q[c];
+      w[r][2 * c] = v.x;
+      w[r][2 * c + 1] = v.y;
+    }
+  }
+}
+template <typename C, bool kX = true, bool kY = true>
+__device__ __forceinline__ void grad_w(const C w[5][6], int c0, C& gx, C& gy) {
+  C sx = C(0), sy = C(0);
+#pragma unroll
+  for (int k = 0; k < 12; ++k) {
+    const int ex = exv(k), ey = eyv(k);
+    if ((kX && ex != 0) || (kY && ey != 0)) {
+      const C w8 = C(wiso(k));
+      C d = w[2 + ey][c0 + ex] - w[2 - ey][c0 - ex];
+      if (kX && ex != 0) sx = sx + w8 * d * C(ex);
+      if (kY && ey != 0) sy = sy + w8 * d * C(ey);
+    }
+  }
+  gx = sx;
+  gy = sy;
+}
+template <typename C>
+__device__ __forceinline__ C lap_w(const C w[5][6], int c0) {
+  const C c = w[2][c0];
+  C acc = C(0);
+#pragma unroll
+  for (int k = 0; k < 12; ++k) {
+    const int ex = exv(k), ey = eyv(k);
+    C d = (w[2 + ey][c0 + ex] + w[2 - ey][c0 - ex]) - C(2) * c;
+    acc = acc + C(wiso(k)) * d;
+  }
+  return C(2) * acc;
+}
+template <typename C>
+__device__ __forceinline__ C upwind3_w(const C w[5][6], int c0, bool along_x, C v) {
+  const C c = w[2][c0];
+  auto at = [&](int o) { return along_x ? w[2][c0 + o] : w[2 + o][c0]; };
+  if (v >= C(0)) {
+    C m2 = at(-2) - c, m1 = at(-1) - c, p1 = at(1) - c;
+    return fdiv(m2 - C(6) * m1 + C(2) * p1, C(6));
+  }
+  C m1 = at(-1) - c, p1 = at(1) - c, p2 = at(2) - c;
+  return fdiv(-C(2) * m1 + C(6) * p1 - p2, C(6));
+}
+// Eq. (energy) right-hand side at the two nodes whose left one is at t[0] (row stride ts);
+// lam, u, v, r: the same nodes in tiles of row stride as.  Left node index must be even.
+template <typename C>
+__device__ __forceinline__ void energy_rhs_pair(const Phys& ph, const C* t, int ts, const C* lam, const C* u,
+                                                const C* v, const C* r, int as, C L[2]) {
+  C w[5][6];
+  C conv[2], gx[2], gy[2], lap[2], T0[2], u0[2], v0[2], lx[2], ly[2], lam0[2], dxux[2], dyuy[2], unused;
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    u0[k] = u[k];
+    v0[k] = v[k];
+  }
+  load_window(t, ts, w);
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    T0[k] = w[2][2 + k];
+    conv[k] = u0[k] * upwind3_w(w, 2 + k, true, u0[k]) + v0[k] * upwind3_w(w, 2 + k, false, v0[k]);
+    grad_w(w, 2 + k, gx[k], gy[k]);
+    lap[k] = lap_w(w, 2 + k);
+  }
+  load_window(lam, as, w);
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    lam0[k] = w[2][2 + k];
+    grad_w(w, 2 + k, lx[k], ly[k]);
+  }
+  load_window(u, as, w);
+#pragma unroll
+  for (int k = 0; k < 2; ++k) grad_w<C, true, false>(w, 2 + k, dxux[k], unused);
+  load_window(v, as, w);
+#pragma unroll
+  for (int k = 0; k < 2; ++k) grad_w<C, false, true>(w, 2 + k, unused, dyuy[k]);
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const C r0 = r[k];
+    C divu = dxux[k] + dyuy[k];
+    C diff = lam0[k] * lap[k] + (lx[k] * gx[k] + ly[k] * gy[k]);
+    C work = T0[k] * dpdT_eos(ph, r0, T0[k]) * divu;
+    L[k] = -conv[k] + fdiv(diff, r0 * pc<C>(ph).c_v) - fdiv(work, r0 * pc<C>(ph).c_v);
+  }
+}
+
+constexpr int kEnergyThreads = kEnergyTX * kEnergyTY / 2;
+
+template <typename C>
+__global__ void __launch_bounds__(kEnergyThreads)
     k_energy(Geo g, Phys ph, const C* __restrict__ Tin, C* __restrict__ Tout, const C* __restrict__ rho,
              const C* __restrict__ ux, const C* __restrict__ uy, const uint8_t* __restrict__ mask,
              double* partial, unsigned* counter, double* hf, int nb, int do_hf) {
   constexpr int H = 4, AX = kEnergyTX + 2 * H, AY = kEnergyTY + 2 * H;  // inputs: tile + 4
   constexpr int BX = kEnergyTX + 4, BY = kEnergyTY + 4;                 // stage 1: tile + 2
-  constexpr int NT = kEnergyTX * kEnergyTY;
-  __shared__ C sT[AY * AX], sL[AY * AX], sU[AY * AX], sV[AY * AX], sR[AY * AX];
-  __shared__ C sT1[BY * BX];
+  constexpr int NT = kEnergyThreads;
+  __shared__ __align__(16) C sT[AY * AX];
+  __shared__ __align__(16) C sL[AY * AX];
+  __shared__ __align__(16) C sU[AY * AX];
+  __shared__ __align__(16) C sV[AY * AX];
+  __shared__ __align__(16) C sR[AY * AX];
+  __shared__ __align__(16) C sT1[BY * BX];
   __shared__ uint8_t sM[AY * AX];
   __shared__ double red[NT / 32];
   __shared__ int done_last;
-  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * kEnergyTX + tx;
+  const int tid = threadIdx.x;
   const int x0 = blockIdx.x * kEnergyTX, y0 = blockIdx.y * kEnergyTY;
   for (int p = tid; p < AX * AY; p += NT) {
     const int gx = x0 + p % AX - H, gy = y0 + p / AX - H;
@@ -615,17 +744,21 @@ __global__ void __launch_bounds__(kEnergyTX* kEnergyTY)
     sM[p] = mask[nid];
   }
   __syncthreads();
-  // stage 1: T1 = T + L(T) on the tile and a 2-node halo
-  for (int p = tid; p < BX * BY; p += NT) {
-    const int bx = p % BX, by = p / BX;
-    const int gx = x0 + bx - 2;
-    if (!g.periodic_x && (gx < 0 || gx >= g.nx)) continue;  // filled from the edge column below
+  // stage 1: T1 = T + L(T) on the tile and a 2-node halo, two nodes per thread
+  for (int p = tid; p < (BX / 2) * BY; p += NT) {
+    const int by = p / (BX / 2), bx = (p % (BX / 2)) * 2;
     const int a = (by + 2) * AX + bx + 2;
-    C t1;
-    if (sM[a] & kSolid) t1 = pc<C>(ph).T_wall;
-    else if (!g.periodic_x && gx == 0) t1 = pc<C>(ph).T_sat;
-    else t1 = sT[a] + energy_rhs_t(ph, &sT[a], AX, &sL[a], &sU[a], &sV[a], &sR[a], AX);
-    sT1[p] = t1;
+    C L[2];
+    energy_rhs_pair(ph, &sT[a], AX, &sL[a], &sU[a], &sV[a], &sR[a], AX, L);
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const int gx = x0 + bx + k - 2;
+      C t1;
+      if (sM[a + k] & kSolid) t1 = pc<C>(ph).T_wall;
+      else if (!g.periodic_x && gx == 0) t1 = pc<C>(ph).T_sat;
+      else t1 = sT[a + k] + L[k];
+      sT1[by * BX + bx + k] = t1;  // positions past a non-periodic edge are replaced below
+    }
   }
   __syncthreads();
   if (!g.periodic_x && (x0 < 2 || x0 + kEnergyTX + 2 > g.nx)) {
@@ -636,29 +769,39 @@ __global__ void __launch_bounds__(kEnergyTX* kEnergyTY)
     }
     __syncthreads();
   }
-  const int x = x0 + tx, y = y0 + ty;
-  const bool inside = x < g.nx && y < g.ny;
+  // stage 2 on the tile: T^{n+1} = (T + T1 + L(T1)) / 2
+  const int tx = (tid % (kEnergyTX / 2)) * 2, ty = tid / (kEnergyTX / 2);
   const int a = (ty + H) * AX + tx + H, b = (ty + 2) * BX + tx + 2;
+  C L[2];
+  energy_rhs_pair(ph, &sT1[b], BX, &sL[a], &sU[a], &sV[a], &sR[a], AX, L);
   double q = 0.0;
-  if (inside) {
-    C out;
-    if (sM[a] & kSolid) out = pc<C>(ph).T_wall;
-    else if (!g.periodic_x && x == 0) out = pc<C>(ph).T_sat;
-    else out = ((sT[a] + sT1[b]) + energy_rhs_t(ph, &sT1[b], BX, &sL[a], &sU[a], &sV[a], &sR[a], AX)) * C(0.5);
-    Tout[(long long)y * g.pitch + x] = out;
-    if (do_hf && (sM[a] & kNearWall)) {
-      // wall heat flux -lambda grad T . n at this boundary node, from T^n (Sec. IV.B)
-      C gx, gy;
-      grad_t(&sT[a], AX, gx, gy);
-      const double dx = x - g.xc, dy = y - g.yc, rr = sqrt(dx * dx + dy * dy);
-      const double nxv = dx / rr, nyv = dy / rr;
-      q = -(double)sL[a] * ((double)gx * nxv + (double)gy * nyv);
+  const int y = y0 + ty;
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const int x = x0 + tx + k;
+    if (x < g.nx && y < g.ny) {
+      C out;
+      if (sM[a + k] & kSolid) out = pc<C>(ph).T_wall;
+      else if (!g.periodic_x && x == 0) out = pc<C>(ph).T_sat;
+      else out = ((sT[a + k] + sT1[b + k]) + L[k]) * C(0.5);
+      Tout[(long long)y * g.pitch + x] = out;
+      if (do_hf && (sM[a + k] & kNearWall)) {
+        // wall heat flux -lambda grad T . n at this boundary node, from T^n (Sec. IV.B)
+        C gx, gy;
+        grad_t(&sT[a + k], AX, gx, gy);
+        const double dx = x - g.xc, dy = y - g.yc, rr = sqrt(dx * dx + dy * dy);
+        const double nxv = dx / rr, nyv = dy / rr;
+        q += -(double)sL[a + k] * ((double)gx * nxv + (double)gy * nyv);
+      }
     }
   }
   if (do_hf) {
     // FP64 block sum only where the tile touches the cylinder; the last block to finish
     // adds all partials in block order and updates the running statistics
-    const int has = __syncthreads_or(q != 0.0 || (inside && (sM[a] & kNearWall)));
+    int mine = 0;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) mine |= (x0 + tx + k < g.nx && y < g.ny && (sM[a + k] & kNearWall)) ? 1 : 0;
+    const int has = __syncthreads_or(mine);
     double s = 0.0;
     if (has) s = block_sum<NT>(q, red);
     const int nblocks = gridDim.x * gridDim.y;
@@ -809,7 +952,7 @@ int step_impl(const Geo& g, const Phys& ph, const Dev& d, int cur, int tcur, int
   *t_flipped = 0;
   if (energy && forcing) {
     const int do_hf = d.nb > 0;
-    const dim3 blk(kEnergyTX, kEnergyTY), grd((g.nx + kEnergyTX - 1) / kEnergyTX, (g.ny + kEnergyTY - 1) / kEnergyTY);
+    const dim3 blk(kEnergyThreads), grd((g.nx + kEnergyTX - 1) / kEnergyTX, (g.ny + kEnergyTY - 1) / kEnergyTY);
     pre(kKEnergy);
     k_energy<C><<<grd, blk, 0, s>>>(g, ph, T, Tn, rho, ux, uy, d.mask, d.partial, d.counter, d.hf, d.nb, do_hf);
     post(kKEnergy);
