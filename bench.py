@@ -49,7 +49,8 @@ WORKLOADS = {
 # Algorithmic bytes per lattice update of each kernel (FP32 storage and compute): the
 # values a kernel must read and write by its contract, each once.
 ALG_BYTES = {
-    "k_flow": 9 * 4 + 4 + 9 * 4 + 4 * 4,  # f, T in; f*, rho, ux, uy, psi out
+    "k_rho_psi": 9 * 4 + 4 + 4,           # f, T in; psi out
+    "k_collide": 9 * 4 + 4 + 9 * 4 + 12,  # f, psi in; f*, rho, ux, uy out
     "k_energy": 4 * 4 + 4,               # T, rho, ux, uy in; T out
 }
 STEP_ALG_BYTES = 9 * 4 * 2 + 4 * 2        # the whole step: populations and T in and out

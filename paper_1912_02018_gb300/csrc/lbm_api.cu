@@ -16,7 +16,7 @@
 #include "lbm_internal.h"
 
 namespace lbm {
-const char* const kKernelNames[kNumKernels] = {"k_flow", "k_energy", "k_export", "k_import"};
+const char* const kKernelNames[kNumKernels] = {"k_rho_psi", "k_collide", "k_energy", "k_export", "k_import"};
 }  // namespace lbm
 
 namespace {

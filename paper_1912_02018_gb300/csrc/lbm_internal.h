@@ -67,10 +67,9 @@ struct Dev {
 };
 
 // Kernel identifiers for per-launch timing.
-enum KernelId { kKFlow = 0, kKEnergy, kKExport, kKImport, kNumKernels };
+enum KernelId { kKRhoPsi = 0, kKCollide, kKEnergy, kKExport, kKImport, kNumKernels };
 
 // Tile shapes (threads per block = tile nodes).
-constexpr int kFlowTX = 32, kFlowTY = 16;
 constexpr int kEnergyTX = 32, kEnergyTY = 16;
 inline int energy_blocks(int nx, int ny) {
   return ((nx + kEnergyTX - 1) / kEnergyTX) * ((ny + kEnergyTY - 1) / kEnergyTY);

@@ -2,10 +2,10 @@
 // templated on the compute type C (double or float) and population storage type S.
 //
 // Layout: structure of arrays, every field [ny][pitch] with x fastest; populations are
-// 9 such planes, ping-ponged between two buffers.  A step is two kernels:
-//   k_flow    per 32x16 tile: pull f with boundary substitutions, rho, psi(rho, T) on the
-//             tile and a 2-node halo (halo nodes re-pulled, psi kept in shared memory),
-//             interaction force, gravity, CM collision; writes f*, rho, u, psi.
+// 9 such planes, ping-ponged between two buffers.  A step is three kernels:
+//   k_rho_psi pull f with boundary substitutions, rho, psi(rho, T); writes psi.
+//   k_collide pull f again, interaction force from a psi tile with a 2-node halo in
+//             shared memory, gravity, CM collision; writes f*, rho, u.
 //   k_energy  per 32x16 tile: T, rho, u, lambda(rho) on a 4-node halo in shared memory,
 //             Heun stage 1 on a 2-node halo, stage 2 on the tile, two nodes per thread;
 //             writes T^{n+1}; blocks
@@ -492,88 +492,69 @@ __device__ __forceinline__ void collide(const C f[9], C rho, C Fx, C Fy, C Fmx, 
   fs[8] = ((-q * ms5 + q * ms6) - q * ms7) + q * ms8;
 }
 
-// ---------------------------------------------------------------- k_flow
+// ---------------------------------------------------------------- k_rho_psi, k_collide
+constexpr int kCollTX = 32, kCollTY = 8;
+
+// psi(rho, T) at every node (rho from the pulled populations, rho_s in the solid).
 template <typename C, typename S, int PSI>
-__global__ void __launch_bounds__(kFlowTX* kFlowTY)
-    k_flow(Geo g, Phys ph, const S* __restrict__ f, S* __restrict__ fn, const C* __restrict__ T,
-           const uint8_t* __restrict__ mask, const C* __restrict__ side_in, C* __restrict__ side_out,
-           C* __restrict__ rho_o, C* __restrict__ ux_o, C* __restrict__ uy_o, C* __restrict__ psi_o, int forcing,
-           int* status) {
-  constexpr int HX = kFlowTX + 4, HY = kFlowTY + 4;
+__global__ void __launch_bounds__(256) k_rho_psi(Geo g, Phys ph, const S* __restrict__ f, const C* __restrict__ T,
+                                                const uint8_t* __restrict__ mask, const C* __restrict__ side_in,
+                                                C* __restrict__ psi_o, int* status) {
+  const int x = blockIdx.x * kCollTX + threadIdx.x, y = blockIdx.y * kCollTY + threadIdx.y;
+  if (x >= g.nx || y >= g.ny) return;
+  psi_o[(long long)y * g.pitch + x] = psi_node<C, S, PSI>(g, ph, f, T, mask, side_in, x, y, status);
+}
+
+// Pull, interaction force from a psi tile with a 2-node halo, gravity, CM collision;
+// writes f* (other buffer), rho, u and the outlet's streamed values.
+template <typename C, typename S>
+__global__ void __launch_bounds__(kCollTX* kCollTY)
+    k_collide(Geo g, Phys ph, const S* __restrict__ f, S* __restrict__ fn, const C* __restrict__ psi,
+              const uint8_t* __restrict__ mask, const C* __restrict__ side_in, C* __restrict__ side_out,
+              C* __restrict__ rho_o, C* __restrict__ ux_o, C* __restrict__ uy_o, int forcing, int* status) {
+  constexpr int HX = kCollTX + 4, HY = kCollTY + 4;
   __shared__ C s_psi[HY * HX];
+  const PhysC<C>& k = pc<C>(ph);
   const int tx = threadIdx.x, ty = threadIdx.y;
-  const int x0 = blockIdx.x * kFlowTX, y0 = blockIdx.y * kFlowTY;
+  const int x0 = blockIdx.x * kCollTX, y0 = blockIdx.y * kCollTY;
   const int x = x0 + tx, y = y0 + ty;
-  const bool inside = x < g.nx && y < g.ny;
-  const bool multiphase = pc<C>(ph).G != C(0);
-  const long long id = (long long)y * g.pitch + x;
-  C fo[9];
-  C rho = C(0);
-  uint8_t m = kSolid;
-  if (inside) {
-    m = mask[id];
-    if (!(m & kSolid)) {
-      pull_node<C, S>(g, ph, f, mask, side_in, side_out, x, y, m, fo);
-      rho = fo[0];
-#pragma unroll
-      for (int i = 1; i < 9; ++i) rho = rho + fo[i];
-    } else {
-      rho = pc<C>(ph).rho_s;
-    }
-  }
-  C psi0 = C(0);
-  if (multiphase) {
-    if (inside) {
-      psi0 = psi_of<C, PSI>(ph, rho, T[id], status);
-      s_psi[(ty + 2) * HX + tx + 2] = psi0;
-    } else {
-      s_psi[(ty + 2) * HX + tx + 2] =
-          psi_node<C, S, PSI>(g, ph, f, T, mask, side_in, map_x(g, x), map_y(g, y), status);
-    }
-    // the 2-node halo ring, enumerated contiguously so that whole warps share the work:
-    // two rows above, two rows below, then two columns on each side of the tile rows
-    constexpr int NH = 4 * HX + 4 * kFlowTY;
-    for (int j = ty * kFlowTX + tx; j < NH; j += kFlowTX * kFlowTY) {
-      int hx, hy;
-      if (j < 2 * HX) {
-        hy = j / HX;
-        hx = j - hy * HX;
-      } else if (j < 4 * HX) {
-        const int jj = j - 2 * HX;
-        hy = kFlowTY + 2 + jj / HX;
-        hx = jj % HX;
-      } else {
-        const int jj = j - 4 * HX, c4 = jj & 3;
-        hy = 2 + (jj >> 2);
-        hx = c4 < 2 ? c4 : kFlowTX + c4;
-      }
-      s_psi[hy * HX + hx] =
-          psi_node<C, S, PSI>(g, ph, f, T, mask, side_in, map_x(g, x0 + hx - 2), map_y(g, y0 + hy - 2), status);
+  const bool multiphase = k.G != C(0);
+  if (multiphase && forcing) {
+    for (int p = ty * kCollTX + tx; p < HX * HY; p += kCollTX * kCollTY) {
+      const int hx = p % HX, hy = p / HX;
+      s_psi[p] = psi[(long long)map_y(g, y0 + hy - 2) * g.pitch + map_x(g, x0 + hx - 2)];
     }
     __syncthreads();
   }
-  if (!inside) return;
+  if (x >= g.nx || y >= g.ny) return;
+  const long long id = (long long)y * g.pitch + x;
+  const uint8_t m = mask[id];
   if (m & kSolid) {
-    rho_o[id] = pc<C>(ph).rho_s;
+    rho_o[id] = k.rho_s;
     ux_o[id] = C(0);
     uy_o[id] = C(0);
-    psi_o[id] = psi0;
     return;
   }
+  C fo[9];
+  pull_node<C, S>(g, ph, f, mask, side_in, side_out, x, y, m, fo);
+  C rho = fo[0];
+#pragma unroll
+  for (int i = 1; i < 9; ++i) rho = rho + fo[i];
   const C cs2 = C(1.0 / 3.0);
-  C Fmx = C(0), Fmy = C(0), Fx = C(0), Fy = C(0);
+  C Fmx = C(0), Fmy = C(0), Fx = C(0), Fy = C(0), psi0 = C(0);
+  if (multiphase) psi0 = psi[id];
   if (forcing && multiphase) {
     C sx, sy;
     grad_t(&s_psi[(ty + 2) * HX + tx + 2], HX, sx, sy);
-    Fmx = -pc<C>(ph).G * cs2 * psi0 * sx;
-    Fmy = -pc<C>(ph).G * cs2 * psi0 * sy;
+    Fmx = -k.G * cs2 * psi0 * sx;
+    Fmy = -k.G * cs2 * psi0 * sy;
   }
   if (forcing) {
-    Fx = Fmx - (rho - pc<C>(ph).rho_l) * pc<C>(ph).g;
+    Fx = Fmx - (rho - k.rho_l) * k.g;
     Fy = Fmy;
   }
   const C omega = fdiv(C(1), fdiv(nu_of(ph, rho), cs2) + C(0.5));
-  const C sig = (forcing && multiphase) ? pc<C>(ph).sigma : C(0);
+  const C sig = (forcing && multiphase) ? k.sigma : C(0);
   C fs[9], ux, uy;
   collide(fo, rho, Fx, Fy, Fmx, Fmy, psi0, omega, sig, fs, ux, uy);
 #pragma unroll
@@ -581,7 +562,6 @@ __global__ void __launch_bounds__(kFlowTX* kFlowTY)
   rho_o[id] = rho;
   ux_o[id] = ux;
   uy_o[id] = uy;
-  psi_o[id] = psi0;
   if (!(rho > C(0)) || !(ux == ux) || !(uy == uy)) atomicOr(status, 1);
 }
 
@@ -942,13 +922,15 @@ int step_impl(const Geo& g, const Phys& ph, const Dev& d, int cur, int tcur, int
     if (hook) hook->after(hook->self, k);
     ++n;
   };
-  {
-    const dim3 blk(kFlowTX, kFlowTY), grd((g.nx + kFlowTX - 1) / kFlowTX, (g.ny + kFlowTY - 1) / kFlowTY);
-    pre(kKFlow);
-    k_flow<C, S, PSI><<<grd, blk, 0, s>>>(g, ph, f, fn, T, d.mask, side_in, side_out, rho, ux, uy, psi, forcing,
-                                          d.status);
-    post(kKFlow);
+  const dim3 blk(kCollTX, kCollTY), grd((g.nx + kCollTX - 1) / kCollTX, (g.ny + kCollTY - 1) / kCollTY);
+  if (pc<C>(ph).G != C(0)) {
+    pre(kKRhoPsi);
+    k_rho_psi<C, S, PSI><<<grd, blk, 0, s>>>(g, ph, f, T, d.mask, side_in, psi, d.status);
+    post(kKRhoPsi);
   }
+  pre(kKCollide);
+  k_collide<C, S><<<grd, blk, 0, s>>>(g, ph, f, fn, psi, d.mask, side_in, side_out, rho, ux, uy, forcing, d.status);
+  post(kKCollide);
   *t_flipped = 0;
   if (energy && forcing) {
     const int do_hf = d.nb > 0;

@@ -194,14 +194,15 @@ def test_torch_allocator_and_cudamalloc_agree():
 def test_fp32_psi_modes_match_oracle(psi_mode):
     case = si.SMALL
     init = {"drho": case.drho()}
-    sim = Sim().from_case(case, f64=False, init=init, psi_mode=psi_mode).step(50)
-    ref = Oracle(case, **init).step(50)
+    sim = Sim().from_case(case, f64=False, init=init, psi_mode=psi_mode).step(1)
+    ref = Oracle(case, **init).step(1)
     fluid = ref.field("solid") == 0
     got = sim.fields(("psi", "rho", "T"))
-    # psi is stored in FP32: the double-float and FP64 evaluations round to within 2 ulp-scale of the oracle
-    tol = 1e-6 if psi_mode != 2 else 1e-5
+    # one step: rho differs from the oracle by the FP32 rounding of the pull only, so psi shows
+    # the evaluation error itself (FP32 storage: 2^-24 ~ 6e-8 relative per rounding)
+    tol = 3e-7 if psi_mode != 2 else 1e-6
     assert rel(got["psi"], ref.field("psi"), fluid) < tol
-    assert rel(got["rho"], ref.field("rho"), fluid) < 1e-5
+    assert rel(got["rho"], ref.field("rho"), fluid) < 1e-6
 
 
 def test_library_default_noise_matches_seeded_input_generator():
@@ -217,7 +218,7 @@ def test_profile_counts_launches():
     sim.profile(True)
     sim.step(10)
     prof = sim.profile_read()
-    assert prof["k_flow"][0] == 10 and prof["k_energy"][0] == 10
+    assert prof["k_rho_psi"][0] == 10 and prof["k_collide"][0] == 10 and prof["k_energy"][0] == 10
     assert all(v[1] >= 0 for v in prof.values())
     info = sim.info()
     assert info["steps"] == 10 and info["kernel_launches"] >= 20
