@@ -923,7 +923,7 @@ int step_impl(const Geo& g, const Phys& ph, const Dev& d, int cur, int tcur, int
     ++n;
   };
   const dim3 blk(kCollTX, kCollTY), grd((g.nx + kCollTX - 1) / kCollTX, (g.ny + kCollTY - 1) / kCollTY);
-  if (pc<C>(ph).G != C(0)) {
+  if (ph.d.G != 0.0) {
     pre(kKRhoPsi);
     k_rho_psi<C, S, PSI><<<grd, blk, 0, s>>>(g, ph, f, T, d.mask, side_in, psi, d.status);
     post(kKRhoPsi);
