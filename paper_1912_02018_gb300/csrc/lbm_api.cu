@@ -259,7 +259,8 @@ lbm_status lbm_create(const lbm_domain* domain, const lbm_cylinder* cyl, const l
   const lbm_domain& D = *domain;
   const lbm_params& P = *params;
   if (D.nx < 5 || D.ny < 5) return fail(nullptr, LBM_EINVAL, "nx and ny must be >= 5 (got %d x %d)", D.nx, D.ny);
-  if ((long long)D.nx * D.ny > (1ll << 31)) return fail(nullptr, LBM_EINVAL, "lattice too large");
+  if (9ll * D.ny * ((D.nx + 31) / 32 * 32) >= (1ll << 31))
+    return fail(nullptr, LBM_EINVAL, "lattice too large: 9 ny pitch must stay below 2^31");
   if (P.compute_f64 && P.storage != LBM_STORE_F64)
     return fail(nullptr, LBM_EINVAL, "compute_f64 = 1 needs storage = LBM_STORE_F64");
   if (!P.compute_f64 && P.storage != LBM_STORE_F32)
@@ -376,7 +377,7 @@ lbm_status lbm_create(const lbm_domain* domain, const lbm_cylinder* cyl, const l
   g.ny = D.ny;
   g.pitch = (D.nx + 31) / 32 * 32;
   g.periodic_x = D.periodic_x ? 1 : 0;
-  g.plane = (long long)g.ny * g.pitch;
+  g.plane = g.ny * g.pitch;
   g.xc = cyl->xc;
   g.yc = cyl->yc;
   g.r = has_cyl ? 0.5 * cyl->D : -1.0;

@@ -14,7 +14,7 @@ constexpr uint8_t kNearWall = 2;  // fluid node with a D2Q9 neighbour inside the
 // Lattice geometry.  Arrays are [ny][pitch], pitch >= nx a multiple of 32 elements.
 struct Geo {
   int nx, ny, pitch, periodic_x;
-  long long plane;  // elements per population plane = ny * pitch
+  int plane;        // elements per population plane = ny * pitch (9 * plane < 2^31)
   double xc, yc, r; // cylinder centre and radius (r <= 0: none)
 };
 
@@ -71,8 +71,8 @@ enum KernelId { kKRhoPsi = 0, kKCollide, kKEnergy, kKExport, kKImport, kNumKerne
 
 // Tile shapes (threads per block = tile nodes).
 constexpr int kEnergyTX = 32, kEnergyTY = 16;
-inline int energy_blocks(int nx, int ny) {
-  return ((nx + kEnergyTX - 1) / kEnergyTX) * ((ny + kEnergyTY - 1) / kEnergyTY);
+inline int energy_blocks(int nx, int ny) {  // upper bound over both precisions (FP64 tiles are 32x8)
+  return ((nx + kEnergyTX - 1) / kEnergyTX) * ((ny + 7) / 8);
 }
 extern const char* const kKernelNames[kNumKernels];
 

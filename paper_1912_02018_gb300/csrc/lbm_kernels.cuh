@@ -94,7 +94,7 @@ __device__ __forceinline__ int wrap_y(const Geo& g, int y) {  // offsets |dy| <=
 }
 template <typename C, typename S>
 __device__ __forceinline__ C ldf(const Geo& g, const S* __restrict__ f, int i, int y, int x) {
-  return static_cast<C>(f[i * g.plane + (long long)y * g.pitch + x]);
+  return static_cast<C>(f[i * g.plane + y * g.pitch + x]);
 }
 
 // ---------------------------------------------------------------- double-float arithmetic
@@ -342,7 +342,7 @@ __device__ __forceinline__ void pull_slow(const Geo& g, const Phys& ph, const S*
     C v;
     if (sx < 0 || sx >= g.nx) {
       v = C(0);  // unknown at the inlet or outlet; replaced below
-    } else if (mask[(long long)sy * g.pitch + sx] & kSolid) {
+    } else if (mask[sy * g.pitch + sx] & kSolid) {
       // linear interpolated bounce-back; the wall lies along c_opp(i)
       const int io = oppv(i);
       const C q = C(link_fraction(g, x, y, -cx, -cy));
@@ -351,7 +351,7 @@ __device__ __forceinline__ void pull_slow(const Geo& g, const Phys& ph, const S*
         int nxp = x + cx;
         const int nyp = wrap_y(g, y + cy);
         if (g.periodic_x) nxp = nxp < 0 ? nxp + g.nx : (nxp >= g.nx ? nxp - g.nx : nxp);
-        const bool ok = nxp >= 0 && nxp < g.nx && !(mask[(long long)nyp * g.pitch + nxp] & kSolid);
+        const bool ok = nxp >= 0 && nxp < g.nx && !(mask[nyp * g.pitch + nxp] & kSolid);
         v = ok ? C(2) * q * a + (C(1) - C(2) * q) * ldf<C>(g, f, io, nyp, nxp) : a;
       } else {
         v = fdiv(a, C(2) * q) + fdiv(C(2) * q - C(1), C(2) * q) * ldf<C>(g, f, i, y, x);
@@ -416,7 +416,7 @@ template <typename C, typename S, int PSI>
 __device__ __forceinline__ C psi_node(const Geo& g, const Phys& ph, const S* __restrict__ f,
                                       const C* __restrict__ T, const uint8_t* __restrict__ mask,
                                       const C* __restrict__ side_in, int x, int y, int* status) {
-  const long long id = (long long)y * g.pitch + x;
+  const int id = y * g.pitch + x;
   const uint8_t m = mask[id];
   C rho;
   if (m & kSolid) {
@@ -502,7 +502,7 @@ __global__ void __launch_bounds__(256) k_rho_psi(Geo g, Phys ph, const S* __rest
                                                 C* __restrict__ psi_o, int* status) {
   const int x = blockIdx.x * kCollTX + threadIdx.x, y = blockIdx.y * kCollTY + threadIdx.y;
   if (x >= g.nx || y >= g.ny) return;
-  psi_o[(long long)y * g.pitch + x] = psi_node<C, S, PSI>(g, ph, f, T, mask, side_in, x, y, status);
+  psi_o[y * g.pitch + x] = psi_node<C, S, PSI>(g, ph, f, T, mask, side_in, x, y, status);
 }
 
 // Pull, interaction force from a psi tile with a 2-node halo, gravity, CM collision;
@@ -522,12 +522,12 @@ __global__ void __launch_bounds__(kCollTX* kCollTY)
   if (multiphase && forcing) {
     for (int p = ty * kCollTX + tx; p < HX * HY; p += kCollTX * kCollTY) {
       const int hx = p % HX, hy = p / HX;
-      s_psi[p] = psi[(long long)map_y(g, y0 + hy - 2) * g.pitch + map_x(g, x0 + hx - 2)];
+      s_psi[p] = psi[map_y(g, y0 + hy - 2) * g.pitch + map_x(g, x0 + hx - 2)];
     }
     __syncthreads();
   }
   if (x >= g.nx || y >= g.ny) return;
-  const long long id = (long long)y * g.pitch + x;
+  const int id = y * g.pitch + x;
   const uint8_t m = mask[id];
   if (m & kSolid) {
     rho_o[id] = k.rho_s;
@@ -649,72 +649,84 @@ __device__ __forceinline__ C upwind3_w(const C w[5][6], int c0, bool along_x, C 
   C m1 = at(-1) - c, p1 = at(1) - c, p2 = at(2) - c;
   return fdiv(-C(2) * m1 + C(6) * p1 - p2, C(6));
 }
-// Eq. (energy) right-hand side at the two nodes whose left one is at t[0] (row stride ts);
-// lam, u, v, r: the same nodes in tiles of row stride as.  Left node index must be even.
+// Eq. (energy) splits into parts that depend on rho and u only, frozen during the step
+// (lambda, grad lambda, div u), and parts that depend on the temperature being advanced.
 template <typename C>
-__device__ __forceinline__ void energy_rhs_pair(const Phys& ph, const C* t, int ts, const C* lam, const C* u,
-                                                const C* v, const C* r, int as, C L[2]) {
-  C w[5][6];
-  C conv[2], gx[2], gy[2], lap[2], T0[2], u0[2], v0[2], lx[2], ly[2], lam0[2], dxux[2], dyuy[2], unused;
-#pragma unroll
-  for (int k = 0; k < 2; ++k) {
-    u0[k] = u[k];
-    v0[k] = v[k];
-  }
-  load_window(t, ts, w);
-#pragma unroll
-  for (int k = 0; k < 2; ++k) {
-    T0[k] = w[2][2 + k];
-    conv[k] = u0[k] * upwind3_w(w, 2 + k, true, u0[k]) + v0[k] * upwind3_w(w, 2 + k, false, v0[k]);
-    grad_w(w, 2 + k, gx[k], gy[k]);
-    lap[k] = lap_w(w, 2 + k);
-  }
+struct Frozen {
+  C lam0, lx, ly, divu;
+};
+// Frozen parts at the two nodes whose left one is at lam[0], u[0], v[0] (row stride as;
+// left node index even).
+template <typename C>
+__device__ __forceinline__ void frozen_pair(const C* lam, const C* u, const C* v, int as, Frozen<C> fz[2]) {
+  C w[5][6], unused, dxux[2], dyuy[2];
   load_window(lam, as, w);
 #pragma unroll
   for (int k = 0; k < 2; ++k) {
-    lam0[k] = w[2][2 + k];
-    grad_w(w, 2 + k, lx[k], ly[k]);
+    fz[k].lam0 = w[2][2 + k];
+    grad_w(w, 2 + k, fz[k].lx, fz[k].ly);
   }
   load_window(u, as, w);
 #pragma unroll
   for (int k = 0; k < 2; ++k) grad_w<C, true, false>(w, 2 + k, dxux[k], unused);
   load_window(v, as, w);
 #pragma unroll
-  for (int k = 0; k < 2; ++k) grad_w<C, false, true>(w, 2 + k, unused, dyuy[k]);
+  for (int k = 0; k < 2; ++k) {
+    grad_w<C, false, true>(w, 2 + k, unused, dyuy[k]);
+    fz[k].divu = dxux[k] + dyuy[k];
+  }
+}
+// Right-hand side at the same two nodes for the temperature tile t (row stride ts):
+// -u.grad T + (lambda lap T + grad lambda.grad T)/(rho c_v) - T (dp/dT)_rho div u / (rho c_v).
+template <typename C>
+__device__ __forceinline__ void energy_rhs_pair(const Phys& ph, const C* t, int ts, const C* u, const C* v,
+                                                const C* r, const Frozen<C> fz[2], C L[2]) {
+  C w[5][6];
+  load_window(t, ts, w);
 #pragma unroll
   for (int k = 0; k < 2; ++k) {
-    const C r0 = r[k];
-    C divu = dxux[k] + dyuy[k];
-    C diff = lam0[k] * lap[k] + (lx[k] * gx[k] + ly[k] * gy[k]);
-    C work = T0[k] * dpdT_eos(ph, r0, T0[k]) * divu;
-    L[k] = -conv[k] + fdiv(diff, r0 * pc<C>(ph).c_v) - fdiv(work, r0 * pc<C>(ph).c_v);
+    const C u0 = u[k], v0 = v[k], T0 = w[2][2 + k], r0 = r[k];
+    C conv = u0 * upwind3_w(w, 2 + k, true, u0) + v0 * upwind3_w(w, 2 + k, false, v0);
+    C gx, gy;
+    grad_w(w, 2 + k, gx, gy);
+    C lap = lap_w(w, 2 + k);
+    C diff = fz[k].lam0 * lap + (fz[k].lx * gx + fz[k].ly * gy);
+    C work = T0 * dpdT_eos(ph, r0, T0) * fz[k].divu;
+    L[k] = -conv + fdiv(diff, r0 * pc<C>(ph).c_v) - fdiv(work, r0 * pc<C>(ph).c_v);
   }
 }
 
-constexpr int kEnergyThreads = kEnergyTX * kEnergyTY / 2;
+template <typename C>
+struct EnergyTile {
+  static constexpr int TX = kEnergyTX;
+  static constexpr int TY = sizeof(C) == 8 ? 8 : kEnergyTY;  // FP64 keeps shared memory under 48 KB
+  static constexpr int NT = TX * TY / 2;                     // two nodes per thread
+};
 
 template <typename C>
-__global__ void __launch_bounds__(kEnergyThreads)
+__global__ void __launch_bounds__(EnergyTile<C>::NT)
     k_energy(Geo g, Phys ph, const C* __restrict__ Tin, C* __restrict__ Tout, const C* __restrict__ rho,
              const C* __restrict__ ux, const C* __restrict__ uy, const uint8_t* __restrict__ mask,
              double* partial, unsigned* counter, double* hf, int nb, int do_hf) {
-  constexpr int H = 4, AX = kEnergyTX + 2 * H, AY = kEnergyTY + 2 * H;  // inputs: tile + 4
-  constexpr int BX = kEnergyTX + 4, BY = kEnergyTY + 4;                 // stage 1: tile + 2
-  constexpr int NT = kEnergyThreads;
+  constexpr int TX = EnergyTile<C>::TX, TY = EnergyTile<C>::TY, NT = EnergyTile<C>::NT;
+  constexpr int H = 4, AX = TX + 2 * H, AY = TY + 2 * H;  // inputs: tile + 4
+  constexpr int BX = TX + 4, BY = TY + 4;                 // stage 1: tile + 2
   __shared__ __align__(16) C sT[AY * AX];
   __shared__ __align__(16) C sL[AY * AX];
   __shared__ __align__(16) C sU[AY * AX];
   __shared__ __align__(16) C sV[AY * AX];
   __shared__ __align__(16) C sR[AY * AX];
   __shared__ __align__(16) C sT1[BY * BX];
+  __shared__ Frozen<C> sF[TX * TY];
   __shared__ uint8_t sM[AY * AX];
   __shared__ double red[NT / 32];
   __shared__ int done_last;
   const int tid = threadIdx.x;
-  const int x0 = blockIdx.x * kEnergyTX, y0 = blockIdx.y * kEnergyTY;
+  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+  const bool interior = x0 >= H && y0 >= H && x0 + TX + H <= g.nx && y0 + TY + H <= g.ny;
   for (int p = tid; p < AX * AY; p += NT) {
     const int gx = x0 + p % AX - H, gy = y0 + p / AX - H;
-    const long long nid = (long long)map_y(g, gy) * g.pitch + map_x(g, gx);
+    const int nid = interior ? gy * g.pitch + gx : map_y(g, gy) * g.pitch + map_x(g, gx);
     const C r = rho[nid];
     sT[p] = Tin[nid];
     sR[p] = r;
@@ -724,12 +736,20 @@ __global__ void __launch_bounds__(kEnergyThreads)
     sM[p] = mask[nid];
   }
   __syncthreads();
-  // stage 1: T1 = T + L(T) on the tile and a 2-node halo, two nodes per thread
+  // stage 1: T1 = T + L(T) on the tile and a 2-node halo, two nodes per thread; the frozen
+  // parts of the tile's own nodes are kept for stage 2
   for (int p = tid; p < (BX / 2) * BY; p += NT) {
     const int by = p / (BX / 2), bx = (p % (BX / 2)) * 2;
     const int a = (by + 2) * AX + bx + 2;
+    Frozen<C> fz[2];
+    frozen_pair(&sL[a], &sU[a], &sV[a], AX, fz);
     C L[2];
-    energy_rhs_pair(ph, &sT[a], AX, &sL[a], &sU[a], &sV[a], &sR[a], AX, L);
+    energy_rhs_pair(ph, &sT[a], AX, &sU[a], &sV[a], &sR[a], fz, L);
+    const int tx = bx - 2, ty = by - 2;
+    if (tx >= 0 && tx < TX && ty >= 0 && ty < TY) {
+      sF[ty * TX + tx] = fz[0];
+      sF[ty * TX + tx + 1] = fz[1];
+    }
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
       const int gx = x0 + bx + k - 2;
@@ -741,7 +761,7 @@ __global__ void __launch_bounds__(kEnergyThreads)
     }
   }
   __syncthreads();
-  if (!g.periodic_x && (x0 < 2 || x0 + kEnergyTX + 2 > g.nx)) {
+  if (!g.periodic_x && (x0 < 2 || x0 + TX + 2 > g.nx)) {
     for (int p = tid; p < BX * BY; p += NT) {
       const int bx = p % BX, by = p / BX;
       const int gx = x0 + bx - 2;
@@ -750,10 +770,11 @@ __global__ void __launch_bounds__(kEnergyThreads)
     __syncthreads();
   }
   // stage 2 on the tile: T^{n+1} = (T + T1 + L(T1)) / 2
-  const int tx = (tid % (kEnergyTX / 2)) * 2, ty = tid / (kEnergyTX / 2);
+  const int tx = (tid % (TX / 2)) * 2, ty = tid / (TX / 2);
   const int a = (ty + H) * AX + tx + H, b = (ty + 2) * BX + tx + 2;
+  const Frozen<C> fz[2] = {sF[ty * TX + tx], sF[ty * TX + tx + 1]};
   C L[2];
-  energy_rhs_pair(ph, &sT1[b], BX, &sL[a], &sU[a], &sV[a], &sR[a], AX, L);
+  energy_rhs_pair(ph, &sT1[b], BX, &sU[a], &sV[a], &sR[a], fz, L);
   double q = 0.0;
   const int y = y0 + ty;
 #pragma unroll
@@ -764,7 +785,7 @@ __global__ void __launch_bounds__(kEnergyThreads)
       if (sM[a + k] & kSolid) out = pc<C>(ph).T_wall;
       else if (!g.periodic_x && x == 0) out = pc<C>(ph).T_sat;
       else out = ((sT[a + k] + sT1[b + k]) + L[k]) * C(0.5);
-      Tout[(long long)y * g.pitch + x] = out;
+      Tout[y * g.pitch + x] = out;
       if (do_hf && (sM[a + k] & kNearWall)) {
         // wall heat flux -lambda grad T . n at this boundary node, from T^n (Sec. IV.B)
         C gx, gy;
@@ -845,8 +866,8 @@ __global__ void __launch_bounds__(256) k_init(Geo g, Phys ph, const double* rho0
   const int x = blockIdx.x * 32 + threadIdx.x;
   const int y = blockIdx.y * 8 + threadIdx.y;
   if (x >= g.nx || y >= g.ny) return;
-  const long long id = (long long)y * g.pitch + x;
-  const long long k = (long long)y * g.nx + x;
+  const int id = y * g.pitch + x;
+  const int k = y * g.nx + x;
   double r = rho0 ? rho0[k] : ph.d.rho_l;
   r = r + (drho ? drho[k] : noise_amp * splitmix_pm1(seed, (unsigned long long)k));
   double u = ux0 ? ux0[k] : ph.d.u_in, v = uy0 ? uy0[k] : 0.0;
@@ -873,28 +894,28 @@ __global__ void __launch_bounds__(256) k_init(Geo g, Phys ph, const double* rho0
 }
 
 template <typename E>
-__global__ void k_export(Geo g, const E* __restrict__ src, long long src_pitch, int rows, double* __restrict__ dst,
+__global__ void k_export(Geo g, const E* __restrict__ src, int src_pitch, int rows, double* __restrict__ dst,
                          int ncols) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y;
   if (x >= ncols || y >= rows) return;
-  dst[(long long)y * ncols + x] = (double)src[(long long)y * src_pitch + x];
+  dst[y * ncols + x] = (double)src[y * src_pitch + x];
 }
 
 static __global__ void k_export_solid(Geo g, const uint8_t* __restrict__ mask, double* __restrict__ dst) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y;
   if (x >= g.nx || y >= g.ny) return;
-  dst[(long long)y * g.nx + x] = (mask[(long long)y * g.pitch + x] & kSolid) ? 1.0 : 0.0;
+  dst[y * g.nx + x] = (mask[y * g.pitch + x] & kSolid) ? 1.0 : 0.0;
 }
 
 template <typename E>
-__global__ void k_import(Geo g, E* __restrict__ dst, long long dst_pitch, int rows, const double* __restrict__ src,
+__global__ void k_import(Geo g, E* __restrict__ dst, int dst_pitch, int rows, const double* __restrict__ src,
                          int ncols) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y;
   if (x >= ncols || y >= rows) return;
-  dst[(long long)y * dst_pitch + x] = static_cast<E>(src[(long long)y * ncols + x]);
+  dst[y * dst_pitch + x] = static_cast<E>(src[y * ncols + x]);
 }
 
 }  // namespace kern
@@ -934,7 +955,8 @@ int step_impl(const Geo& g, const Phys& ph, const Dev& d, int cur, int tcur, int
   *t_flipped = 0;
   if (energy && forcing) {
     const int do_hf = d.nb > 0;
-    const dim3 blk(kEnergyThreads), grd((g.nx + kEnergyTX - 1) / kEnergyTX, (g.ny + kEnergyTY - 1) / kEnergyTY);
+    using ET = EnergyTile<C>;
+    const dim3 blk(ET::NT), grd((g.nx + ET::TX - 1) / ET::TX, (g.ny + ET::TY - 1) / ET::TY);
     pre(kKEnergy);
     k_energy<C><<<grd, blk, 0, s>>>(g, ph, T, Tn, rho, ux, uy, d.mask, d.partial, d.counter, d.hf, d.nb, do_hf);
     post(kKEnergy);
