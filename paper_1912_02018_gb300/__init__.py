@@ -3,7 +3,7 @@ pseudopotential lattice Boltzmann model for forced-convection boiling on a cylin
 (Saito et al., arXiv:1912.02018).
 
 The compute path is the CUDA library liblbm.so (C ABI in include/lbm.h), built by
-build.py; this package only marshals arguments to it.  Importing works without a GPU;
+nvcc_build.py; this package only marshals arguments to it.  Importing works without a GPU;
 creating a Sim needs the built library and a CUDA device and fails loudly otherwise.
 """
 from . import _native  # noqa: F401
@@ -13,6 +13,6 @@ __all__ = ["Sim", "build"]
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
-    from .build import build as _b
+    from .nvcc_build import build as _b
 
     return _b(force=force, verbose=verbose)

@@ -70,7 +70,7 @@ def lib():
     if _LIB is not None:
         return _LIB
     if not os.path.exists(LIB_PATH):
-        raise RuntimeError(f"{LIB_PATH} is not built; run paper_1912_02018_gb300/build.py (no CPU fallback exists)")
+        raise RuntimeError(f"{LIB_PATH} is not built; run paper_1912_02018_gb300/nvcc_build.py (no CPU fallback exists)")
     L = C.CDLL(LIB_PATH)
     vp, dp, i64 = C.c_void_p, C.POINTER(C.c_double), C.c_int64
     L.lbm_create.argtypes = [C.POINTER(Domain), C.POINTER(Cylinder), C.POINTER(Params), C.POINTER(Init),
