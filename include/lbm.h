@@ -204,6 +204,30 @@ lbm_status lbm_profile(lbm_ctx *ctx, int enable);
 lbm_status lbm_profile_read(lbm_ctx *ctx, const char **names, int64_t *launches, double *total_ms,
                             int32_t max_kernels, int32_t *n_kernels);
 
+/*
+ * Wall heat flux from caller-owned fields, with no context and no allocation.
+ * The paper has no counterpart of this entry point; it exists for callers that cannot
+ * allocate device memory: code whose device memory is a fixed pool handed out by an outer
+ * framework, or a hook running where an allocation would synchronise the device or is
+ * forbidden outright.  It computes the quantity lbm_wall_heat_flux samples, the mean over
+ * the fluid nodes with a D2Q9 link into the cylinder of -lambda(rho) grad T . n (grad T the
+ * isotropic 24-neighbour gradient, n the outward normal from the centre, lambda from the
+ * parameters as in lbm_create), for the fields the caller passes in.
+ *   T, rho  device arrays of doubles, dense [ny][nx] (as lbm_fields writes them)
+ *   q_out   device pointer to one double receiving the mean; written on cuda_stream
+ * Working memory is a fixed array inside the library (one partial sum and count per tile
+ * of 32 x 8 nodes plus a completion counter, 512 KiB in all) that every GPU loading the
+ * library keeps until the process exits: lattices above 8,388,608 nodes (more than
+ * 32,768 tiles) are rejected with LBM_EINVAL, as are D <= 0 and nx or ny < 5.  The first
+ * call on a device looks up that array's device address with the device current; make
+ * that first call before any stream capture.  All calls share the one array, so calls
+ * whose kernels overlap on the GPU race; serialise them (one stream, or events).  The
+ * call allocates nothing and is asynchronous; synchronise cuda_stream before reading
+ * q_out.  LBM_ECUDA if a CUDA call fails; lbm_last_error does not apply (no context).
+ */
+lbm_status lbm_wall_heat_flux_noalloc(const lbm_domain *domain, const lbm_cylinder *cyl, const lbm_params *params,
+                                      const double *T, const double *rho, double *q_out, void *cuda_stream);
+
 /* Text of the last error of ctx (never NULL); with ctx == NULL, that of the last
  * failed lbm_create on this thread. */
 const char *lbm_last_error(const lbm_ctx *ctx);

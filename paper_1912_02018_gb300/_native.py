@@ -19,7 +19,7 @@ FIELD_BITS = {"rho": 1, "ux": 2, "uy": 4, "T": 8, "psi": 16, "solid": 32}
 # every symbol include/lbm.h declares
 EXPORTS = ("lbm_create", "lbm_step", "lbm_sync", "lbm_wall_heat_flux", "lbm_reset_heat_flux", "lbm_fields",
            "lbm_get_state", "lbm_set_state", "lbm_info", "lbm_profile", "lbm_profile_read", "lbm_last_error",
-           "lbm_destroy")
+           "lbm_destroy", "lbm_wall_heat_flux_noalloc")
 
 
 class Domain(C.Structure):
@@ -88,6 +88,8 @@ def lib():
                                    C.POINTER(C.c_int32)]
     L.lbm_last_error.argtypes = [vp]
     L.lbm_last_error.restype = C.c_char_p
+    L.lbm_wall_heat_flux_noalloc.argtypes = [C.POINTER(Domain), C.POINTER(Cylinder), C.POINTER(Params), vp, vp,
+                                             vp, vp]
     L.lbm_destroy.argtypes = [vp]
     L.lbm_destroy.restype = None
     for name in EXPORTS:

@@ -5,6 +5,7 @@ Translation units, compiled in parallel:
   lbm_f32.cu  FP32 kernels, FMA contraction allowed
   lbm_api.cu  host side of the C ABI (-ffp-contract=off so host FP64 thermodynamics
               round the same on x86-64 and aarch64)
+  lbm_noalloc.cu  the allocation-free wall heat flux
 """
 from __future__ import annotations
 
@@ -28,6 +29,7 @@ UNITS = {
     "lbm_f64.cu": ["--fmad=false"],
     "lbm_f32.cu": ["--fmad=true"],
     "lbm_api.cu": [],
+    "lbm_noalloc.cu": [],
 }
 
 
