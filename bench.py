@@ -46,14 +46,16 @@ WORKLOADS = {
     "small": si.SMALL.replace(name="128x64_D16_Re30_dT0.05Tc_fp32"),
     "probe": si.cylinder_case(8192, 4096, 512.0, Re=300.0, superheat_Tc=0.1, name="8192x4096_D512_probe_fp32"),
 }
-# Algorithmic bytes per lattice update of each kernel (FP32 storage and compute): the
-# values a kernel must read and write by its contract, each once.
+# Algorithmic bytes per lattice update of each kernel (FP32 compute; POP bytes per stored
+# population): the values a kernel must read and write by its contract, each once.
+POP = {"f32": 4, "f64": 8, "f16s": 2}[next((a.split("=", 1)[1] for a in sys.argv if a.startswith("--storage=")),
+                                           sys.argv[sys.argv.index("--storage") + 1] if "--storage" in sys.argv else "f32")]
 ALG_BYTES = {
-    "k_rho_psi": 9 * 4 + 4 + 4,           # f, T in; psi out
-    "k_collide": 9 * 4 + 4 + 9 * 4 + 12,  # f, psi in; f*, rho, ux, uy out
+    "k_rho_psi": 9 * POP + 4 + 4,           # f, T in; psi out
+    "k_collide": 9 * POP + 4 + 9 * POP + 12,  # f, psi in; f*, rho, ux, uy out
     "k_energy": 4 * 4 + 4,               # T, rho, ux, uy in; T out
 }
-STEP_ALG_BYTES = 9 * 4 * 2 + 4 * 2        # the whole step: populations and T in and out
+STEP_ALG_BYTES = 9 * POP * 2 + 4 * 2      # the whole step: populations and T in and out
 KERNEL_SRC = os.path.join(ROOT, "paper_1912_02018_gb300", "csrc", "lbm_kernels.cuh")
 
 
@@ -181,7 +183,7 @@ def run_ours(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     case = WORKLOADS[args.workload]
     nodes = case.nx * case.ny
-    sim = Sim.from_case(case, f64=False, psi_mode=args.psi_mode)  # seeded state generated on the device
+    sim = Sim.from_case(case, f64=False, storage=args.storage, psi_mode=args.psi_mode)  # state made on the device
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     clocks = Clocks(local) if rank == 0 else None
@@ -265,7 +267,7 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": case.name, "nx": case.nx, "ny": case.ny, "D": case.D, "Re": case.Re,
-                   "superheat_Tc": case.superheat_Tc, "storage": "f32",
+                   "superheat_Tc": case.superheat_Tc, "storage": args.storage,
                    "psi": ["double-float (FP32 pairs)", "IEEE f64", "f32"][args.psi_mode],
                    "l2": "flushed (256 MB write) before every timed step", "parallelism": "replicas"},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -292,6 +294,8 @@ def main():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="paper_shaped")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--storage", default="f32", choices=("f32", "f64", "f16s"),
+                    help="population storage of the FP32 build (shifted FP16: f - w rho_l)")
     ap.add_argument("--psi-mode", type=int, default=0, choices=(0, 1, 2),
                     help="psi evaluation of the FP32 build: 0 double-float (default), 1 IEEE FP64, 2 FP32")
     args = ap.parse_args()

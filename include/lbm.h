@@ -58,11 +58,13 @@ typedef enum {
     LBM_ESTATE = -6     /* call not valid in the context's current state */
 } lbm_status;
 
-/* Population storage.  Arithmetic is FP64 when compute_f64 is set, FP32 otherwise.
- * In the FP32 build the pseudopotential (Eq. potential) is evaluated with FP64-class
- * accuracy by default (see lbm_params.psi_mode); the wall heat flux is always
- * accumulated in FP64. */
-typedef enum { LBM_STORE_F64 = 0, LBM_STORE_F32 = 1 } lbm_storage;
+/* Population storage.  Arithmetic is FP64 when compute_f64 is set (storage must then be
+ * LBM_STORE_F64), FP32 otherwise, with populations stored as FP64, FP32 or shifted FP16
+ * h_i = f_i - w_i rho_l (FP16 rounding is finest near zero, where liquid populations then
+ * sit).  In the FP32 build the pseudopotential (Eq. potential) is evaluated with FP64-class
+ * accuracy by default (see lbm_params.psi_mode); the wall heat flux is always accumulated
+ * in FP64. */
+typedef enum { LBM_STORE_F64 = 0, LBM_STORE_F32 = 1, LBM_STORE_F16S = 2 } lbm_storage;
 
 typedef struct {
     int32_t nx, ny;     /* lattice size; nx, ny >= 5 */
@@ -93,7 +95,7 @@ typedef struct {
     double outlet_U;    /* convective-outlet speed; < 0: u_in */
     int64_t warmup_steps; /* steps with no force and no energy equation */
     int32_t energy;       /* 1: solve Eq. (energy); 0: keep T fixed */
-    int32_t storage;      /* lbm_storage; must be LBM_STORE_F64 when compute_f64 = 1 */
+    int32_t storage;      /* lbm_storage of the populations; must be LBM_STORE_F64 when compute_f64 = 1 */
     int32_t compute_f64;  /* 1: FP64 arithmetic throughout (the parity build) */
     int32_t psi_mode;     /* FP32 build only: how psi of Eq. (potential) is evaluated from FP32 rho, T:
                              0 double-float (FP32 pairs, ~2^-44 relative), 1 IEEE FP64, 2 FP32 */

@@ -13,7 +13,8 @@ LIB_PATH = os.path.join(HERE, "liblbm.so")
 LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_EUNSTABLE, LBM_ETIMEOUT, LBM_ESTATE = 0, -1, -2, -3, -4, -5, -6
 STATUS_NAMES = {0: "LBM_OK", -1: "LBM_EINVAL", -2: "LBM_ENOMEM", -3: "LBM_ECUDA", -4: "LBM_EUNSTABLE",
                 -5: "LBM_ETIMEOUT", -6: "LBM_ESTATE"}
-LBM_STORE_F64, LBM_STORE_F32 = 0, 1
+LBM_STORE_F64, LBM_STORE_F32, LBM_STORE_F16S = 0, 1, 2
+STORAGE = {"f64": LBM_STORE_F64, "f32": LBM_STORE_F32, "f16s": LBM_STORE_F16S}
 FIELD_BITS = {"rho": 1, "ux": 2, "uy": 4, "T": 8, "psi": 16, "solid": 32}
 
 # every symbol include/lbm.h declares

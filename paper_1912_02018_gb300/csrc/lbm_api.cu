@@ -239,12 +239,12 @@ lbm_status check_status(lbm_ctx* c) {
 }
 
 int do_export(lbm_ctx* c, int which, double* dst) {
-  return c->f64 ? lbm::export_f64(c->geo, c->dev, c->cur, c->tcur, which, dst, c->stream)
-                : lbm::export_f32(c->geo, c->dev, c->cur, c->tcur, which, dst, c->stream);
+  return c->f64 ? lbm::export_f64(c->geo, c->ph, c->dev, c->cur, c->tcur, which, dst, c->stream)
+                : lbm::export_f32(c->geo, c->ph, c->dev, c->cur, c->tcur, which, c->prm.storage, dst, c->stream);
 }
 int do_import(lbm_ctx* c, int which, const double* src) {
-  return c->f64 ? lbm::import_f64(c->geo, c->dev, c->cur, c->tcur, which, src, c->stream)
-                : lbm::import_f32(c->geo, c->dev, c->cur, c->tcur, which, src, c->stream);
+  return c->f64 ? lbm::import_f64(c->geo, c->ph, c->dev, c->cur, c->tcur, which, src, c->stream)
+                : lbm::import_f32(c->geo, c->ph, c->dev, c->cur, c->tcur, which, c->prm.storage, src, c->stream);
 }
 
 }  // namespace
@@ -263,8 +263,8 @@ lbm_status lbm_create(const lbm_domain* domain, const lbm_cylinder* cyl, const l
     return fail(nullptr, LBM_EINVAL, "lattice too large: 9 ny pitch must stay below 2^31");
   if (P.compute_f64 && P.storage != LBM_STORE_F64)
     return fail(nullptr, LBM_EINVAL, "compute_f64 = 1 needs storage = LBM_STORE_F64");
-  if (!P.compute_f64 && P.storage != LBM_STORE_F32)
-    return fail(nullptr, LBM_EINVAL, "FP32 compute needs storage = LBM_STORE_F32");
+  if (!P.compute_f64 && P.storage != LBM_STORE_F32 && P.storage != LBM_STORE_F64 && P.storage != LBM_STORE_F16S)
+    return fail(nullptr, LBM_EINVAL, "storage must be LBM_STORE_F64, LBM_STORE_F32 or LBM_STORE_F16S");
   if (P.psi_mode < 0 || P.psi_mode > 2) return fail(nullptr, LBM_EINVAL, "psi_mode must be 0, 1 or 2");
   if (!(P.a > 0 && P.b > 0 && P.R > 0)) return fail(nullptr, LBM_EINVAL, "EOS constants a, b, R must be > 0");
   if (P.G > 0) return fail(nullptr, LBM_EINVAL, "G must be <= 0 (Eq. potential needs G < 0; 0 = single phase)");
@@ -352,6 +352,11 @@ lbm_status lbm_create(const lbm_domain* domain, const lbm_cylinder* cyl, const l
   phys.invTc2 = split(1.0 / eos.Tc);
   phys.cs22 = split(1.0 / 3.0);
   phys.k2 = split(P.G != 0 ? 2.0 / (P.G * (1.0 / 3.0)) : 0.0);
+  {
+    static const double W[9] = {4.0 / 9.0, 1.0 / 9.0, 1.0 / 9.0, 1.0 / 9.0, 1.0 / 9.0,
+                                1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0};
+    for (int i = 0; i < 9; ++i) phys.pop_shift[i] = (float)(W[i] * rho_l);
+  }
   for (double nu : {ph.nu_l, ph.nu_v}) {
     const double omega = 1.0 / (nu * 3.0 + 0.5);
     if (!(nu > 0) || !(omega > 0 && omega < 2)) {
@@ -416,11 +421,12 @@ lbm_status lbm_create(const lbm_domain* domain, const lbm_cylinder* cyl, const l
     }
 
   // device memory
-  const size_t es = c->f64 ? sizeof(double) : sizeof(float);
+  const size_t es = c->f64 ? sizeof(double) : sizeof(float);  // compute-type fields
+  const size_t ps = P.storage == LBM_STORE_F64 ? 8 : (P.storage == LBM_STORE_F16S ? 2 : 4);  // populations
   const size_t N = (size_t)plane;
   lbm::Dev& d = c->dev;
-  d.f[0] = dalloc(c, 9 * N * es);
-  d.f[1] = dalloc(c, 9 * N * es);
+  d.f[0] = dalloc(c, 9 * N * ps);
+  d.f[1] = dalloc(c, 9 * N * ps);
   d.T[0] = dalloc(c, N * es);
   d.T[1] = dalloc(c, N * es);
   d.psi = dalloc(c, N * es);
@@ -476,9 +482,9 @@ lbm_status lbm_create(const lbm_domain* domain, const lbm_cylinder* cyl, const l
   const int ok = c->f64 ? lbm::init_f64(g, phys, d, dsrc[0], dsrc[1], dsrc[2], dsrc[3], dsrc[4], P.seed, P.noise_amp,
                                         c->stream)
                         : lbm::init_f32(g, phys, d, dsrc[0], dsrc[1], dsrc[2], dsrc[3], dsrc[4], P.seed, P.noise_amp,
-                                        c->stream);
+                                        P.storage, c->stream);
   if (ok < 0) chk(cudaGetLastError());
-  chk(cudaMemcpyAsync(d.f[1], d.f[0], 9 * N * es, cudaMemcpyDeviceToDevice, c->stream));
+  chk(cudaMemcpyAsync(d.f[1], d.f[0], 9 * N * ps, cudaMemcpyDeviceToDevice, c->stream));
   chk(cudaMemcpyAsync(d.T[1], d.T[0], N * es, cudaMemcpyDeviceToDevice, c->stream));
   chk(cudaMemcpyAsync(d.side[1], d.side[0], 3 * g.ny * es, cudaMemcpyDeviceToDevice, c->stream));
   chk(cudaStreamSynchronize(c->stream));
@@ -504,7 +510,7 @@ lbm_status lbm_step(lbm_ctx* c, int64_t n) {
     const int k = c->f64 ? lbm::step_f64(c->geo, c->ph, c->dev, c->cur, c->tcur, forcing, c->prm.energy,
                                          c->prm.psi_mode, c->stream, hk, &flipped)
                          : lbm::step_f32(c->geo, c->ph, c->dev, c->cur, c->tcur, forcing, c->prm.energy,
-                                         c->prm.psi_mode, c->stream, hk, &flipped);
+                                         c->prm.psi_mode, c->prm.storage, c->stream, hk, &flipped);
     if (k < 0) return fail(c, LBM_ECUDA, "kernel launch failed: %s", cudaGetErrorString(cudaGetLastError()));
     c->launches += k;
     c->cur ^= 1;

@@ -1,27 +1,54 @@
-// FP32 instantiation of the step kernels: float populations and float arithmetic
-// (FMA contraction allowed).  psi is evaluated in double-float arithmetic by default
+// FP32-compute instantiation of the step kernels (FMA contraction allowed), for populations
+// stored as FP64, FP32 or shifted FP16.  psi is evaluated in double-float arithmetic by default
 // (IEEE FP64 or plain FP32 on request) and the wall heat flux is accumulated in FP64.
+#include "lbm.h"
 #include "lbm_kernels.cuh"
 
 namespace lbm {
 
-int step_f32(const Geo& g, const Phys& ph, const Dev& d, int cur, int tcur, int forcing, int energy, int psi_mode,
-             cudaStream_t s, const LaunchHook* hook, int* t_flipped) {
+namespace {
+template <typename S>
+int step_s(const Geo& g, const Phys& ph, const Dev& d, int cur, int tcur, int forcing, int energy, int psi_mode,
+           cudaStream_t s, const LaunchHook* hook, int* t_flipped) {
   switch (psi_mode) {
-    case kPsiF64: return step_impl<float, float, kPsiF64>(g, ph, d, cur, tcur, forcing, energy, s, hook, t_flipped);
-    case kPsiF32: return step_impl<float, float, kPsiF32>(g, ph, d, cur, tcur, forcing, energy, s, hook, t_flipped);
-    default: return step_impl<float, float, kPsiDF>(g, ph, d, cur, tcur, forcing, energy, s, hook, t_flipped);
+    case kPsiF64: return step_impl<float, S, kPsiF64>(g, ph, d, cur, tcur, forcing, energy, s, hook, t_flipped);
+    case kPsiF32: return step_impl<float, S, kPsiF32>(g, ph, d, cur, tcur, forcing, energy, s, hook, t_flipped);
+    default: return step_impl<float, S, kPsiDF>(g, ph, d, cur, tcur, forcing, energy, s, hook, t_flipped);
   }
 }
-int export_f32(const Geo& g, const Dev& d, int cur, int tcur, int which, double* dst, cudaStream_t s) {
-  return export_impl<float, float>(g, d, cur, tcur, which, dst, s);
+}  // namespace
+
+int step_f32(const Geo& g, const Phys& ph, const Dev& d, int cur, int tcur, int forcing, int energy, int psi_mode,
+             int storage, cudaStream_t s, const LaunchHook* hook, int* t_flipped) {
+  switch (storage) {
+    case LBM_STORE_F64: return step_s<double>(g, ph, d, cur, tcur, forcing, energy, psi_mode, s, hook, t_flipped);
+    case LBM_STORE_F16S: return step_s<__half>(g, ph, d, cur, tcur, forcing, energy, psi_mode, s, hook, t_flipped);
+    default: return step_s<float>(g, ph, d, cur, tcur, forcing, energy, psi_mode, s, hook, t_flipped);
+  }
 }
-int import_f32(const Geo& g, const Dev& d, int cur, int tcur, int which, const double* src, cudaStream_t s) {
-  return import_impl<float, float>(g, d, cur, tcur, which, src, s);
+int export_f32(const Geo& g, const Phys& ph, const Dev& d, int cur, int tcur, int which, int storage, double* dst,
+               cudaStream_t s) {
+  switch (storage) {
+    case LBM_STORE_F64: return export_impl<float, double>(g, ph, d, cur, tcur, which, dst, s);
+    case LBM_STORE_F16S: return export_impl<float, __half>(g, ph, d, cur, tcur, which, dst, s);
+    default: return export_impl<float, float>(g, ph, d, cur, tcur, which, dst, s);
+  }
+}
+int import_f32(const Geo& g, const Phys& ph, const Dev& d, int cur, int tcur, int which, int storage,
+               const double* src, cudaStream_t s) {
+  switch (storage) {
+    case LBM_STORE_F64: return import_impl<float, double>(g, ph, d, cur, tcur, which, src, s);
+    case LBM_STORE_F16S: return import_impl<float, __half>(g, ph, d, cur, tcur, which, src, s);
+    default: return import_impl<float, float>(g, ph, d, cur, tcur, which, src, s);
+  }
 }
 int init_f32(const Geo& g, const Phys& ph, const Dev& d, const double* rho0, const double* drho, const double* ux0,
-             const double* uy0, const double* T0, unsigned long long seed, double amp, cudaStream_t s) {
-  return init_impl<float, float>(g, ph, d, rho0, drho, ux0, uy0, T0, seed, amp, s);
+             const double* uy0, const double* T0, unsigned long long seed, double amp, int storage, cudaStream_t s) {
+  switch (storage) {
+    case LBM_STORE_F64: return init_impl<float, double>(g, ph, d, rho0, drho, ux0, uy0, T0, seed, amp, s);
+    case LBM_STORE_F16S: return init_impl<float, __half>(g, ph, d, rho0, drho, ux0, uy0, T0, seed, amp, s);
+    default: return init_impl<float, float>(g, ph, d, rho0, drho, ux0, uy0, T0, seed, amp, s);
+  }
 }
 
 }  // namespace lbm

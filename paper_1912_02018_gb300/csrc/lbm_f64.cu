@@ -10,11 +10,12 @@ int step_f64(const Geo& g, const Phys& ph, const Dev& d, int cur, int tcur, int 
   (void)psi_mode;  // the FP64 build always evaluates psi in IEEE FP64
   return step_impl<double, double, kPsiF64>(g, ph, d, cur, tcur, forcing, energy, s, hook, t_flipped);
 }
-int export_f64(const Geo& g, const Dev& d, int cur, int tcur, int which, double* dst, cudaStream_t s) {
-  return export_impl<double, double>(g, d, cur, tcur, which, dst, s);
+int export_f64(const Geo& g, const Phys& ph, const Dev& d, int cur, int tcur, int which, double* dst, cudaStream_t s) {
+  return export_impl<double, double>(g, ph, d, cur, tcur, which, dst, s);
 }
-int import_f64(const Geo& g, const Dev& d, int cur, int tcur, int which, const double* src, cudaStream_t s) {
-  return import_impl<double, double>(g, d, cur, tcur, which, src, s);
+int import_f64(const Geo& g, const Phys& ph, const Dev& d, int cur, int tcur, int which, const double* src,
+               cudaStream_t s) {
+  return import_impl<double, double>(g, ph, d, cur, tcur, which, src, s);
 }
 int init_f64(const Geo& g, const Phys& ph, const Dev& d, const double* rho0, const double* drho, const double* ux0,
              const double* uy0, const double* T0, unsigned long long seed, double amp, cudaStream_t s) {

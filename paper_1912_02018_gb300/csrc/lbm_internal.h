@@ -41,6 +41,7 @@ struct Phys {
   PhysC<double> d;
   PhysC<float> f;
   F2 a2, b2, R2, kappa2, invTc2, cs22, k2;
+  float pop_shift[9];  // shifted FP16 storage keeps f_i - w_i rho_l; these are w_i rho_l
 };
 
 // psi evaluation of the FP32 build (Eq. potential with Eq. eos); values of lbm_params.psi_mode.
@@ -89,22 +90,26 @@ struct LaunchHook {
 // Returns the number of kernels launched, or -1 on a launch error.
 int step_f64(const Geo& g, const Phys& ph, const Dev& d, int cur, int tcur, int forcing, int energy, int psi_mode,
              cudaStream_t s, const LaunchHook* hook, int* t_flipped);
+// FP32 compute with population storage `storage` (lbm_storage: 0 FP64, 1 FP32, 2 shifted FP16).
 int step_f32(const Geo& g, const Phys& ph, const Dev& d, int cur, int tcur, int forcing, int energy, int psi_mode,
-             cudaStream_t s, const LaunchHook* hook, int* t_flipped);
+             int storage, cudaStream_t s, const LaunchHook* hook, int* t_flipped);
 
 // Field export: copy a typed [ny][pitch] field (which: 0 rho, 1 ux, 2 uy, 3 T, 4 psi, 5 solid,
 // 10+i population plane i of buffer cur, 20+j outlet side row j of buffer cur) into a dense
 // double buffer.  T is taken from buffer tcur.
-int export_f64(const Geo& g, const Dev& d, int cur, int tcur, int which, double* dst, cudaStream_t s);
-int export_f32(const Geo& g, const Dev& d, int cur, int tcur, int which, double* dst, cudaStream_t s);
+int export_f64(const Geo& g, const Phys& ph, const Dev& d, int cur, int tcur, int which, double* dst, cudaStream_t s);
+int export_f32(const Geo& g, const Phys& ph, const Dev& d, int cur, int tcur, int which, int storage, double* dst,
+               cudaStream_t s);
 // Field import: the reverse, for T (3), population planes (10+i) and side rows (20+j).
-int import_f64(const Geo& g, const Dev& d, int cur, int tcur, int which, const double* src, cudaStream_t s);
-int import_f32(const Geo& g, const Dev& d, int cur, int tcur, int which, const double* src, cudaStream_t s);
+int import_f64(const Geo& g, const Phys& ph, const Dev& d, int cur, int tcur, int which, const double* src,
+               cudaStream_t s);
+int import_f32(const Geo& g, const Phys& ph, const Dev& d, int cur, int tcur, int which, int storage,
+               const double* src, cudaStream_t s);
 // Initial state: populations at the Hermite equilibrium of (rho0 + drho, ux0, uy0), T = T0;
 // array arguments are dense [ny][nx] device doubles or NULL (see lbm_init in lbm.h).
 int init_f64(const Geo& g, const Phys& ph, const Dev& d, const double* rho0, const double* drho, const double* ux0,
              const double* uy0, const double* T0, unsigned long long seed, double amp, cudaStream_t s);
 int init_f32(const Geo& g, const Phys& ph, const Dev& d, const double* rho0, const double* drho, const double* ux0,
-             const double* uy0, const double* T0, unsigned long long seed, double amp, cudaStream_t s);
+             const double* uy0, const double* T0, unsigned long long seed, double amp, int storage, cudaStream_t s);
 
 }  // namespace lbm

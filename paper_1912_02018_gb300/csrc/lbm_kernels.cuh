@@ -15,6 +15,8 @@
 // that the FP64 build (compiled without FMA contraction) rounds like a plain reference.
 #pragma once
 
+#include <cuda_fp16.h>
+
 #include <cstdint>
 
 #include "lbm_internal.h"
@@ -92,9 +94,33 @@ __device__ __forceinline__ int map_x(const Geo& g, int x) {
 __device__ __forceinline__ int wrap_y(const Geo& g, int y) {  // offsets |dy| <= 2 < ny
   return y < 0 ? y + g.ny : (y >= g.ny ? y - g.ny : y);
 }
+// Population storage: FP64 or FP32 values as they are, or shifted FP16 h_i = f_i - w_i rho_l
+// (the shift keeps liquid populations near zero, where FP16 is finest).
 template <typename C, typename S>
-__device__ __forceinline__ C ldf(const Geo& g, const S* __restrict__ f, int i, int y, int x) {
-  return static_cast<C>(f[i * g.plane + y * g.pitch + x]);
+struct PopIO {
+  static __device__ __forceinline__ C ld(S v, int, const Phys&) { return static_cast<C>(v); }
+  static __device__ __forceinline__ S st(C v, int, const Phys&) { return static_cast<S>(v); }
+  static __device__ __forceinline__ double ld_d(S v, int, const Phys&) { return static_cast<double>(v); }
+  static __device__ __forceinline__ S st_d(double v, int, const Phys&) { return static_cast<S>(v); }
+};
+template <typename C>
+struct PopIO<C, __half> {
+  static __device__ __forceinline__ C ld(__half v, int i, const Phys& ph) {
+    return static_cast<C>(__half2float(v) + ph.pop_shift[i]);
+  }
+  static __device__ __forceinline__ __half st(C v, int i, const Phys& ph) {
+    return __float2half_rn(static_cast<float>(v) - ph.pop_shift[i]);
+  }
+  static __device__ __forceinline__ double ld_d(__half v, int i, const Phys& ph) {
+    return static_cast<double>(__half2float(v) + ph.pop_shift[i]);
+  }
+  static __device__ __forceinline__ __half st_d(double v, int i, const Phys& ph) {
+    return __float2half_rn(static_cast<float>(v) - ph.pop_shift[i]);
+  }
+};
+template <typename C, typename S>
+__device__ __forceinline__ C ldf(const Geo& g, const Phys& ph, const S* __restrict__ f, int i, int y, int x) {
+  return PopIO<C, S>::ld(f[i * g.plane + y * g.pitch + x], i, ph);
 }
 
 // ---------------------------------------------------------------- double-float arithmetic
@@ -346,18 +372,18 @@ __device__ __forceinline__ void pull_slow(const Geo& g, const Phys& ph, const S*
       // linear interpolated bounce-back; the wall lies along c_opp(i)
       const int io = oppv(i);
       const C q = C(link_fraction(g, x, y, -cx, -cy));
-      const C a = ldf<C>(g, f, io, y, x);
+      const C a = ldf<C>(g, ph, f, io, y, x);
       if (q < C(0.5)) {
         int nxp = x + cx;
         const int nyp = wrap_y(g, y + cy);
         if (g.periodic_x) nxp = nxp < 0 ? nxp + g.nx : (nxp >= g.nx ? nxp - g.nx : nxp);
         const bool ok = nxp >= 0 && nxp < g.nx && !(mask[nyp * g.pitch + nxp] & kSolid);
-        v = ok ? C(2) * q * a + (C(1) - C(2) * q) * ldf<C>(g, f, io, nyp, nxp) : a;
+        v = ok ? C(2) * q * a + (C(1) - C(2) * q) * ldf<C>(g, ph, f, io, nyp, nxp) : a;
       } else {
-        v = fdiv(a, C(2) * q) + fdiv(C(2) * q - C(1), C(2) * q) * ldf<C>(g, f, i, y, x);
+        v = fdiv(a, C(2) * q) + fdiv(C(2) * q - C(1), C(2) * q) * ldf<C>(g, ph, f, i, y, x);
       }
     } else {
-      v = ldf<C>(g, f, i, sy, sx);
+      v = ldf<C>(g, ph, f, i, sy, sx);
     }
     fo[i] = v;
   }
@@ -376,7 +402,7 @@ __device__ __forceinline__ void pull_slow(const Geo& g, const Phys& ph, const S*
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
       const int i = j == 0 ? 2 : (j == 1 ? 6 : 8);
-      const C inner = ldf<C>(g, f, i, wrap_y(g, y - cyv(i)), g.nx - 1);
+      const C inner = ldf<C>(g, ph, f, i, wrap_y(g, y - cyv(i)), g.nx - 1);
       const C v = fdiv(side_in[j * g.ny + y] + U * inner, C(1) + U);
       fo[i] = v;
       if (side_out) side_out[j * g.ny + y] = v;
@@ -400,15 +426,15 @@ __device__ __forceinline__ void pull_node(const Geo& g, const Phys& ph, const S*
     xm = xm < 0 ? g.nx - 1 : xm;
     xp = xp >= g.nx ? 0 : xp;
   }
-  fo[0] = ldf<C>(g, f, 0, y, x);
-  fo[1] = ldf<C>(g, f, 1, y, xm);
-  fo[2] = ldf<C>(g, f, 2, y, xp);
-  fo[3] = ldf<C>(g, f, 3, ym, x);
-  fo[4] = ldf<C>(g, f, 4, yp, x);
-  fo[5] = ldf<C>(g, f, 5, ym, xm);
-  fo[6] = ldf<C>(g, f, 6, yp, xp);
-  fo[7] = ldf<C>(g, f, 7, yp, xm);
-  fo[8] = ldf<C>(g, f, 8, ym, xp);
+  fo[0] = ldf<C>(g, ph, f, 0, y, x);
+  fo[1] = ldf<C>(g, ph, f, 1, y, xm);
+  fo[2] = ldf<C>(g, ph, f, 2, y, xp);
+  fo[3] = ldf<C>(g, ph, f, 3, ym, x);
+  fo[4] = ldf<C>(g, ph, f, 4, yp, x);
+  fo[5] = ldf<C>(g, ph, f, 5, ym, xm);
+  fo[6] = ldf<C>(g, ph, f, 6, yp, xp);
+  fo[7] = ldf<C>(g, ph, f, 7, yp, xm);
+  fo[8] = ldf<C>(g, ph, f, 8, ym, xp);
 }
 
 // psi at node (x, y): pull, rho = sum f, Eq. (potential); solid nodes use rho_s.
@@ -558,7 +584,7 @@ __global__ void __launch_bounds__(kCollTX* kCollTY)
   C fs[9], ux, uy;
   collide(fo, rho, Fx, Fy, Fmx, Fmy, psi0, omega, sig, fs, ux, uy);
 #pragma unroll
-  for (int i = 0; i < 9; ++i) fn[i * g.plane + id] = static_cast<S>(fs[i]);
+  for (int i = 0; i < 9; ++i) fn[i * g.plane + id] = PopIO<C, S>::st(fs[i], i, ph);
   rho_o[id] = rho;
   ux_o[id] = ux;
   uy_o[id] = uy;
@@ -881,7 +907,7 @@ __global__ void __launch_bounds__(256) k_init(Geo g, Phys ph, const double* rho0
   double fe[9];
   feq_hermite(r, u, v, fe);
 #pragma unroll
-  for (int i = 0; i < 9; ++i) f[i * g.plane + id] = static_cast<S>(fe[i]);
+  for (int i = 0; i < 9; ++i) f[i * g.plane + id] = PopIO<C, S>::st_d(fe[i], i, ph);
   T[id] = (C)t;
   rho_o[id] = (C)r;
   ux_o[id] = (C)u;
@@ -907,6 +933,21 @@ static __global__ void k_export_solid(Geo g, const uint8_t* __restrict__ mask, d
   const int y = blockIdx.y;
   if (x >= g.nx || y >= g.ny) return;
   dst[y * g.nx + x] = (mask[y * g.pitch + x] & kSolid) ? 1.0 : 0.0;
+}
+
+template <typename C, typename S>
+__global__ void k_export_pop(Geo g, Phys ph, const S* __restrict__ src, int i, double* __restrict__ dst) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y;
+  if (x >= g.nx || y >= g.ny) return;
+  dst[y * g.nx + x] = PopIO<C, S>::ld_d(src[y * g.pitch + x], i, ph);
+}
+template <typename C, typename S>
+__global__ void k_import_pop(Geo g, Phys ph, S* __restrict__ dst, int i, const double* __restrict__ src) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y;
+  if (x >= g.nx || y >= g.ny) return;
+  dst[y * g.pitch + x] = PopIO<C, S>::st_d(src[y * g.nx + x], i, ph);
 }
 
 template <typename E>
@@ -966,7 +1007,7 @@ int step_impl(const Geo& g, const Phys& ph, const Dev& d, int cur, int tcur, int
 }
 
 template <typename C, typename S>
-int export_impl(const Geo& g, const Dev& d, int cur, int tcur, int which, double* dst, cudaStream_t s) {
+int export_impl(const Geo& g, const Phys& ph, const Dev& d, int cur, int tcur, int which, double* dst, cudaStream_t s) {
   using namespace kern;
   const dim3 blk(256);
   if (which >= 20 && which < 23) {
@@ -974,7 +1015,7 @@ int export_impl(const Geo& g, const Dev& d, int cur, int tcur, int which, double
     k_export<C><<<dim3((g.ny + 255) / 256, 1), blk, 0, s>>>(g, src, g.ny, 1, dst, g.ny);
   } else if (which >= 10 && which < 19) {
     const S* src = static_cast<const S*>(d.f[cur]) + (which - 10) * g.plane;
-    k_export<S><<<dim3((g.nx + 255) / 256, g.ny), blk, 0, s>>>(g, src, g.pitch, g.ny, dst, g.nx);
+    k_export_pop<C, S><<<dim3((g.nx + 255) / 256, g.ny), blk, 0, s>>>(g, ph, src, which - 10, dst);
   } else if (which == 5) {
     k_export_solid<<<dim3((g.nx + 255) / 256, g.ny), blk, 0, s>>>(g, d.mask, dst);
   } else {
@@ -985,7 +1026,8 @@ int export_impl(const Geo& g, const Dev& d, int cur, int tcur, int which, double
 }
 
 template <typename C, typename S>
-int import_impl(const Geo& g, const Dev& d, int cur, int tcur, int which, const double* src, cudaStream_t s) {
+int import_impl(const Geo& g, const Phys& ph, const Dev& d, int cur, int tcur, int which, const double* src,
+                cudaStream_t s) {
   using namespace kern;
   const dim3 blk(256);
   if (which >= 20 && which < 23) {
@@ -993,7 +1035,7 @@ int import_impl(const Geo& g, const Dev& d, int cur, int tcur, int which, const 
     k_import<C><<<dim3((g.ny + 255) / 256, 1), blk, 0, s>>>(g, dst, g.ny, 1, src, g.ny);
   } else if (which >= 10 && which < 19) {
     S* dst = static_cast<S*>(d.f[cur]) + (which - 10) * g.plane;
-    k_import<S><<<dim3((g.nx + 255) / 256, g.ny), blk, 0, s>>>(g, dst, g.pitch, g.ny, src, g.nx);
+    k_import_pop<C, S><<<dim3((g.nx + 255) / 256, g.ny), blk, 0, s>>>(g, ph, dst, which - 10, src);
   } else if (which == 3) {
     k_import<C><<<dim3((g.nx + 255) / 256, g.ny), blk, 0, s>>>(g, static_cast<C*>(d.T[tcur]), g.pitch, g.ny, src,
                                                                  g.nx);

@@ -31,14 +31,16 @@ class Sim:
 
     nx, ny, periodic_x             lattice (flow along +x; periodic in y)
     D, xc, yc, superheat_Tc, rho_s  cylinder (D <= 0: none)
-    f64                            FP64 arithmetic and storage (else FP32)
+    f64                            FP64 arithmetic and storage (else FP32 arithmetic)
+    storage                        FP32 arithmetic only: populations stored as "f32" (default), "f64" or
+                                   "f16s" (shifted FP16)
     init                           optional dict of [ny][nx] arrays: rho, drho, ux, uy, T
     other keywords                 fields of lbm_params (see include/lbm.h)
     torch_alloc                    device memory from PyTorch's caching allocator
     """
 
     def __init__(self, nx, ny, D=0.0, xc=0.0, yc=0.0, periodic_x=0, superheat_Tc=0.05, rho_s=0.0, f64=False,
-                 init=None, stream=None, torch_alloc=True, **params):
+                 storage="f32", init=None, stream=None, torch_alloc=True, **params):
         import torch
 
         self._torch = torch
@@ -56,7 +58,7 @@ class Sim:
                        Tr_sat=kw["Tr_sat"], Re=kw["Re"], u_in=kw["u_in"], nu_l=kw["nu_l"],
                        nu_ratio=kw["nu_ratio"], Pr_l=kw["Pr_l"], Pr_v=kw["Pr_v"], c_v=kw["c_v"], g=kw["g"],
                        outlet_U=kw["outlet_U"], warmup_steps=int(kw["warmup"]), energy=int(kw["energy"]),
-                       storage=N.LBM_STORE_F64 if f64 else N.LBM_STORE_F32, compute_f64=1 if f64 else 0,
+                       storage=N.LBM_STORE_F64 if f64 else N.STORAGE[storage], compute_f64=1 if f64 else 0,
                        psi_mode=int(kw["psi_mode"]), seed=int(kw["seed"]), noise_amp=kw["noise_amp"])
         n = self.nx * self.ny
         init = init or {}

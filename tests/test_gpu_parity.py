@@ -99,6 +99,29 @@ def test_fp32_parity_200_steps_plain_method_case():
     assert abs(hg["q_mean"] - hr["q_mean"]) <= 1e-3 * abs(hr["q_mean"])
 
 
+@pytest.mark.parametrize("storage,tol", [("f64", 1e-5), ("f16s", 2e-4)])
+def test_fp32_compute_with_other_population_storage(storage, tol):
+    # FP32 arithmetic with populations stored as FP64 or as shifted FP16 (h = f - w rho_l)
+    case = si.SMALL
+    init = {"drho": case.drho()}
+    sim = Sim().from_case(case, f64=False, storage=storage, init=init).step(200)
+    ref = Oracle(case, **init).step(200)
+    fluid = ref.field("solid") == 0
+    got = sim.fields(("rho", "T"))
+    errs = {k: rel(got[k], ref.field(k), fluid) for k in ("rho", "T")}
+    assert max(errs.values()) < tol, errs
+
+
+def test_shifted_fp16_state_round_trip():
+    case = si.SMALL
+    a = Sim().from_case(case, storage="f16s").step(10)
+    f, T, side, n = a.get_state()
+    b = Sim().from_case(case, storage="f16s")
+    b.set_state(f, T, side, n)
+    f2, T2, side2, n2 = b.get_state()
+    assert np.array_equal(f, f2) and np.array_equal(T, T2) and n2 == n
+
+
 def _two_phase_periodic():
     c = si.Case(nx=40, ny=24, D=0.0, xc=0.0, yc=0.0, periodic_x=1, g=3e-5, u_in=0.0, nu_l=0.1,
                 superheat_Tc=0.0, noise_amp=0.0, name="periodic_two_phase")
