@@ -169,6 +169,51 @@ def run_reference(args):
     return 0
 
 
+def run_batch(args):
+    """Boiling-curve sweep: 64 independent domains, batched (tuned tiles, CUDA graph) against the
+    same 64 domains stepped one after another through their own contexts."""
+    import torch
+
+    from paper_1912_02018_gb300 import Batch, Sim
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    cases = si.batch_sweep(64, seed=1)
+    nodes = sum(c.nx * c.ny for c in cases)
+    stream = torch.cuda.current_stream()
+    b = Batch(cases)
+    variant = b.tune(2)
+    b.step(args.warmup)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    b.step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_b = e0.elapsed_time(e1)
+    b.close()
+    sims = [Sim.from_case(c) for c in cases]
+    for _ in range(args.warmup):
+        for s in sims:
+            s.step(1)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        for s in sims:
+            s.step(1)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_s = e0.elapsed_time(e1)
+    line = {"metric": METRIC, "value": nodes * args.steps / (ms_b / 1e3) / 1e6, "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_b / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "sweep64_12Dx6D_D40-128_Re300", "domains": len(cases), "nodes": nodes,
+                       "l2": "inputs larger than L2", "tile_variant": variant},
+            "sequential": {"value": nodes * args.steps / (ms_s / 1e3) / 1e6, "ms_per_step": ms_s / args.steps},
+            "speedup_vs_sequential": ms_s / ms_b}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -291,7 +336,7 @@ def main():
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=50)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="paper_shaped")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["sweep64"], default="paper_shaped")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--storage", default="f32", choices=("f32", "f64", "f16s"),
@@ -303,6 +348,8 @@ def main():
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "sweep64":
+        return run_batch(args)
     return run_ours(args)
 
 

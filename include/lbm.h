@@ -206,6 +206,34 @@ lbm_status lbm_profile(lbm_ctx *ctx, int enable);
 lbm_status lbm_profile_read(lbm_ctx *ctx, const char **names, int64_t *launches, double *total_ms,
                             int32_t max_kernels, int32_t *n_kernels);
 
+/* ---------------------------------------------------------------------------------
+ * Batches: many independent domains (uneven sizes allowed) stepped together.
+ * Each step is one kernel launch per pass (psi, collision, energy) over the tiles of all
+ * domains; once every domain is past its warm-up, pairs of steps are replayed from a
+ * CUDA graph.  Not part of the paper's method (its boiling curve is a set of separate
+ * runs, Sec. IV.B); it changes how the same per-domain step is scheduled, not what it
+ * computes: every domain gives the same fields as its own context would.
+ * ------------------------------------------------------------------------------- */
+typedef struct lbm_batch lbm_batch; /* opaque, owned by the library */
+
+/* Create n >= 1 domains from arrays of n descriptors.  All must share compute_f64, with
+ * storage F32 (FP32 build) or F64 (FP64 build) and psi_mode 0.  Errors as lbm_create;
+ * cuda_stream: the caller's stream, on which lbm_batch_step orders its work. */
+lbm_status lbm_batch_create(int32_t n, const lbm_domain *domains, const lbm_cylinder *cyls, const lbm_params *params,
+                            const lbm_allocator *alloc, void *cuda_stream, lbm_batch **out);
+/* Enqueue n >= 0 steps of every domain (asynchronous). */
+lbm_status lbm_batch_step(lbm_batch *b, int64_t n);
+/* Autotuner: time each tile-shape variant on steps_per_variant real steps (they advance
+ * the simulation), keep the fastest; *variant (may be NULL) receives its index. */
+lbm_status lbm_batch_tune(lbm_batch *b, int32_t steps_per_variant, int32_t *variant);
+/* CUDA-graph replay on (1, default) or off (0). */
+lbm_status lbm_batch_graph(lbm_batch *b, int enable);
+/* Borrowed handle of domain i for lbm_fields, lbm_get_state, lbm_wall_heat_flux and
+ * friends; lbm_step on it returns LBM_ESTATE and lbm_destroy on it does nothing. */
+lbm_status lbm_batch_domain(lbm_batch *b, int32_t i, lbm_ctx **ctx);
+/* Release the batch and all its domains.  NULL is a no-op. */
+void lbm_batch_destroy(lbm_batch *b);
+
 /*
  * Wall heat flux from caller-owned fields, with no context and no allocation.
  * The paper has no counterpart of this entry point; it exists for callers that cannot

@@ -7,9 +7,9 @@ nvcc_build.py; this package only marshals arguments to it.  Importing works with
 creating a Sim needs the built library and a CUDA device and fails loudly otherwise.
 """
 from . import _native  # noqa: F401
-from .sim import Sim  # noqa: F401
+from .sim import Batch, Sim  # noqa: F401
 
-__all__ = ["Sim", "build"]
+__all__ = ["Sim", "Batch", "build"]
 
 
 def build(force: bool = False, verbose: bool = False) -> str:

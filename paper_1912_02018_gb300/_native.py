@@ -20,7 +20,8 @@ FIELD_BITS = {"rho": 1, "ux": 2, "uy": 4, "T": 8, "psi": 16, "solid": 32}
 # every symbol include/lbm.h declares
 EXPORTS = ("lbm_create", "lbm_step", "lbm_sync", "lbm_wall_heat_flux", "lbm_reset_heat_flux", "lbm_fields",
            "lbm_get_state", "lbm_set_state", "lbm_info", "lbm_profile", "lbm_profile_read", "lbm_last_error",
-           "lbm_destroy", "lbm_wall_heat_flux_noalloc")
+           "lbm_destroy", "lbm_wall_heat_flux_noalloc", "lbm_batch_create", "lbm_batch_step", "lbm_batch_tune",
+           "lbm_batch_graph", "lbm_batch_domain", "lbm_batch_destroy")
 
 
 class Domain(C.Structure):
@@ -93,8 +94,16 @@ def lib():
                                              vp, vp]
     L.lbm_destroy.argtypes = [vp]
     L.lbm_destroy.restype = None
+    L.lbm_batch_create.argtypes = [C.c_int32, C.POINTER(Domain), C.POINTER(Cylinder), C.POINTER(Params),
+                                   C.POINTER(Allocator), vp, C.POINTER(vp)]
+    L.lbm_batch_step.argtypes = [vp, i64]
+    L.lbm_batch_tune.argtypes = [vp, C.c_int32, C.POINTER(C.c_int32)]
+    L.lbm_batch_graph.argtypes = [vp, C.c_int]
+    L.lbm_batch_domain.argtypes = [vp, C.c_int32, C.POINTER(vp)]
+    L.lbm_batch_destroy.argtypes = [vp]
+    L.lbm_batch_destroy.restype = None
     for name in EXPORTS:
-        if name not in ("lbm_last_error", "lbm_destroy"):
+        if name not in ("lbm_last_error", "lbm_destroy", "lbm_batch_destroy"):
             getattr(L, name).restype = C.c_int
     _LIB = L
     return L

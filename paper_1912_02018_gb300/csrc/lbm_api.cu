@@ -8,6 +8,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -156,6 +157,27 @@ struct lbm_ctx {
   double prof_ms[lbm::kNumKernels] = {};
   int64_t prof_n[lbm::kNumKernels] = {};
   cudaEvent_t open_ev = nullptr;
+  bool batch_owned = false;  // stepped only through its lbm_batch
+};
+
+struct lbm_batch {
+  std::vector<lbm_ctx*> ctx;
+  cudaStream_t stream = nullptr;   // the caller's stream
+  cudaStream_t gstream = nullptr;  // capture and replay stream of the graphs
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  bool f64 = false;
+  int variant = 0;
+  int cur = 0, tcur = 0;
+  long long steps = 0, max_warmup = 0;
+  std::vector<lbm::BatchDomain> h_doms;
+  lbm::BatchDomain* d_doms = nullptr;
+  int* d_maps = nullptr;  // psi map, collision map, energy map (each at most max_tiles)
+  int max_tiles = 0;
+  int nb_psi = 0, nb_coll = 0, nb_en = 0;
+  bool use_graph = true;
+  cudaGraphExec_t gexec = nullptr;
+  int g_cur = -1, g_tcur = -1, g_variant = -1;
+  std::string err = "no error";
 };
 
 namespace {
@@ -501,6 +523,7 @@ lbm_status lbm_create(const lbm_domain* domain, const lbm_cylinder* cyl, const l
 
 lbm_status lbm_step(lbm_ctx* c, int64_t n) {
   if (!c) return LBM_EINVAL;
+  if (c->batch_owned) return fail(c, LBM_ESTATE, "this domain belongs to a batch; step it with lbm_batch_step");
   if (n < 0) return fail(c, LBM_EINVAL, "negative step count");
   lbm::LaunchHook hook{hook_before, hook_after, c};
   const lbm::LaunchHook* hk = c->prof ? &hook : nullptr;
@@ -686,7 +709,7 @@ lbm_status lbm_profile_read(lbm_ctx* c, const char** names, int64_t* launches, d
 const char* lbm_last_error(const lbm_ctx* c) { return c ? c->err.c_str() : g_create_error.c_str(); }
 
 void lbm_destroy(lbm_ctx* c) {
-  if (!c) return;
+  if (!c || c->batch_owned) return;
   cudaStreamSynchronize(c->stream);
   for (auto& p : c->pending) {
     cudaEventDestroy(p.e0);
@@ -695,6 +718,262 @@ void lbm_destroy(lbm_ctx* c) {
   for (auto e : c->pool) cudaEventDestroy(e);
   dfree_all(c);
   delete c;
+}
+
+
+// ---------------------------------------------------------------- batches
+
+static lbm_status batch_fail(lbm_batch* b, lbm_status st, const char* msg) {
+  if (b) b->err = msg;
+  g_create_error = msg;
+  return st;
+}
+
+// Tile numbering of every pass for the current variant, and the block -> domain maps.
+static lbm_status batch_layout(lbm_batch* b) {
+  int cty, ety;
+  lbm::batch_variant(b->variant, b->f64, cty, ety);
+  std::vector<int> mp, mc, me;
+  for (size_t k = 0; k < b->ctx.size(); ++k) {
+    lbm::BatchDomain& D = b->h_doms[k];
+    const lbm::Geo& g = D.g;
+    const int ntx = (g.nx + 31) / 32;
+    D.psi_first = (int)mp.size();
+    D.psi_ntx = ntx;
+    mp.insert(mp.end(), (size_t)ntx * ((g.ny + 7) / 8), (int)k);
+    D.coll_first = (int)mc.size();
+    D.coll_ntx = ntx;
+    mc.insert(mc.end(), (size_t)ntx * ((g.ny + cty - 1) / cty), (int)k);
+    D.en_first = (int)me.size();
+    D.en_ntx = ntx;
+    D.en_nblocks = ntx * ((g.ny + ety - 1) / ety);
+    me.insert(me.end(), (size_t)D.en_nblocks, (int)k);
+  }
+  b->nb_psi = (int)mp.size();
+  b->nb_coll = (int)mc.size();
+  b->nb_en = (int)me.size();
+  if (b->nb_psi > b->max_tiles || b->nb_coll > b->max_tiles || b->nb_en > b->max_tiles)
+    return batch_fail(b, LBM_ESTATE, "batch tile maps larger than allocated");
+  cudaError_t e = cudaMemcpyAsync(b->d_doms, b->h_doms.data(), sizeof(lbm::BatchDomain) * b->h_doms.size(),
+                                  cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b->d_maps, mp.data(), sizeof(int) * mp.size(), cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b->d_maps + b->max_tiles, mc.data(), sizeof(int) * mc.size(), cudaMemcpyHostToDevice,
+                        b->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b->d_maps + 2 * b->max_tiles, me.data(), sizeof(int) * me.size(), cudaMemcpyHostToDevice,
+                        b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) return batch_fail(b, LBM_ECUDA, cudaGetErrorString(e));
+  return LBM_OK;
+}
+
+static int batch_launch(lbm_batch* b, cudaStream_t s) {
+  const int* m = b->d_maps;
+  return b->f64 ? lbm::batch_step_f64(b->variant, b->d_doms, m, b->nb_psi, m + b->max_tiles, b->nb_coll,
+                                      m + 2 * b->max_tiles, b->nb_en, b->cur, b->tcur, b->steps, s)
+                : lbm::batch_step_f32(b->variant, b->d_doms, m, b->nb_psi, m + b->max_tiles, b->nb_coll,
+                                      m + 2 * b->max_tiles, b->nb_en, b->cur, b->tcur, b->steps, s);
+}
+
+static void batch_advance(lbm_batch* b, int launches) {
+  b->cur ^= 1;
+  b->tcur ^= 1;
+  b->steps++;
+  for (lbm_ctx* c : b->ctx) {
+    c->cur = b->cur;
+    c->tcur = b->tcur;
+    c->steps = b->steps;
+    c->launches += launches;
+  }
+}
+
+
+lbm_status lbm_batch_create(int32_t n, const lbm_domain* domains, const lbm_cylinder* cyls, const lbm_params* params,
+                            const lbm_allocator* alloc, void* cuda_stream, lbm_batch** out) {
+  if (n < 1 || !domains || !cyls || !params || !out) return batch_fail(nullptr, LBM_EINVAL, "bad batch arguments");
+  *out = nullptr;
+  for (int k = 0; k < n; ++k) {
+    if (params[k].compute_f64 != params[0].compute_f64)
+      return batch_fail(nullptr, LBM_EINVAL, "all domains of a batch must share compute_f64");
+    const int want = params[k].compute_f64 ? LBM_STORE_F64 : LBM_STORE_F32;
+    if (params[k].storage != want || params[k].psi_mode != 0)
+      return batch_fail(nullptr, LBM_EINVAL, "batches need storage F32 (FP32) or F64 (FP64 build) and psi_mode 0");
+  }
+  lbm_batch* b = new lbm_batch();
+  b->stream = static_cast<cudaStream_t>(cuda_stream);
+  b->f64 = params[0].compute_f64 != 0;
+  for (int k = 0; k < n; ++k) {
+    lbm_ctx* c = nullptr;
+    lbm_status st = lbm_create(&domains[k], &cyls[k], &params[k], nullptr, alloc, cuda_stream, &c);
+    if (st != LBM_OK) {
+      std::string m = "domain " + std::to_string(k) + ": " + g_create_error;
+      for (lbm_ctx* x : b->ctx) {
+        x->batch_owned = false;
+        lbm_destroy(x);
+      }
+      delete b;
+      return batch_fail(nullptr, st, m.c_str());
+    }
+    c->batch_owned = true;
+    b->ctx.push_back(c);
+    lbm::BatchDomain D{};
+    D.g = c->geo;
+    D.ph = c->ph;
+    D.d = c->dev;
+    D.warmup = params[k].warmup_steps;
+    D.energy = params[k].energy;
+    b->h_doms.push_back(D);
+    b->max_warmup = std::max<long long>(b->max_warmup, params[k].warmup_steps);
+    b->max_tiles += ((domains[k].nx + 31) / 32) * ((domains[k].ny + 7) / 8);
+  }
+  cudaError_t e = cudaMalloc(&b->d_doms, sizeof(lbm::BatchDomain) * n);
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_maps, sizeof(int) * 3 * (size_t)b->max_tiles);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->gstream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming);
+  if (e != cudaSuccess) {
+    std::string m = cudaGetErrorString(e);
+    lbm_batch_destroy(b);
+    return batch_fail(nullptr, LBM_ENOMEM, m.c_str());
+  }
+  lbm_status st = batch_layout(b);
+  if (st != LBM_OK) {
+    std::string m = b->err;
+    lbm_batch_destroy(b);
+    return batch_fail(nullptr, st, m.c_str());
+  }
+  *out = b;
+  return LBM_OK;
+}
+
+lbm_status lbm_batch_step(lbm_batch* b, int64_t n) {
+  if (!b) return LBM_EINVAL;
+  if (n < 0) return batch_fail(b, LBM_EINVAL, "negative step count");
+  int64_t s = 0;
+  // eager steps until every domain is past its warm-up (the graph bakes in the step counter)
+  while (s < n && (b->steps < b->max_warmup || !b->use_graph || n - s < 2)) {
+    const int k = batch_launch(b, b->stream);
+    if (k < 0) return batch_fail(b, LBM_ECUDA, cudaGetErrorString(cudaGetLastError()));
+    batch_advance(b, k);
+    ++s;
+  }
+  if (s + 1 >= n) {
+    if (s < n) {
+      const int k = batch_launch(b, b->stream);
+      if (k < 0) return batch_fail(b, LBM_ECUDA, cudaGetErrorString(cudaGetLastError()));
+      batch_advance(b, k);
+    }
+    return LBM_OK;
+  }
+  // pairs of steps from a CUDA graph captured for the current buffer parity and variant
+  if (!b->gexec || b->g_cur != b->cur || b->g_tcur != b->tcur || b->g_variant != b->variant) {
+    if (b->gexec) {
+      cudaGraphExecDestroy(b->gexec);
+      b->gexec = nullptr;
+    }
+    cudaGraph_t graph = nullptr;
+    if (cudaStreamBeginCapture(b->gstream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+      return batch_fail(b, LBM_ECUDA, "stream capture failed to begin");
+    const int c0 = b->cur, t0 = b->tcur;
+    const long long s0 = b->steps;
+    int k1 = batch_launch(b, b->gstream);
+    b->cur ^= 1;
+    b->tcur ^= 1;
+    b->steps++;
+    int k2 = batch_launch(b, b->gstream);
+    b->cur = c0;
+    b->tcur = t0;
+    b->steps = s0;
+    cudaError_t e = cudaStreamEndCapture(b->gstream, &graph);
+    if (k1 < 0 || k2 < 0 || e != cudaSuccess) return batch_fail(b, LBM_ECUDA, "graph capture failed");
+    e = cudaGraphInstantiate(&b->gexec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return batch_fail(b, LBM_ECUDA, cudaGetErrorString(e));
+    b->g_cur = b->cur;
+    b->g_tcur = b->tcur;
+    b->g_variant = b->variant;
+  }
+  if (cudaEventRecord(b->ev_in, b->stream) != cudaSuccess || cudaStreamWaitEvent(b->gstream, b->ev_in, 0) != cudaSuccess)
+    return batch_fail(b, LBM_ECUDA, "event ordering failed");
+  for (; s + 2 <= n; s += 2) {
+    if (cudaGraphLaunch(b->gexec, b->gstream) != cudaSuccess) return batch_fail(b, LBM_ECUDA, "graph launch failed");
+    batch_advance(b, 3);
+    batch_advance(b, 3);
+  }
+  if (cudaEventRecord(b->ev_out, b->gstream) != cudaSuccess || cudaStreamWaitEvent(b->stream, b->ev_out, 0) != cudaSuccess)
+    return batch_fail(b, LBM_ECUDA, "event ordering failed");
+  if (s < n) {
+    const int k = batch_launch(b, b->stream);
+    if (k < 0) return batch_fail(b, LBM_ECUDA, cudaGetErrorString(cudaGetLastError()));
+    batch_advance(b, k);
+  }
+  return LBM_OK;
+}
+
+lbm_status lbm_batch_tune(lbm_batch* b, int32_t steps_per_variant, int32_t* variant) {
+  if (!b || steps_per_variant < 1) return LBM_EINVAL;
+  const int nv = b->f64 ? 2 : lbm::kBatchVariants;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  int best = 0;
+  float best_ms = 1e30f;
+  for (int v = 0; v < nv; ++v) {
+    b->variant = v;
+    lbm_status st = batch_layout(b);
+    if (st != LBM_OK) return st;
+    cudaEventRecord(e0, b->stream);
+    for (int s = 0; s < steps_per_variant; ++s) {
+      const int k = batch_launch(b, b->stream);
+      if (k < 0) return batch_fail(b, LBM_ECUDA, cudaGetErrorString(cudaGetLastError()));
+      batch_advance(b, k);
+    }
+    cudaEventRecord(e1, b->stream);
+    cudaEventSynchronize(e1);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = v;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  b->variant = best;
+  lbm_status st = batch_layout(b);
+  if (variant) *variant = best;
+  return st;
+}
+
+lbm_status lbm_batch_graph(lbm_batch* b, int enable) {
+  if (!b) return LBM_EINVAL;
+  b->use_graph = enable != 0;
+  return LBM_OK;
+}
+
+lbm_status lbm_batch_domain(lbm_batch* b, int32_t i, lbm_ctx** ctx) {
+  if (!b || !ctx || i < 0 || i >= (int32_t)b->ctx.size()) return LBM_EINVAL;
+  *ctx = b->ctx[i];
+  return LBM_OK;
+}
+
+void lbm_batch_destroy(lbm_batch* b) {
+  if (!b) return;
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  if (b->gstream) cudaStreamSynchronize(b->gstream);
+  if (b->gexec) cudaGraphExecDestroy(b->gexec);
+  if (b->ev_in) cudaEventDestroy(b->ev_in);
+  if (b->ev_out) cudaEventDestroy(b->ev_out);
+  if (b->gstream) cudaStreamDestroy(b->gstream);
+  if (b->d_doms) cudaFree(b->d_doms);
+  if (b->d_maps) cudaFree(b->d_maps);
+  for (lbm_ctx* c : b->ctx) {
+    c->batch_owned = false;
+    lbm_destroy(c);
+  }
+  delete b;
 }
 
 }  // extern "C"

@@ -67,6 +67,33 @@ struct Dev {
   double* stage;     // nx*ny doubles for exports/imports
 };
 
+// One domain of a batch, as the batched kernels see it.  Tiles of every pass are numbered
+// consecutively over the domains; *_first is this domain's first tile of that pass.
+struct BatchDomain {
+  Geo g;
+  Phys ph;
+  Dev d;
+  long long warmup;
+  int energy;
+  int psi_first, psi_ntx;                 // psi pass: 32 x 8 tiles
+  int coll_first, coll_ntx;               // collision pass: 32 x CTY tiles
+  int en_first, en_ntx, en_nblocks;       // energy pass: 32 x ETY tiles
+};
+
+// Tile-height variants of the batched step the autotuner chooses from: (CTY, ETY).
+constexpr int kBatchVariants = 4;
+inline void batch_variant(int v, bool f64, int& cty, int& ety) {
+  cty = (v & 1) ? 16 : 8;
+  ety = f64 ? 8 : ((v & 2) ? 8 : 16);
+}
+
+// Batched step over all domains (one launch per pass).  maps: block -> domain index for
+// the psi, collision and energy passes.  Returns the number of launches or -1.
+int batch_step_f32(int variant, const BatchDomain* doms, const int* map_psi, int nb_psi, const int* map_coll,
+                   int nb_coll, const int* map_en, int nb_en, int cur, int tcur, long long step, cudaStream_t s);
+int batch_step_f64(int variant, const BatchDomain* doms, const int* map_psi, int nb_psi, const int* map_coll,
+                   int nb_coll, const int* map_en, int nb_en, int cur, int tcur, long long step, cudaStream_t s);
+
 // Kernel identifiers for per-launch timing.
 enum KernelId { kKRhoPsi = 0, kKCollide, kKEnergy, kKExport, kKImport, kNumKernels };
 

@@ -521,32 +521,42 @@ __device__ __forceinline__ void collide(const C f[9], C rho, C Fx, C Fy, C Fmx, 
 // ---------------------------------------------------------------- k_rho_psi, k_collide
 constexpr int kCollTX = 32, kCollTY = 8;
 
-// psi(rho, T) at every node (rho from the pulled populations, rho_s in the solid).
+// psi(rho, T) at every node of tile (bx, by) of 32 x 8 nodes (rho from the pulled
+// populations, rho_s in the solid).
+template <typename C, typename S, int PSI>
+__device__ __forceinline__ void rho_psi_tile(const Geo& g, const Phys& ph, const S* __restrict__ f,
+                                             const C* __restrict__ T, const uint8_t* __restrict__ mask,
+                                             const C* __restrict__ side_in, C* __restrict__ psi_o, int* status, int bx,
+                                             int by) {
+  const int x = bx * kCollTX + threadIdx.x, y = by * 8 + threadIdx.y;
+  if (x >= g.nx || y >= g.ny) return;
+  psi_o[y * g.pitch + x] = psi_node<C, S, PSI>(g, ph, f, T, mask, side_in, x, y, status);
+}
 template <typename C, typename S, int PSI>
 __global__ void __launch_bounds__(256) k_rho_psi(Geo g, Phys ph, const S* __restrict__ f, const C* __restrict__ T,
                                                 const uint8_t* __restrict__ mask, const C* __restrict__ side_in,
                                                 C* __restrict__ psi_o, int* status) {
-  const int x = blockIdx.x * kCollTX + threadIdx.x, y = blockIdx.y * kCollTY + threadIdx.y;
-  if (x >= g.nx || y >= g.ny) return;
-  psi_o[y * g.pitch + x] = psi_node<C, S, PSI>(g, ph, f, T, mask, side_in, x, y, status);
+  rho_psi_tile<C, S, PSI>(g, ph, f, T, mask, side_in, psi_o, status, blockIdx.x, blockIdx.y);
 }
 
-// Pull, interaction force from a psi tile with a 2-node halo, gravity, CM collision;
-// writes f* (other buffer), rho, u and the outlet's streamed values.
-template <typename C, typename S>
-__global__ void __launch_bounds__(kCollTX* kCollTY)
-    k_collide(Geo g, Phys ph, const S* __restrict__ f, S* __restrict__ fn, const C* __restrict__ psi,
-              const uint8_t* __restrict__ mask, const C* __restrict__ side_in, C* __restrict__ side_out,
-              C* __restrict__ rho_o, C* __restrict__ ux_o, C* __restrict__ uy_o, int forcing, int* status) {
-  constexpr int HX = kCollTX + 4, HY = kCollTY + 4;
+// Pull, interaction force from a psi tile with a 2-node halo, gravity, CM collision, for
+// tile (bx, by) of 32 x CTY nodes; writes f* (other buffer), rho, u and the outlet's
+// streamed values.
+template <typename C, typename S, int CTY>
+__device__ __forceinline__ void collide_tile(const Geo& g, const Phys& ph, const S* __restrict__ f,
+                                             S* __restrict__ fn, const C* __restrict__ psi,
+                                             const uint8_t* __restrict__ mask, const C* __restrict__ side_in,
+                                             C* __restrict__ side_out, C* __restrict__ rho_o, C* __restrict__ ux_o,
+                                             C* __restrict__ uy_o, int forcing, int* status, int bx, int by) {
+  constexpr int HX = kCollTX + 4, HY = CTY + 4;
   __shared__ C s_psi[HY * HX];
   const PhysC<C>& k = pc<C>(ph);
   const int tx = threadIdx.x, ty = threadIdx.y;
-  const int x0 = blockIdx.x * kCollTX, y0 = blockIdx.y * kCollTY;
+  const int x0 = bx * kCollTX, y0 = by * CTY;
   const int x = x0 + tx, y = y0 + ty;
   const bool multiphase = k.G != C(0);
   if (multiphase && forcing) {
-    for (int p = ty * kCollTX + tx; p < HX * HY; p += kCollTX * kCollTY) {
+    for (int p = ty * kCollTX + tx; p < HX * HY; p += kCollTX * CTY) {
       const int hx = p % HX, hy = p / HX;
       s_psi[p] = psi[map_y(g, y0 + hy - 2) * g.pitch + map_x(g, x0 + hx - 2)];
     }
@@ -589,6 +599,14 @@ __global__ void __launch_bounds__(kCollTX* kCollTY)
   ux_o[id] = ux;
   uy_o[id] = uy;
   if (!(rho > C(0)) || !(ux == ux) || !(uy == uy)) atomicOr(status, 1);
+}
+template <typename C, typename S>
+__global__ void __launch_bounds__(kCollTX* kCollTY)
+    k_collide(Geo g, Phys ph, const S* __restrict__ f, S* __restrict__ fn, const C* __restrict__ psi,
+              const uint8_t* __restrict__ mask, const C* __restrict__ side_in, C* __restrict__ side_out,
+              C* __restrict__ rho_o, C* __restrict__ ux_o, C* __restrict__ uy_o, int forcing, int* status) {
+  collide_tile<C, S, kCollTY>(g, ph, f, fn, psi, mask, side_in, side_out, rho_o, ux_o, uy_o, forcing, status,
+                              blockIdx.x, blockIdx.y);
 }
 
 // ---------------------------------------------------------------- k_energy
@@ -722,19 +740,22 @@ __device__ __forceinline__ void energy_rhs_pair(const Phys& ph, const C* t, int 
   }
 }
 
-template <typename C>
+template <typename C, int TY_ = (sizeof(C) == 8 ? 8 : kEnergyTY)>
 struct EnergyTile {
   static constexpr int TX = kEnergyTX;
-  static constexpr int TY = sizeof(C) == 8 ? 8 : kEnergyTY;  // FP64 keeps shared memory under 48 KB
-  static constexpr int NT = TX * TY / 2;                     // two nodes per thread
+  static constexpr int TY = TY_;          // FP64 defaults to 8 rows to keep shared memory under 48 KB
+  static constexpr int NT = TX * TY / 2;  // two nodes per thread
 };
 
-template <typename C>
-__global__ void __launch_bounds__(EnergyTile<C>::NT)
-    k_energy(Geo g, Phys ph, const C* __restrict__ Tin, C* __restrict__ Tout, const C* __restrict__ rho,
-             const C* __restrict__ ux, const C* __restrict__ uy, const uint8_t* __restrict__ mask,
-             double* partial, unsigned* counter, double* hf, int nb, int do_hf) {
-  constexpr int TX = EnergyTile<C>::TX, TY = EnergyTile<C>::TY, NT = EnergyTile<C>::NT;
+// Both Heun stages on tile (bx, by); bid, nblocks: this tile's index among the domain's
+// nblocks tiles (for the heat-flux partials and the last-block reduction).
+template <typename C, int ETY>
+__device__ __forceinline__ void energy_tile(const Geo& g, const Phys& ph, const C* __restrict__ Tin,
+                                            C* __restrict__ Tout, const C* __restrict__ rho, const C* __restrict__ ux,
+                                            const C* __restrict__ uy, const uint8_t* __restrict__ mask,
+                                            double* partial, unsigned* counter, double* hf, int nb, int do_hf, int bx,
+                                            int by, int bid, int nblocks) {
+  constexpr int TX = EnergyTile<C, ETY>::TX, TY = EnergyTile<C, ETY>::TY, NT = EnergyTile<C, ETY>::NT;
   constexpr int H = 4, AX = TX + 2 * H, AY = TY + 2 * H;  // inputs: tile + 4
   constexpr int BX = TX + 4, BY = TY + 4;                 // stage 1: tile + 2
   __shared__ __align__(16) C sT[AY * AX];
@@ -748,7 +769,7 @@ __global__ void __launch_bounds__(EnergyTile<C>::NT)
   __shared__ double red[NT / 32];
   __shared__ int done_last;
   const int tid = threadIdx.x;
-  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+  const int x0 = bx * TX, y0 = by * TY;
   const bool interior = x0 >= H && y0 >= H && x0 + TX + H <= g.nx && y0 + TY + H <= g.ny;
   for (int p = tid; p < AX * AY; p += NT) {
     const int gx = x0 + p % AX - H, gy = y0 + p / AX - H;
@@ -831,9 +852,8 @@ __global__ void __launch_bounds__(EnergyTile<C>::NT)
     const int has = __syncthreads_or(mine);
     double s = 0.0;
     if (has) s = block_sum<NT>(q, red);
-    const int nblocks = gridDim.x * gridDim.y;
     if (tid == 0) {
-      partial[blockIdx.y * gridDim.x + blockIdx.x] = s;
+      partial[bid] = s;
       __threadfence();
       done_last = atomicInc(counter, nblocks - 1) == (unsigned)(nblocks - 1);
     }
@@ -852,6 +872,69 @@ __global__ void __launch_bounds__(EnergyTile<C>::NT)
       }
     }
   }
+}
+template <typename C>
+__global__ void __launch_bounds__(EnergyTile<C>::NT)
+    k_energy(Geo g, Phys ph, const C* __restrict__ Tin, C* __restrict__ Tout, const C* __restrict__ rho,
+             const C* __restrict__ ux, const C* __restrict__ uy, const uint8_t* __restrict__ mask,
+             double* partial, unsigned* counter, double* hf, int nb, int do_hf) {
+  energy_tile<C, EnergyTile<C>::TY>(g, ph, Tin, Tout, rho, ux, uy, mask, partial, counter, hf, nb, do_hf, blockIdx.x,
+                                    blockIdx.y, blockIdx.y * gridDim.x + blockIdx.x, gridDim.x * gridDim.y);
+}
+
+// ---------------------------------------------------------------- batched passes
+// Every block of a batched pass finds its domain through the block -> domain map and its
+// tile from its index within that domain; the tile bodies are the single-domain ones.
+template <typename C, typename S, int PSI>
+__global__ void __launch_bounds__(256) kb_rho_psi(const BatchDomain* __restrict__ doms, const int* __restrict__ map,
+                                                 int cur, int tcur) {
+  const BatchDomain& D = doms[map[blockIdx.x]];
+  if (pc<C>(D.ph).G == C(0)) return;
+  const int local = blockIdx.x - D.psi_first;
+  rho_psi_tile<C, S, PSI>(D.g, D.ph, static_cast<const S*>(D.d.f[cur]), static_cast<const C*>(D.d.T[tcur]),
+                          D.d.mask, static_cast<const C*>(D.d.side[cur]), static_cast<C*>(D.d.psi), D.d.status,
+                          local % D.psi_ntx, local / D.psi_ntx);
+}
+template <typename C, typename S, int CTY>
+__global__ void __launch_bounds__(kCollTX* CTY) kb_collide(const BatchDomain* __restrict__ doms,
+                                                          const int* __restrict__ map, int cur, long long step) {
+  const BatchDomain& D = doms[map[blockIdx.x]];
+  const int local = blockIdx.x - D.coll_first;
+  collide_tile<C, S, CTY>(D.g, D.ph, static_cast<const S*>(D.d.f[cur]), static_cast<S*>(D.d.f[cur ^ 1]),
+                          static_cast<const C*>(D.d.psi), D.d.mask, static_cast<const C*>(D.d.side[cur]),
+                          static_cast<C*>(D.d.side[cur ^ 1]), static_cast<C*>(D.d.rho), static_cast<C*>(D.d.ux),
+                          static_cast<C*>(D.d.uy), step >= D.warmup, D.d.status, local % D.coll_ntx,
+                          local / D.coll_ntx);
+}
+template <typename C, int ETY>
+__global__ void __launch_bounds__(EnergyTile<C, ETY>::NT) kb_energy(const BatchDomain* __restrict__ doms,
+                                                                   const int* __restrict__ map, int tcur,
+                                                                   long long step) {
+  const BatchDomain& D = doms[map[blockIdx.x]];
+  const int local = blockIdx.x - D.en_first, bx = local % D.en_ntx, by = local / D.en_ntx;
+  const C* Tin = static_cast<const C*>(D.d.T[tcur]);
+  C* Tout = static_cast<C*>(D.d.T[tcur ^ 1]);
+  if (!D.energy || step < D.warmup) {
+    // no energy update for this domain this step: carry T over so all domains flip together
+    constexpr int TX = EnergyTile<C, ETY>::TX, TY = EnergyTile<C, ETY>::TY;
+    for (int p = threadIdx.x; p < TX * TY; p += EnergyTile<C, ETY>::NT) {
+      const int x = bx * TX + p % TX, y = by * TY + p / TX;
+      if (x < D.g.nx && y < D.g.ny) Tout[y * D.g.pitch + x] = Tin[y * D.g.pitch + x];
+    }
+    return;
+  }
+  energy_tile<C, ETY>(D.g, D.ph, Tin, Tout, static_cast<const C*>(D.d.rho), static_cast<const C*>(D.d.ux),
+                      static_cast<const C*>(D.d.uy), D.d.mask, D.d.partial, D.d.counter, D.d.hf, D.d.nb, D.d.nb > 0,
+                      bx, by, local, D.en_nblocks);
+}
+
+template <typename C, typename S, int PSI, int CTY, int ETY>
+int batch_step_impl(const BatchDomain* doms, const int* map_psi, int nb_psi, const int* map_coll, int nb_coll,
+                    const int* map_en, int nb_en, int cur, int tcur, long long step, cudaStream_t s) {
+  kb_rho_psi<C, S, PSI><<<nb_psi, dim3(kCollTX, 8), 0, s>>>(doms, map_psi, cur, tcur);
+  kb_collide<C, S, CTY><<<nb_coll, dim3(kCollTX, CTY), 0, s>>>(doms, map_coll, cur, step);
+  kb_energy<C, ETY><<<nb_en, EnergyTile<C, ETY>::NT, 0, s>>>(doms, map_en, tcur, step);
+  return cudaPeekAtLastError() == cudaSuccess ? 3 : -1;
 }
 
 // ---------------------------------------------------------------- init / export / import

@@ -17,6 +17,52 @@ _PARAM_DEFAULTS = dict(a=2.0 / 49.0, b=2.0 / 21.0, R=1.0, acentric=0.344, G=-1.0
                        outlet_U=-1.0, warmup=0, energy=1, seed=0, noise_amp=1e-4, psi_mode=0)
 
 
+def _structs(nx, ny, D, xc, yc, periodic_x, superheat_Tc, rho_s, f64, storage, params):
+    kw = dict(_PARAM_DEFAULTS)
+    unknown = set(params) - set(kw)
+    if unknown:
+        raise TypeError(f"unknown parameters {sorted(unknown)}")
+    kw.update(params)
+    dom = N.Domain(int(nx), int(ny), int(periodic_x), 0)
+    cyl = N.Cylinder(float(xc), float(yc), float(D), float(superheat_Tc), float(rho_s))
+    prm = N.Params(a=kw["a"], b=kw["b"], R=kw["R"], acentric=kw["acentric"], G=kw["G"], sigma=kw["sigma"],
+                   Tr_sat=kw["Tr_sat"], Re=kw["Re"], u_in=kw["u_in"], nu_l=kw["nu_l"],
+                   nu_ratio=kw["nu_ratio"], Pr_l=kw["Pr_l"], Pr_v=kw["Pr_v"], c_v=kw["c_v"], g=kw["g"],
+                   outlet_U=kw["outlet_U"], warmup_steps=int(kw["warmup"]), energy=int(kw["energy"]),
+                   storage=N.LBM_STORE_F64 if f64 else N.STORAGE[storage], compute_f64=1 if f64 else 0,
+                   psi_mode=int(kw["psi_mode"]), seed=int(kw["seed"]), noise_amp=kw["noise_amp"])
+    return dom, cyl, prm, kw
+
+
+def _torch_allocator(torch, device, enabled):
+    """Device memory for the library from PyTorch's caching allocator (or None: cudaMalloc)."""
+    blocks = {}
+    if not enabled:
+        return blocks, None, None, None
+    dev = torch.device("cuda", device)
+
+    def _alloc(nbytes, user):
+        t = torch.empty(int(nbytes), dtype=torch.uint8, device=dev)
+        blocks[t.data_ptr()] = t
+        return t.data_ptr()
+
+    def _free(ptr, user):
+        blocks.pop(ptr, None)
+
+    cb = (N.ALLOC_FN(_alloc), N.FREE_FN(_free))
+    allocator = N.Allocator(cb[0], cb[1], None)
+    return blocks, cb, allocator, C.byref(allocator)
+
+
+def _case_kwargs(case):
+    names = [k for k in _PARAM_DEFAULTS if hasattr(case, k)]
+    params = {k: getattr(case, k) for k in names}
+    if hasattr(case, "U_out"):
+        params["outlet_U"] = case.U_out
+    return dict(nx=case.nx, ny=case.ny, D=case.D, xc=case.xc, yc=case.yc, periodic_x=case.periodic_x,
+                superheat_Tc=case.superheat_Tc, rho_s=getattr(case, "rho_s", 0.0), params=params)
+
+
 def _dense(a, n):
     if a is None:
         return None
@@ -46,20 +92,7 @@ class Sim:
         self._torch = torch
         L = N.lib()
         self.nx, self.ny, self.D = int(nx), int(ny), float(D)
-        kw = dict(_PARAM_DEFAULTS)
-        unknown = set(params) - set(kw)
-        if unknown:
-            raise TypeError(f"unknown parameters {sorted(unknown)}")
-        kw.update(params)
-        self.params = kw
-        dom = N.Domain(self.nx, self.ny, int(periodic_x), 0)
-        cyl = N.Cylinder(float(xc), float(yc), float(D), float(superheat_Tc), float(rho_s))
-        prm = N.Params(a=kw["a"], b=kw["b"], R=kw["R"], acentric=kw["acentric"], G=kw["G"], sigma=kw["sigma"],
-                       Tr_sat=kw["Tr_sat"], Re=kw["Re"], u_in=kw["u_in"], nu_l=kw["nu_l"],
-                       nu_ratio=kw["nu_ratio"], Pr_l=kw["Pr_l"], Pr_v=kw["Pr_v"], c_v=kw["c_v"], g=kw["g"],
-                       outlet_U=kw["outlet_U"], warmup_steps=int(kw["warmup"]), energy=int(kw["energy"]),
-                       storage=N.LBM_STORE_F64 if f64 else N.STORAGE[storage], compute_f64=1 if f64 else 0,
-                       psi_mode=int(kw["psi_mode"]), seed=int(kw["seed"]), noise_amp=kw["noise_amp"])
+        dom, cyl, prm, self.params = _structs(nx, ny, D, xc, yc, periodic_x, superheat_Tc, rho_s, f64, storage, params)
         n = self.nx * self.ny
         init = init or {}
         keep = {k: _dense(init.get(k), n) for k in ("rho", "drho", "ux", "uy", "T")}
@@ -67,22 +100,8 @@ class Sim:
                        for k in ("rho", "drho", "ux", "uy", "T")])
         self.device = torch.cuda.current_device()
         self.stream = stream if stream is not None else torch.cuda.current_stream()
-        self._blocks = {}
-        alloc_p = None
-        if torch_alloc:
-            dev = torch.device("cuda", self.device)
-
-            def _alloc(nbytes, user):
-                t = torch.empty(int(nbytes), dtype=torch.uint8, device=dev)
-                self._blocks[t.data_ptr()] = t
-                return t.data_ptr()
-
-            def _free(ptr, user):
-                self._blocks.pop(ptr, None)
-
-            self._alloc_cb = (N.ALLOC_FN(_alloc), N.FREE_FN(_free))
-            self._allocator = N.Allocator(self._alloc_cb[0], self._alloc_cb[1], None)
-            alloc_p = C.byref(self._allocator)
+        self._owner = None
+        self._blocks, self._alloc_cb, self._allocator, alloc_p = _torch_allocator(torch, self.device, torch_alloc)
         h = C.c_void_p()
         N.check(L.lbm_create(C.byref(dom), C.byref(cyl), C.byref(prm), C.byref(ini), alloc_p,
                              C.c_void_p(self.stream.cuda_stream), C.byref(h)))
@@ -91,16 +110,30 @@ class Sim:
     @classmethod
     def from_case(cls, case, f64=False, **kw):
         """Build from an object with the attributes of a workload description (nx, ny, D, ...)."""
-        names = [k for k in _PARAM_DEFAULTS if hasattr(case, k) and k not in kw]
-        params = {k: getattr(case, k) for k in names}
-        if hasattr(case, "U_out") and "outlet_U" not in kw:
-            params["outlet_U"] = case.U_out
-        rho_s = getattr(case, "rho_s", 0.0)
-        return cls(case.nx, case.ny, D=case.D, xc=case.xc, yc=case.yc, periodic_x=case.periodic_x,
-                   superheat_Tc=case.superheat_Tc, rho_s=rho_s, f64=f64, **params, **kw)
+        k = _case_kwargs(case)
+        params = {p: v for p, v in k.pop("params").items() if p not in kw}
+        return cls(k["nx"], k["ny"], D=k["D"], xc=k["xc"], yc=k["yc"], periodic_x=k["periodic_x"],
+                   superheat_Tc=k["superheat_Tc"], rho_s=k["rho_s"], f64=f64, **params, **kw)
 
     # ------------------------------------------------------------------ lifecycle
+    @classmethod
+    def _borrowed(cls, handle, nx, ny, D, owner):
+        """A view of a domain owned by a Batch (no ownership of the handle)."""
+        import torch
+
+        self = cls.__new__(cls)
+        self._torch = torch
+        self.h = handle
+        self.nx, self.ny, self.D = nx, ny, D
+        self._owner = owner
+        self._blocks = {}
+        self.device = torch.cuda.current_device()
+        return self
+
     def close(self):
+        if getattr(self, "_owner", None) is not None:
+            self.h = None
+            return
         if getattr(self, "h", None) is not None and self.h.value:
             N.lib().lbm_destroy(self.h)
             self.h = None
@@ -188,3 +221,67 @@ class Sim:
         nk = C.c_int32()
         self._chk(N.lib().lbm_profile_read(self.h, names, launches, ms, k, C.byref(nk)))
         return {names[i].decode(): (launches[i], ms[i]) for i in range(nk.value) if names[i]}
+
+
+class Batch:
+    """Independent domains stepped together (lbm_batch_*): one launch per pass over all
+    domains' tiles, pairs of steps replayed from a CUDA graph once every domain is past its
+    warm-up.  domain(i) gives a Sim view of domain i for fields and heat flux."""
+
+    def __init__(self, cases, f64=False, stream=None, torch_alloc=True):
+        import torch
+
+        self._torch = torch
+        L = N.lib()
+        kws = [_case_kwargs(c) for c in cases]
+        n = len(kws)
+        doms, cyls, prms = (N.Domain * n)(), (N.Cylinder * n)(), (N.Params * n)()
+        for i, k in enumerate(kws):
+            doms[i], cyls[i], prms[i], _ = _structs(k["nx"], k["ny"], k["D"], k["xc"], k["yc"], k["periodic_x"],
+                                                    k["superheat_Tc"], k["rho_s"], f64, "f32", k["params"])
+        self.shapes = [(k["nx"], k["ny"], k["D"]) for k in kws]
+        self.device = torch.cuda.current_device()
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self._blocks, self._alloc_cb, self._allocator, alloc_p = _torch_allocator(torch, self.device, torch_alloc)
+        h = C.c_void_p()
+        N.check(L.lbm_batch_create(n, doms, cyls, prms, alloc_p, C.c_void_p(self.stream.cuda_stream), C.byref(h)))
+        self.h = h
+
+    def __len__(self):
+        return len(self.shapes)
+
+    def step(self, n: int = 1):
+        N.check(N.lib().lbm_batch_step(self.h, int(n)))
+        return self
+
+    def tune(self, steps_per_variant: int = 2) -> int:
+        v = C.c_int32()
+        N.check(N.lib().lbm_batch_tune(self.h, int(steps_per_variant), C.byref(v)))
+        return v.value
+
+    def graph(self, enable: bool = True):
+        N.check(N.lib().lbm_batch_graph(self.h, 1 if enable else 0))
+
+    def domain(self, i: int) -> Sim:
+        hd = C.c_void_p()
+        N.check(N.lib().lbm_batch_domain(self.h, int(i), C.byref(hd)))
+        nx, ny, D = self.shapes[i]
+        return Sim._borrowed(hd, nx, ny, D, self)
+
+    def sync(self):
+        self._torch.cuda.current_stream().synchronize()
+        for i in range(len(self)):
+            self.domain(i).sync()
+        return self
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            N.lib().lbm_batch_destroy(self.h)
+            self.h = None
+            self._blocks.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,103 @@
+"""Batched stepping of independent domains (lbm_batch_*) against individual contexts.
+
+A batch changes how the per-domain step is scheduled (one launch per pass over all domains'
+tiles, CUDA-graph replay), not what it computes, so every domain must give exactly the
+fields of its own context; the FP64 batch is also held to the oracle at 1e-12.
+"""
+import numpy as np
+import pytest
+
+import synthetic_inputs as si
+from oracle import Oracle
+
+pytestmark = pytest.mark.gpu
+
+CASES = [
+    si.SMALL.replace(seed=1),
+    si.Case(nx=96, ny=48, D=12.0, xc=24.3, yc=23.6, Re=40.0, superheat_Tc=0.08, warmup=7, seed=2),
+    si.Case(nx=70, ny=27, D=9.4, xc=20.3, yc=11.7, Re=40.0, energy=0, seed=3),
+]
+FIELDS = ("rho", "ux", "uy", "T", "psi")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+
+    from oracle import build as ob
+    from paper_1912_02018_gb300 import build
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    build()
+    ob.build()
+    torch.cuda.set_device(0)
+
+
+def singles(cases, steps, f64=False):
+    from paper_1912_02018_gb300 import Sim
+
+    return [Sim.from_case(c, f64=f64).step(steps) for c in cases]
+
+
+def assert_same(batch, sims, hf_tol=0.0):
+    for i, s in enumerate(sims):
+        a, b = batch.domain(i).fields(FIELDS), s.fields(FIELDS)
+        for k in FIELDS:
+            assert np.array_equal(a[k], b[k]), (i, k)
+        ha, hb = batch.domain(i).heat_flux(), s.heat_flux()
+        assert ha["count"] == hb["count"]
+        assert abs(ha["q_mean"] - hb["q_mean"]) <= hf_tol * abs(hb["q_mean"]), (i, ha, hb)
+
+
+def test_batch_with_graph_equals_individual_contexts():
+    from paper_1912_02018_gb300 import Batch
+
+    b = Batch(CASES).step(25)
+    assert_same(b, singles(CASES, 25))
+
+
+def test_batch_without_graph_equals_individual_contexts():
+    from paper_1912_02018_gb300 import Batch
+
+    b = Batch(CASES)
+    b.graph(False)
+    b.step(9)
+    b.step(4)
+    assert_same(b, singles(CASES, 13))
+
+
+def test_tuned_batch_keeps_results():
+    from paper_1912_02018_gb300 import Batch
+
+    b = Batch(CASES)
+    v = b.tune(2)  # 4 variants x 2 real steps
+    assert 0 <= v < 4
+    b.step(12)
+    # another tile height changes only the order of the heat-flux partial sums
+    assert_same(b, singles(CASES, 20), hf_tol=1e-12)
+
+
+def test_fp64_batch_matches_oracle():
+    from paper_1912_02018_gb300 import Batch
+
+    cases = CASES[:2]
+    b = Batch(cases, f64=True).step(40)
+    for i, c in enumerate(cases):
+        ref = Oracle(c, drho=c.drho()).step(40)
+        got = b.domain(i).fields(FIELDS)
+        fluid = ref.field("solid") == 0
+        for k in FIELDS:
+            r = ref.field(k)[fluid]
+            scale = np.abs(r).max() if k not in ("ux", "uy") else np.hypot(ref.field("ux"), ref.field("uy"))[fluid].max()
+            assert np.abs(got[k][fluid] - r).max() <= 1e-12 * scale, (i, k)
+
+
+def test_batch_domain_cannot_be_stepped_alone():
+    from paper_1912_02018_gb300 import Batch
+    from paper_1912_02018_gb300._native import LBM_ESTATE, LbmError
+
+    b = Batch(CASES[:1])
+    with pytest.raises(LbmError) as e:
+        b.domain(0).step(1)
+    assert e.value.status == LBM_ESTATE
