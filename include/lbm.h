@@ -77,6 +77,11 @@ typedef struct {
     double D;            /* diameter; D <= 0 means no cylinder */
     double superheat_Tc; /* wall superheat (T_w - T_sat) as a fraction of T_c, Sec. IV.A */
     double rho_solid;    /* density given to solid nodes for psi; 0 means rho_l */
+    const double *wall_dT; /* optional: n_wall knots of extra superheat (fractions of T_c), equally spaced
+                              in the angle from +x; a solid node at angle theta gets the periodic-linear
+                              interpolation; NULL or n_wall = 0: uniform wall (copied at creation) */
+    int32_t n_wall;
+    int32_t reserved;
 } lbm_cylinder;
 
 typedef struct {
@@ -105,7 +110,8 @@ typedef struct {
 
 /* Optional initial fields (host, [ny][nx]); any pointer may be NULL.
  * rho0 = (rho ? rho : rho_l) + (drho ? drho : SplitMix64(seed) noise of amplitude noise_amp),
- * u0 = (ux, uy) or (u_in, 0), T0 = T or T_sat; solid nodes get rho_solid, u = 0, T_w.
+ * u0 = (ux, uy) or (u_in, 0), T0 = T or T_sat; solid nodes get rho_solid, u = 0 and their wall
+ * temperature T_w(x), which they keep (the energy equation updates fluid nodes only).
  * Populations start at the fourth-order Hermite equilibrium of Eq. (equi). */
 typedef struct {
     const double *rho, *drho, *ux, *uy, *T;
@@ -189,7 +195,9 @@ lbm_status lbm_fields(lbm_ctx *ctx, uint32_t mask, void *dst, size_t bytes, int 
 lbm_status lbm_get_state(lbm_ctx *ctx, double *f, double *T, double *side, int64_t *steps);
 
 /* Restore (any subset of) a checkpoint written by lbm_get_state; NULL keeps that part.
- * steps < 0 keeps the step counter.  Host doubles are converted to the storage type. */
+ * steps < 0 keeps the step counter.  Host doubles are converted to the storage type.
+ * T at solid nodes is the wall temperature from then on: pass the values lbm_get_state
+ * returned there to keep the wall created with the context. */
 lbm_status lbm_set_state(lbm_ctx *ctx, const double *f, const double *T, const double *side, int64_t steps);
 
 /* Derived constants and counters. */

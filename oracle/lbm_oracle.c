@@ -33,7 +33,11 @@
  *      upwind convection, isotropic 24-neighbour gradient and Laplacian (Sec. II.C).
  * For n < warmup the force and steps 5-6 are skipped (Sec. IV.A).
  */
+#define _USE_MATH_DEFINES
 #include <math.h>
+#ifndef M_PI
+#define M_PI 3.14159265358979323846
+#endif
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -71,6 +75,8 @@ typedef struct {
     double rho_l, rho_v, rho_s; /* coexistence densities; virtual solid density */
     double nu_l, nu_v, alpha_l, alpha_v, c_v;
     double g, u_in, U_out;      /* gravity; inlet speed; convective-outlet speed */
+    int32_t n_wall, pad;        /* optional angular wall-superheat profile (knots, fractions of Tc) */
+    const double *wall_dT;
 } orc_params;
 
 typedef struct {
@@ -84,6 +90,7 @@ typedef struct {
     double *side;   /* [3][ny] last streamed values of f_2, f_6, f_8 at x = nx-1 */
     double *T, *T1, *L;
     double *rho, *ux, *uy, *psi, *lam;
+    double *Tw;     /* wall temperature of each solid node */
     int nb;
     int *bnode;
     double *bnx, *bny;
@@ -410,7 +417,7 @@ orc_t *orc_create(const orc_params *p, const double *rho0, const double *ux0, co
     o->fs = (double *)malloc(sizeof(double) * N * Q);
     o->fp = (double *)malloc(sizeof(double) * N * Q);
     o->side = (double *)malloc(sizeof(double) * 3 * ny);
-    double **fields[] = {&o->T, &o->T1, &o->L, &o->rho, &o->ux, &o->uy, &o->psi, &o->lam};
+    double **fields[] = {&o->T, &o->T1, &o->L, &o->rho, &o->ux, &o->uy, &o->psi, &o->lam, &o->Tw};
     for (unsigned k = 0; k < sizeof(fields) / sizeof(fields[0]); ++k)
         *fields[k] = (double *)calloc(N, sizeof(double));
     double M[Q * Q];
@@ -448,6 +455,27 @@ orc_t *orc_create(const orc_params *p, const double *rho0, const double *ux0, co
             }
         }
 
+    /* wall temperature: T_w = T_sat + superheat, plus an optional angular profile interpolated
+     * periodically-linearly between n_wall equally spaced knots (angle from the +x axis) */
+    for (int y = 0; y < ny; ++y)
+        for (int x = 0; x < nx; ++x) {
+            int id = y * nx + x;
+            if (!o->solid[id]) continue;
+            double tw = p->T_wall;
+            if (p->n_wall > 0 && p->wall_dT) {
+                double th = atan2(y - p->yc, x - p->xc);
+                double s = th / (2.0 * M_PI);
+                if (s < 0.0) s += 1.0;
+                double pos = s * p->n_wall;
+                double fl = floor(pos);
+                int k0 = ((int)fl) % p->n_wall, k1 = (k0 + 1) % p->n_wall;
+                double t = pos - fl;
+                double d = (1.0 - t) * p->wall_dT[k0] + t * p->wall_dT[k1];
+                tw = p->T_wall + d * p->Tc;
+            }
+            o->Tw[id] = tw;
+        }
+
     /* initial state (Sec. IV.A): f* = f^eq(rho0, u0) in the fluid */
     for (int id = 0; id < N; ++id) {
         double feq[Q];
@@ -459,7 +487,7 @@ orc_t *orc_create(const orc_params *p, const double *rho0, const double *ux0, co
         o->rho[id] = r;
         o->ux[id] = u;
         o->uy[id] = v;
-        o->T[id] = o->solid[id] ? p->T_wall : (T0 ? T0[id] : p->T_sat);
+        o->T[id] = o->solid[id] ? o->Tw[id] : (T0 ? T0[id] : p->T_sat);
     }
     if (!p->periodic_x)
         for (int y = 0; y < ny; ++y) {
@@ -476,7 +504,7 @@ void orc_destroy(orc_t *o)
     if (!o) return;
     free(o->solid); free(o->qlink); free(o->fs); free(o->fp); free(o->side);
     free(o->T); free(o->T1); free(o->L); free(o->rho); free(o->ux); free(o->uy);
-    free(o->psi); free(o->lam); free(o->bnode); free(o->bnx); free(o->bny);
+    free(o->psi); free(o->lam); free(o->Tw); free(o->bnode); free(o->bnx); free(o->bny);
     free(o);
 }
 
@@ -621,7 +649,7 @@ void orc_step(orc_t *o, int64_t nsteps)
             for (int y = 0; y < ny; ++y)
                 for (int x = 0; x < nx; ++x) {
                     int id = y * nx + x;
-                    if (o->solid[id]) o->T1[id] = p->T_wall;
+                    if (o->solid[id]) o->T1[id] = o->Tw[id];
                     else if (is_dirichlet_T(o, x, id)) o->T1[id] = p->T_sat;
                     else o->T1[id] = o->T[id] + energy_rhs(o, o->T, x, y);
                 }
@@ -633,7 +661,7 @@ void orc_step(orc_t *o, int64_t nsteps)
                 }
             for (int id = 0; id < N; ++id) {
                 int x = id % nx;
-                if (o->solid[id]) o->T[id] = p->T_wall;
+                if (o->solid[id]) o->T[id] = o->Tw[id];
                 else if (is_dirichlet_T(o, x, id)) o->T[id] = p->T_sat;
                 else o->T[id] = (o->T[id] + o->T1[id] + o->L[id]) * 0.5;
             }

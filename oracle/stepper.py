@@ -27,6 +27,7 @@ class OrcParams(C.Structure):
         ("nu_l", C.c_double), ("nu_v", C.c_double), ("alpha_l", C.c_double), ("alpha_v", C.c_double),
         ("c_v", C.c_double),
         ("g", C.c_double), ("u_in", C.c_double), ("U_out", C.c_double),
+        ("n_wall", C.c_int32), ("pad", C.c_int32), ("wall_dT", C.POINTER(C.c_double)),
     ]
 
 
@@ -141,6 +142,11 @@ def derive(case) -> tuple[OrcParams, Derived]:
         rho_s=case.rho_s if case.rho_s > 0 else rho_l,
         nu_l=nu_l, nu_v=nu_v, alpha_l=alpha_l, alpha_v=alpha_v, c_v=case.c_v,
         g=g, u_in=case.u_in, U_out=U_out)
+    knots = np.ascontiguousarray(getattr(case, "wall_dT", ()) or (), dtype=np.float64)
+    if knots.size:
+        p.n_wall = knots.size
+        p.wall_dT = knots.ctypes.data_as(C.POINTER(C.c_double))
+        p._keep = knots  # the knots must outlive the structure
     d = Derived(eos, Tc, T_sat, T_wall, rho_l, rho_v, nu_l, nu_v, alpha_l, alpha_v, g, U_out,
                 rho_v * case.c_v * alpha_v)
     return p, d

@@ -30,7 +30,8 @@ class Domain(C.Structure):
 
 class Cylinder(C.Structure):
     _fields_ = [("xc", C.c_double), ("yc", C.c_double), ("D", C.c_double), ("superheat_Tc", C.c_double),
-                ("rho_solid", C.c_double)]
+                ("rho_solid", C.c_double), ("wall_dT", C.POINTER(C.c_double)), ("n_wall", C.c_int32),
+                ("reserved", C.c_int32)]
 
 
 class Params(C.Structure):

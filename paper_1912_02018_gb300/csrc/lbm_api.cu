@@ -468,7 +468,7 @@ lbm_status lbm_create(const lbm_domain* domain, const lbm_cylinder* cyl, const l
   d.bn = dbv;
   d.hf = static_cast<double*>(dalloc(c, 4 * sizeof(double)));
   d.status = static_cast<int*>(dalloc(c, sizeof(int)));
-  d.stage = static_cast<double*>(dalloc(c, sizeof(double) * (size_t)g.nx * g.ny * 5));
+  d.stage = static_cast<double*>(dalloc(c, sizeof(double) * (size_t)g.nx * g.ny * 6));
   if (!d.f[0] || !d.f[1] || !d.T[0] || !d.T[1] || !d.psi || !d.rho || !d.ux || !d.uy || !d.side[0] ||
       !d.side[1] || !d.partial || !d.counter || !dmask || !dbn || !dbv || !d.hf || !d.status || !d.stage) {
     dfree_all(c);
@@ -491,20 +491,37 @@ lbm_status lbm_create(const lbm_domain* domain, const lbm_cylinder* cyl, const l
     chk(cudaMemcpyAsync(dbn, bnode.data(), sizeof(int) * bnode.size(), cudaMemcpyHostToDevice, c->stream));
     chk(cudaMemcpyAsync(dbv, bnv.data(), sizeof(double) * bnv.size(), cudaMemcpyHostToDevice, c->stream));
   }
-  // optional initial fields, staged through the export buffer (5 dense planes)
+  // optional initial fields, staged through the export buffer (6 dense planes); the sixth holds
+  // the wall temperature of the solid nodes when an angular profile is given
   const size_t M = (size_t)g.nx * g.ny;
-  const double* src[5] = {init ? init->rho : nullptr, init ? init->drho : nullptr, init ? init->ux : nullptr,
-                          init ? init->uy : nullptr, init ? init->T : nullptr};
-  const double* dsrc[5] = {};
-  for (int k = 0; k < 5; ++k)
+  std::vector<double> wallT;
+  if (has_cyl && cyl->n_wall > 0 && cyl->wall_dT) {
+    wallT.assign(M, ph.T_wall);
+    const double two_pi = 2.0 * std::acos(-1.0);
+    for (int y = 0; y < g.ny; ++y)
+      for (int x = 0; x < g.nx; ++x) {
+        if (!solid_at(x, y)) continue;
+        double s = std::atan2(y - g.yc, x - g.xc) / two_pi;
+        if (s < 0.0) s += 1.0;
+        const double pos = s * cyl->n_wall, fl = std::floor(pos), t = pos - fl;
+        const int k0 = ((int)fl) % cyl->n_wall, k1 = (k0 + 1) % cyl->n_wall;
+        const double dlt = (1.0 - t) * cyl->wall_dT[k0] + t * cyl->wall_dT[k1];
+        wallT[(size_t)y * g.nx + x] = ph.T_wall + dlt * eos.Tc;
+      }
+  }
+  const double* src[6] = {init ? init->rho : nullptr, init ? init->drho : nullptr, init ? init->ux : nullptr,
+                          init ? init->uy : nullptr, init ? init->T : nullptr,
+                          wallT.empty() ? nullptr : wallT.data()};
+  const double* dsrc[6] = {};
+  for (int k = 0; k < 6; ++k)
     if (src[k]) {
       chk(cudaMemcpyAsync(d.stage + k * M, src[k], M * sizeof(double), cudaMemcpyHostToDevice, c->stream));
       dsrc[k] = d.stage + k * M;
     }
-  const int ok = c->f64 ? lbm::init_f64(g, phys, d, dsrc[0], dsrc[1], dsrc[2], dsrc[3], dsrc[4], P.seed, P.noise_amp,
-                                        c->stream)
-                        : lbm::init_f32(g, phys, d, dsrc[0], dsrc[1], dsrc[2], dsrc[3], dsrc[4], P.seed, P.noise_amp,
-                                        P.storage, c->stream);
+  const int ok = c->f64 ? lbm::init_f64(g, phys, d, dsrc[0], dsrc[1], dsrc[2], dsrc[3], dsrc[4], dsrc[5], P.seed,
+                                        P.noise_amp, c->stream)
+                        : lbm::init_f32(g, phys, d, dsrc[0], dsrc[1], dsrc[2], dsrc[3], dsrc[4], dsrc[5], P.seed,
+                                        P.noise_amp, P.storage, c->stream);
   if (ok < 0) chk(cudaGetLastError());
   chk(cudaMemcpyAsync(d.f[1], d.f[0], 9 * N * ps, cudaMemcpyDeviceToDevice, c->stream));
   chk(cudaMemcpyAsync(d.T[1], d.T[0], N * es, cudaMemcpyDeviceToDevice, c->stream));

@@ -43,11 +43,11 @@ int import_f32(const Geo& g, const Phys& ph, const Dev& d, int cur, int tcur, in
   }
 }
 int init_f32(const Geo& g, const Phys& ph, const Dev& d, const double* rho0, const double* drho, const double* ux0,
-             const double* uy0, const double* T0, unsigned long long seed, double amp, int storage, cudaStream_t s) {
+             const double* uy0, const double* T0, const double* Tw, unsigned long long seed, double amp, int storage, cudaStream_t s) {
   switch (storage) {
-    case LBM_STORE_F64: return init_impl<float, double>(g, ph, d, rho0, drho, ux0, uy0, T0, seed, amp, s);
-    case LBM_STORE_F16S: return init_impl<float, __half>(g, ph, d, rho0, drho, ux0, uy0, T0, seed, amp, s);
-    default: return init_impl<float, float>(g, ph, d, rho0, drho, ux0, uy0, T0, seed, amp, s);
+    case LBM_STORE_F64: return init_impl<float, double>(g, ph, d, rho0, drho, ux0, uy0, T0, Tw, seed, amp, s);
+    case LBM_STORE_F16S: return init_impl<float, __half>(g, ph, d, rho0, drho, ux0, uy0, T0, Tw, seed, amp, s);
+    default: return init_impl<float, float>(g, ph, d, rho0, drho, ux0, uy0, T0, Tw, seed, amp, s);
   }
 }
 

@@ -18,8 +18,8 @@ int import_f64(const Geo& g, const Phys& ph, const Dev& d, int cur, int tcur, in
   return import_impl<double, double>(g, ph, d, cur, tcur, which, src, s);
 }
 int init_f64(const Geo& g, const Phys& ph, const Dev& d, const double* rho0, const double* drho, const double* ux0,
-             const double* uy0, const double* T0, unsigned long long seed, double amp, cudaStream_t s) {
-  return init_impl<double, double>(g, ph, d, rho0, drho, ux0, uy0, T0, seed, amp, s);
+             const double* uy0, const double* T0, const double* Tw, unsigned long long seed, double amp, cudaStream_t s) {
+  return init_impl<double, double>(g, ph, d, rho0, drho, ux0, uy0, T0, Tw, seed, amp, s);
 }
 
 int batch_step_f64(int variant, const BatchDomain* doms, const int* mp, int np, const int* mc, int nc,

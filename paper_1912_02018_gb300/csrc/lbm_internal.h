@@ -134,9 +134,12 @@ int import_f32(const Geo& g, const Phys& ph, const Dev& d, int cur, int tcur, in
                const double* src, cudaStream_t s);
 // Initial state: populations at the Hermite equilibrium of (rho0 + drho, ux0, uy0), T = T0;
 // array arguments are dense [ny][nx] device doubles or NULL (see lbm_init in lbm.h).
+// Tw: dense wall temperatures of the solid nodes (NULL: T_wall everywhere).
 int init_f64(const Geo& g, const Phys& ph, const Dev& d, const double* rho0, const double* drho, const double* ux0,
-             const double* uy0, const double* T0, unsigned long long seed, double amp, cudaStream_t s);
+             const double* uy0, const double* T0, const double* Tw, unsigned long long seed, double amp,
+             cudaStream_t s);
 int init_f32(const Geo& g, const Phys& ph, const Dev& d, const double* rho0, const double* drho, const double* ux0,
-             const double* uy0, const double* T0, unsigned long long seed, double amp, int storage, cudaStream_t s);
+             const double* uy0, const double* T0, const double* Tw, unsigned long long seed, double amp, int storage,
+             cudaStream_t s);
 
 }  // namespace lbm

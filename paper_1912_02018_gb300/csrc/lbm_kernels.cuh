@@ -801,7 +801,7 @@ __device__ __forceinline__ void energy_tile(const Geo& g, const Phys& ph, const 
     for (int k = 0; k < 2; ++k) {
       const int gx = x0 + bx + k - 2;
       C t1;
-      if (sM[a + k] & kSolid) t1 = pc<C>(ph).T_wall;
+      if (sM[a + k] & kSolid) t1 = sT[a + k];  // solid nodes keep their wall temperature
       else if (!g.periodic_x && gx == 0) t1 = pc<C>(ph).T_sat;
       else t1 = sT[a + k] + L[k];
       sT1[by * BX + bx + k] = t1;  // positions past a non-periodic edge are replaced below
@@ -829,7 +829,7 @@ __device__ __forceinline__ void energy_tile(const Geo& g, const Phys& ph, const 
     const int x = x0 + tx + k;
     if (x < g.nx && y < g.ny) {
       C out;
-      if (sM[a + k] & kSolid) out = pc<C>(ph).T_wall;
+      if (sM[a + k] & kSolid) out = sT[a + k];
       else if (!g.periodic_x && x == 0) out = pc<C>(ph).T_sat;
       else out = ((sT[a + k] + sT1[b + k]) + L[k]) * C(0.5);
       Tout[y * g.pitch + x] = out;
@@ -970,7 +970,8 @@ __device__ __forceinline__ double splitmix_pm1(unsigned long long seed, unsigned
 template <typename C, typename S>
 __global__ void __launch_bounds__(256) k_init(Geo g, Phys ph, const double* rho0, const double* drho,
                                              const double* ux0, const double* uy0, const double* T0,
-                                             unsigned long long seed, double noise_amp, S* f, C* T, C* rho_o,
+                                             const double* Tw, unsigned long long seed, double noise_amp, S* f,
+                                             C* T, C* rho_o,
                                              C* ux_o, C* uy_o, C* side, const uint8_t* __restrict__ mask) {
   const int x = blockIdx.x * 32 + threadIdx.x;
   const int y = blockIdx.y * 8 + threadIdx.y;
@@ -985,7 +986,7 @@ __global__ void __launch_bounds__(256) k_init(Geo g, Phys ph, const double* rho0
     r = ph.d.rho_s;
     u = 0.0;
     v = 0.0;
-    t = ph.d.T_wall;
+    t = Tw ? Tw[k] : ph.d.T_wall;
   }
   double fe[9];
   feq_hermite(r, u, v, fe);
@@ -1130,10 +1131,11 @@ int import_impl(const Geo& g, const Phys& ph, const Dev& d, int cur, int tcur, i
 
 template <typename C, typename S>
 int init_impl(const Geo& g, const Phys& ph, const Dev& d, const double* rho0, const double* drho, const double* ux0,
-              const double* uy0, const double* T0, unsigned long long seed, double amp, cudaStream_t s) {
+              const double* uy0, const double* T0, const double* Tw, unsigned long long seed, double amp,
+              cudaStream_t s) {
   using namespace kern;
   const dim3 blk(32, 8), grd((g.nx + 31) / 32, (g.ny + 7) / 8);
-  k_init<C, S><<<grd, blk, 0, s>>>(g, ph, rho0, drho, ux0, uy0, T0, seed, amp, static_cast<S*>(d.f[0]),
+  k_init<C, S><<<grd, blk, 0, s>>>(g, ph, rho0, drho, ux0, uy0, T0, Tw, seed, amp, static_cast<S*>(d.f[0]),
                                    static_cast<C*>(d.T[0]), static_cast<C*>(d.rho), static_cast<C*>(d.ux),
                                    static_cast<C*>(d.uy), static_cast<C*>(d.side[0]), d.mask);
   return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;

@@ -14,7 +14,7 @@ from . import _native as N
 
 _PARAM_DEFAULTS = dict(a=2.0 / 49.0, b=2.0 / 21.0, R=1.0, acentric=0.344, G=-1.0, sigma=0.38, Tr_sat=0.86,
                        Re=30.0, u_in=0.05, nu_l=0.0, nu_ratio=1.0, Pr_l=0.862, Pr_v=1.5, c_v=11.0, g=-1.0,
-                       outlet_U=-1.0, warmup=0, energy=1, seed=0, noise_amp=1e-4, psi_mode=0)
+                       outlet_U=-1.0, warmup=0, energy=1, seed=0, noise_amp=1e-4, psi_mode=0, wall_dT=())
 
 
 def _structs(nx, ny, D, xc, yc, periodic_x, superheat_Tc, rho_s, f64, storage, params):
@@ -25,6 +25,11 @@ def _structs(nx, ny, D, xc, yc, periodic_x, superheat_Tc, rho_s, f64, storage, p
     kw.update(params)
     dom = N.Domain(int(nx), int(ny), int(periodic_x), 0)
     cyl = N.Cylinder(float(xc), float(yc), float(D), float(superheat_Tc), float(rho_s))
+    knots = np.ascontiguousarray(kw.pop("wall_dT", ()) or (), dtype=np.float64)
+    if knots.size:
+        cyl.wall_dT = knots.ctypes.data_as(C.POINTER(C.c_double))
+        cyl.n_wall = knots.size
+        cyl._keep = knots  # copied by the library at creation
     prm = N.Params(a=kw["a"], b=kw["b"], R=kw["R"], acentric=kw["acentric"], G=kw["G"], sigma=kw["sigma"],
                    Tr_sat=kw["Tr_sat"], Re=kw["Re"], u_in=kw["u_in"], nu_l=kw["nu_l"],
                    nu_ratio=kw["nu_ratio"], Pr_l=kw["Pr_l"], Pr_v=kw["Pr_v"], c_v=kw["c_v"], g=kw["g"],

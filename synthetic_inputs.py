@@ -46,7 +46,8 @@ def density_perturbation(nx: int, ny: int, seed: int, amp: float) -> np.ndarray:
 class Case:
     """Raw description of one boiling-on-a-cylinder run (lattice units).
 
-    superheat_Tc: wall superheat as a fraction of the critical temperature.
+    superheat_Tc: wall superheat as a fraction of the critical temperature; wall_dT adds a
+    periodic-linear angular profile over len(wall_dT) equally spaced knots (angle from +x).
     g < 0 means "derive from u_in/sqrt(g D) = 4"; U_out < 0 means "use u_in";
     nu_l == 0 means "derive from Re"; rho_s == 0 means "use the liquid density".
     """
@@ -78,6 +79,7 @@ class Case:
     rho_s: float = 0.0
     seed: int = 0
     noise_amp: float = 1e-4
+    wall_dT: tuple = ()  # optional angular profile of extra wall superheat (fractions of Tc), equal knots
     name: str = ""
 
     def replace(self, **kw) -> "Case":

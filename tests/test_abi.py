@@ -38,7 +38,7 @@ def test_library_exports_every_declared_symbol(lib):
 
 def test_struct_sizes_match_header_layout():
     assert C.sizeof(N.Domain) == 16
-    assert C.sizeof(N.Cylinder) == 40
+    assert C.sizeof(N.Cylinder) == 56
     assert C.sizeof(N.Params) == 16 * 8 + 8 + 16 + 16
     assert C.sizeof(N.Init) == 40
     assert C.sizeof(N.Info) == 14 * 8 + 4 * 8

@@ -138,6 +138,7 @@ EDGE_CASES = {
     "warmup_30": (si.SMALL.replace(warmup=30), None),
     "viscosity_ratio_2": (si.SMALL.replace(nu_ratio=2.0, Pr_v=1.0), None),
     "no_energy": (si.SMALL.replace(energy=0), None),
+    "wall_profile_7_knots": (si.SMALL.replace(wall_dT=(0.0, 0.03, -0.02, 0.05, 0.01, -0.04, 0.02)), None),
 }
 
 

@@ -155,6 +155,32 @@ def test_sigma_enters_through_sigma_over_psi_squared():
         assert np.abs(a - b).max() <= 1e-12 * np.abs(a).max()
 
 
+def test_wall_profile_interpolates_knots_periodically_in_the_angle():
+    # knots at angles 0, pi/2, pi, 3pi/2 measured from +x; solid nodes on the axes take a knot,
+    # nodes on the diagonals the mean of the two neighbouring knots (the last pair wraps around)
+    knots = (0.01, 0.03, -0.02, 0.04)
+    c = si.SMALL.replace(wall_dT=knots)  # cylinder of radius 8 at (32, 32)
+    o = Oracle(c, drho=c.drho()).step(3)
+    _, d = stepper.derive(c)
+    T = o.field("T")
+    expect = {(35, 32): knots[0], (32, 35): knots[1], (29, 32): knots[2], (32, 29): knots[3],
+              (34, 34): 0.5 * (knots[0] + knots[1]), (34, 30): 0.5 * (knots[3] + knots[0]),
+              (30, 30): 0.5 * (knots[2] + knots[3])}
+    for (x, y), k in expect.items():
+        assert o.field("solid")[y, x] == 1
+        assert abs(T[y, x] - (d.T_wall + k * d.Tc)) < 1e-14 * d.T_wall, (x, y)
+
+
+def test_uniform_wall_profile_equals_a_larger_superheat():
+    a = si.SMALL.replace(superheat_Tc=0.05, wall_dT=(0.02, 0.02, 0.02))
+    b = si.SMALL.replace(superheat_Tc=0.07)
+    oa = Oracle(a, drho=a.drho()).step(30)
+    ob = Oracle(b, drho=b.drho()).step(30)
+    for k in ("rho", "ux", "uy", "T"):
+        x, y = oa.field(k), ob.field(k)
+        assert np.abs(x - y).max() <= 1e-12 * np.abs(y).max(), k
+
+
 # ---------------------------------------------------------------- closed forms
 
 def test_taylor_green_decay_matches_closed_form():
