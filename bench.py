@@ -13,6 +13,8 @@ stages of the temperature equation).  Default workload: the paper-shaped single 
              (lbm_fields) plus the heat flux.
   roofline   the dominant kernel's algorithmic bytes per launch / its mean event-timed
              duration, against the measured HBM copy bandwidth.
+  adjoint    cost of the checkpointed adjoint window (512 x 256, D = 32, 500 steps,
+             checkpoint every 50) relative to the forward window.
   cpu_baseline  the FP64 CPU oracle on a bounded number of steps of the same workload.
 
 --impl reference times that oracle alone (the reference arm for this method: the
@@ -38,7 +40,7 @@ if ROOT not in sys.path:
 
 import synthetic_inputs as si  # noqa: E402
 
-METRIC = "MLUPS and % HBM roofline per boiling step"
+METRIC = "MLUPS and % HBM roofline per boiling step; adjoint/forward cost ratio"
 UNIT = "MLUPS"
 WORKLOADS = {
     "paper_shaped": si.PAPER_SHAPED.replace(warmup=0, name="1536x768_D96_Re300_dT0.10Tc_fp32"),
@@ -214,6 +216,48 @@ def run_batch(args):
     return 0
 
 
+def adjoint_cost(window=500, ckpt_every=50, spin_up=2000):
+    """Cost of the adjoint window against the forward steps it differentiates, on the
+    512 x 256 lattice, D = 32, Re = 300 (FP32 forward and adjoint fields, FP64 parameter
+    sums): forward = lbm_step over the window; adjoint = lbm_adjoint_window (its own
+    checkpointed forward pass, then segment recompute and reverse steps)."""
+    import ctypes as C
+
+    import torch
+
+    from paper_1912_02018_gb300 import Sim
+    from paper_1912_02018_gb300 import _native as N
+
+    case = si.ADJOINT
+    sim = Sim.from_case(case, f64=False).step(spin_up)
+    state = sim.get_state()
+    stream = torch.cuda.current_stream()
+    L = N.lib()
+    res = {}
+    for rep in range(2):  # the first pass allocates the adjoint buffers
+        sim.set_state(*state)
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        torch.cuda.synchronize()
+        e[0].record(stream)
+        sim.step(window)
+        e[1].record(stream)
+        sim.set_state(*state)
+        g = N.WindowGrad()
+        torch.cuda.synchronize()
+        e[2].record(stream)
+        N.check(L.lbm_adjoint_window(sim.h, window, ckpt_every, C.byref(g)), sim.h)
+        e[3].record(stream)
+        torch.cuda.synchronize()
+        fwd, adj = e[0].elapsed_time(e[1]), e[2].elapsed_time(e[3])
+        res = {"workload": case.name, "window": window, "ckpt_every": ckpt_every, "spin_up": spin_up,
+               "forward_ms": fwd, "adjoint_window_ms": adj, "reverse_ms": adj - fwd,
+               "ratio": (adj - fwd) / fwd, "ratio_incl_forward": adj / fwd, "J": g.J,
+               "dJ_dsuperheat": g.dJ_dsuperheat, "dJ_du_in": g.dJ_du_in,
+               "note": "ratio = (adjoint window - forward window) / forward window; L2-resident lattice"}
+    sim.close()
+    return res
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -321,6 +365,8 @@ def run_ours(args):
         "step_roofline": {"alg_bytes_per_lup": STEP_ALG_BYTES, "achieved_gbs": step_gbs, "frac": step_gbs / peak},
         "kernels": kernels, "gpu_launches": launches, "e2e": e2e, "clocks": clk,
     }
+    if world == 1 and not args.no_adjoint:
+        line["adjoint"] = adjoint_cost()
     if world == 1 and not args.no_cpu_baseline:
         cpu, _, _ = oracle_sample(case, budget_s=args.cpu_seconds, max_steps=10 ** 6)
         line["cpu_baseline"] = cpu
@@ -338,6 +384,7 @@ def main():
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["sweep64"], default="paper_shaped")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint-window cost measurement")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--storage", default="f32", choices=("f32", "f64", "f16s"),
                     help="population storage of the FP32 build (shifted FP16: f - w rho_l)")

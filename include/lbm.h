@@ -243,6 +243,54 @@ lbm_status lbm_batch_domain(lbm_batch *b, int32_t i, lbm_ctx **ctx);
 void lbm_batch_destroy(lbm_batch *b);
 
 /*
+ * Adjoint (reverse-mode derivative) of the time step.  The paper has no adjoint; these are
+ * the exact transpose of the discrete update above (upwind switches and clamps take the
+ * branch the forward took), for design and inverse problems on the wall heat flux of
+ * Sec. IV.B.  Both need energy = 1, every step at or past the warm-up, and (FP32 build)
+ * storage = LBM_STORE_F32; otherwise LBM_EINVAL / LBM_ESTATE.  Forward values are
+ * recomputed in the context's precision; parameter gradients accumulate in FP64.
+ *
+ * Objective of a window of n steps from the current state:
+ *   J = (1/n) sum_{s<n} q_s,  q_s the heat-flux sample of step s (lbm_wall_heat_flux),
+ * with the solid nodes held at their wall temperature T_w from the first step on.
+ * Parameters: T_w per solid node; superheat_Tc (T_w = T_sat + (superheat_Tc + profile) T_c);
+ * the profile knots of lbm_cylinder.wall_dT; u_in, as the speed of the Zou-He inlet only
+ * (nu_l, g and outlet_U stay at the context's values: pass them explicitly in
+ * lbm_params when comparing with finite differences of u_in).
+ */
+typedef struct {
+    double J;              /* out: the window's mean heat flux */
+    double dJ_dsuperheat;  /* out: dJ / d superheat_Tc */
+    double dJ_du_in;       /* out: dJ / d u_in */
+    double *dJ_dwall_dT;   /* in: NULL or room for n_wall values; out: dJ / d knot k */
+    double *dJ_dTw;        /* in: NULL or room for ny*nx doubles; out: dJ / dT_w at each solid
+                              node, 0 at fluid nodes (host, [ny][nx]) */
+} lbm_window_grad;
+
+/*
+ * Run the window's n_steps forward from the current state (the context advances exactly as
+ * with lbm_step, heat-flux statistics included; T at solid nodes is first reset to T_w) and
+ * return J and its gradient.  The reverse pass keeps a checkpoint every ckpt_every steps and
+ * recomputes each segment from it: device memory (ckpt_every + 1 states, ckpt_every sets of
+ * rho, psi, u, one state per checkpoint, ~40 work planes) is allocated on first use through
+ * the context's allocator and kept for later windows.  Synchronises.
+ */
+lbm_status lbm_adjoint_window(lbm_ctx *ctx, int64_t n_steps, int32_t ckpt_every, lbm_window_grad *out);
+
+/*
+ * Vector-Jacobian product of one step at the current state (the context does not advance).
+ * Seeds on the step's outputs: fb ([9][ny][nx], on f* after the step), Tb ([ny][nx], on T
+ * after the step), sb ([3][ny], on the outlet side values after the step) and q_weight (on
+ * this step's heat-flux sample); NULL seeds are zero.  Results on the step's inputs: fb_out
+ * (f* before the step), Tb_out (T before the step; at solid nodes it is the part that reaches
+ * T_w through the state), sb_out, and the direct parameter parts dJ_dTw ([ny][nx], solid
+ * nodes: through the Dirichlet values this step assigns) and dJ_du_in.  Host doubles; NULL
+ * outputs are skipped.  Synchronises.
+ */
+lbm_status lbm_adjoint_step(lbm_ctx *ctx, const double *fb, const double *Tb, const double *sb, double q_weight,
+                            double *fb_out, double *Tb_out, double *sb_out, double *dJ_dTw, double *dJ_du_in);
+
+/*
  * Wall heat flux from caller-owned fields, with no context and no allocation.
  * The paper has no counterpart of this entry point; it exists for callers that cannot
  * allocate device memory: code whose device memory is a fixed pool handed out by an outer

@@ -5,11 +5,12 @@ pseudopotential lattice Boltzmann model for forced-convection boiling on a cylin
 The compute path is the CUDA library liblbm.so (C ABI in include/lbm.h), built by
 nvcc_build.py; this package only marshals arguments to it.  Importing works without a GPU;
 creating a Sim needs the built library and a CUDA device and fails loudly otherwise.
+The adjoint submodule (imported on demand) wraps the adjoint window in torch.autograd.
 """
 from . import _native  # noqa: F401
 from .sim import Batch, Sim  # noqa: F401
 
-__all__ = ["Sim", "Batch", "build"]
+__all__ = ["Sim", "Batch", "build", "adjoint"]
 
 
 def build(force: bool = False, verbose: bool = False) -> str:

@@ -21,7 +21,7 @@ FIELD_BITS = {"rho": 1, "ux": 2, "uy": 4, "T": 8, "psi": 16, "solid": 32}
 EXPORTS = ("lbm_create", "lbm_step", "lbm_sync", "lbm_wall_heat_flux", "lbm_reset_heat_flux", "lbm_fields",
            "lbm_get_state", "lbm_set_state", "lbm_info", "lbm_profile", "lbm_profile_read", "lbm_last_error",
            "lbm_destroy", "lbm_wall_heat_flux_noalloc", "lbm_batch_create", "lbm_batch_step", "lbm_batch_tune",
-           "lbm_batch_graph", "lbm_batch_domain", "lbm_batch_destroy")
+           "lbm_batch_graph", "lbm_batch_domain", "lbm_batch_destroy", "lbm_adjoint_window", "lbm_adjoint_step")
 
 
 class Domain(C.Structure):
@@ -47,6 +47,11 @@ class Params(C.Structure):
 class Init(C.Structure):
     _fields_ = [("rho", C.c_void_p), ("drho", C.c_void_p), ("ux", C.c_void_p), ("uy", C.c_void_p),
                 ("T", C.c_void_p)]
+
+
+class WindowGrad(C.Structure):
+    _fields_ = [("J", C.c_double), ("dJ_dsuperheat", C.c_double), ("dJ_du_in", C.c_double),
+                ("dJ_dwall_dT", C.POINTER(C.c_double)), ("dJ_dTw", C.POINTER(C.c_double))]
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
@@ -101,6 +106,8 @@ def lib():
     L.lbm_batch_tune.argtypes = [vp, C.c_int32, C.POINTER(C.c_int32)]
     L.lbm_batch_graph.argtypes = [vp, C.c_int]
     L.lbm_batch_domain.argtypes = [vp, C.c_int32, C.POINTER(vp)]
+    L.lbm_adjoint_window.argtypes = [vp, i64, C.c_int32, C.POINTER(WindowGrad)]
+    L.lbm_adjoint_step.argtypes = [vp, vp, vp, vp, C.c_double, vp, vp, vp, vp, dp]
     L.lbm_batch_destroy.argtypes = [vp]
     L.lbm_batch_destroy.restype = None
     for name in EXPORTS:

@@ -1,0 +1,674 @@
+// Discrete adjoint of one time step: the reverse-mode derivative of the update of Sec. II
+// and Sec. IV.A of arXiv:1912.02018 (pull-streaming with the wall, inlet and outlet
+// substitutions; rho and psi of Eq. (potential) with the Peng-Robinson EOS of Eq. (eos); the
+// interaction force of Eq. (interForce) and gravity; the CM collision with the consistency
+// terms of Eq. (postColl2); the Heun update of Eq. (energy); the wall heat-flux sample of
+// Sec. IV.B), for seeds on the step's outputs (f*, T, outlet side values) and on its
+// heat-flux sample.  The paper has no adjoint; this is the transpose of its step.
+//
+// Every kernel is a gather (one thread per node, no atomics): a transposed stencil reads the
+// sources whose stencil reaches the node, with the forward's clamped (zero-gradient) columns
+// at a non-periodic inlet and outlet mapped back to every source that read them.  Upwind
+// switches and the clamp of the phase fraction take the branch the forward took.  Forward
+// values come from the stored state of the step and the rho, psi, u of its collision.
+// Parameter gradients (wall temperature per solid node, inlet speed per row) accumulate in
+// FP64; the adjoint fields are in the compute precision.
+#pragma once
+
+#include "lbm_kernels.cuh"
+
+namespace lbm {
+namespace adj {
+
+using namespace kern;
+
+// ---------------------------------------------------------------- dual numbers
+template <typename C>
+struct Dl {
+  C v, d;
+};
+template <typename C>
+__device__ __forceinline__ Dl<C> operator+(Dl<C> a, Dl<C> b) { return {a.v + b.v, a.d + b.d}; }
+template <typename C>
+__device__ __forceinline__ Dl<C> operator-(Dl<C> a, Dl<C> b) { return {a.v - b.v, a.d - b.d}; }
+template <typename C>
+__device__ __forceinline__ Dl<C> operator*(Dl<C> a, Dl<C> b) { return {a.v * b.v, a.d * b.v + a.v * b.d}; }
+template <typename C>
+__device__ __forceinline__ Dl<C> operator/(Dl<C> a, Dl<C> b) {
+  const C q = fdiv(a.v, b.v);
+  return {q, fdiv(a.d - q * b.d, b.v)};
+}
+template <typename C>
+__device__ __forceinline__ Dl<C> operator*(C s, Dl<C> a) { return {s * a.v, s * a.d}; }
+template <typename C>
+__device__ __forceinline__ Dl<C> operator+(C s, Dl<C> a) { return {s + a.v, a.d}; }
+template <typename C>
+__device__ __forceinline__ Dl<C> operator-(C s, Dl<C> a) { return {s - a.v, -a.d}; }
+template <typename C>
+__device__ __forceinline__ Dl<C> dsqrt(Dl<C> a) {
+  const C s = sqrt(a.v);
+  return {s, fdiv(a.d, C(2) * s)};
+}
+
+// Peng-Robinson p(rho, T), Eq. (eos), and (dp/dT)_rho, on dual numbers.
+template <typename C>
+__device__ __forceinline__ Dl<C> pr_p(const PhysC<C>& k, Dl<C> rho, Dl<C> T) {
+  const Dl<C> s = C(1) + k.kappa * (C(1) - dsqrt(T * Dl<C>{C(1) / k.Tc, C(0)}));
+  const Dl<C> rep = (k.R * T) * rho / (C(1) - k.b * rho);
+  const Dl<C> att = (k.a * (s * s)) * (rho * rho) / ((C(1) + C(2) * k.b * rho) - (k.b * k.b) * (rho * rho));
+  return rep - att;
+}
+template <typename C>
+__device__ __forceinline__ Dl<C> pr_dpdT(const PhysC<C>& k, Dl<C> rho, Dl<C> T) {
+  const Dl<C> sq = dsqrt(T * Dl<C>{C(1) / k.Tc, C(0)});
+  const Dl<C> s = C(1) + k.kappa * (C(1) - sq);
+  const Dl<C> dphi = (-k.kappa * s) / dsqrt(T * Dl<C>{k.Tc, C(0)});
+  const Dl<C> rep = k.R * rho / (C(1) - k.b * rho);
+  const Dl<C> att = (k.a * dphi) * (rho * rho) / ((C(1) + C(2) * k.b * rho) - (k.b * k.b) * (rho * rho));
+  return rep - att;
+}
+// d phase_frac / d rho with the branch of the clamp that the forward took (inclusive ends).
+template <typename C>
+__device__ __forceinline__ C dphase(const PhysC<C>& k, C rho) {
+  if (!(k.rho_l > k.rho_v)) return C(0);
+  const C f = fdiv(rho - k.rho_v, k.rho_l - k.rho_v);
+  return (f >= C(0) && f <= C(1)) ? fdiv(C(1), k.rho_l - k.rho_v) : C(0);
+}
+template <typename C>
+__device__ __forceinline__ C dlam(const Phys& ph, C rho) {
+  const PhysC<C>& k = pc<C>(ph);
+  const C alpha = k.alpha_v + phase_frac(ph, rho) * (k.alpha_l - k.alpha_v);
+  return k.c_v * alpha + rho * k.c_v * dphase(k, rho) * (k.alpha_l - k.alpha_v);
+}
+
+template <typename C>
+using Args = AdjArgs<C>;
+
+__device__ __forceinline__ bool node_of_thread(const Geo& g, int& x, int& y) {
+  x = blockIdx.x * 32 + threadIdx.x;
+  y = blockIdx.y * 8 + threadIdx.y;
+  return x < g.nx && y < g.ny;
+}
+template <typename C>
+__device__ __forceinline__ C at(const Geo& g, const C* p, int x, int y) {
+  return p[map_y(g, y) * g.pitch + map_x(g, x)];
+}
+__device__ __forceinline__ bool interior_T(const Geo& g, uint8_t m, int x) {
+  return !(m & kSolid) && !(!g.periodic_x && x == 0);
+}
+// Columns sx with map_x(sx + ex) == x: the sources that read column x at offset ex.
+__device__ __forceinline__ void src_cols(const Geo& g, int x, int ex, int& lo, int& hi) {
+  if (g.periodic_x) {
+    int s = x - ex;
+    s = s < 0 ? s + g.nx : (s >= g.nx ? s - g.nx : s);
+    lo = hi = s;
+    return;
+  }
+  if (x == 0) {
+    lo = 0;
+    hi = -ex;  // empty for ex > 0
+  } else if (x == g.nx - 1) {
+    lo = g.nx - 1 - ex;  // empty for ex < 0
+    hi = g.nx - 1;
+  } else {
+    lo = hi = x - ex;
+  }
+  lo = lo < 0 ? 0 : lo;
+  hi = hi > g.nx - 1 ? g.nx - 1 : hi;
+}
+__device__ __forceinline__ double w_of(int ex, int ey) {
+  const int e2 = ex * ex + ey * ey;
+  return e2 == 1 ? 4.0 / 21.0 : e2 == 2 ? 4.0 / 45.0 : e2 == 4 ? 1.0 / 60.0 : e2 == 5 ? 2.0 / 315.0
+       : e2 == 8 ? 1.0 / 5040.0 : 0.0;
+}
+// Coefficient of phi(x + k) in the third-order upwind derivative at x (v >= 0 or v < 0).
+template <typename C>
+__device__ __forceinline__ C upw_coef(int k, bool pos) {
+  if (pos) return k == -2 ? C(1.0 / 6.0) : k == -1 ? C(-1) : k == 0 ? C(0.5) : k == 1 ? C(1.0 / 3.0) : C(0);
+  return k == -1 ? C(-1.0 / 3.0) : k == 0 ? C(-0.5) : k == 1 ? C(1) : k == 2 ? C(-1.0 / 6.0) : C(0);
+}
+
+// Stencil parts of Eq. (energy) at (x, y) for the temperature field t.
+template <typename C>
+struct Parts {
+  C upx, upy, gx, gy, lap, lx, ly, divu;
+};
+template <typename C>
+__device__ __forceinline__ Parts<C> energy_parts(const Args<C>& a, const C* t, int x, int y) {
+  const Geo& g = a.g;
+  Parts<C> P;
+  const C c = at(g, t, x, y);
+  const C ux0 = at(g, a.ux, x, y), uy0 = at(g, a.uy, x, y);
+  {
+    const C m2 = at(g, t, x - 2, y) - c, m1 = at(g, t, x - 1, y) - c, p1 = at(g, t, x + 1, y) - c,
+            p2 = at(g, t, x + 2, y) - c;
+    P.upx = ux0 >= C(0) ? fdiv(m2 - C(6) * m1 + C(2) * p1, C(6)) : fdiv(-C(2) * m1 + C(6) * p1 - p2, C(6));
+  }
+  {
+    const C m2 = at(g, t, x, y - 2) - c, m1 = at(g, t, x, y - 1) - c, p1 = at(g, t, x, y + 1) - c,
+            p2 = at(g, t, x, y + 2) - c;
+    P.upy = uy0 >= C(0) ? fdiv(m2 - C(6) * m1 + C(2) * p1, C(6)) : fdiv(-C(2) * m1 + C(6) * p1 - p2, C(6));
+  }
+  C gx = 0, gy = 0, lap = 0, lx = 0, ly = 0, dxux = 0, dyuy = 0;
+#pragma unroll
+  for (int k = 0; k < 12; ++k) {
+    const int ex = exv(k), ey = eyv(k);
+    const C w = C(wiso(k));
+    const C tp = at(g, t, x + ex, y + ey), tm = at(g, t, x - ex, y - ey);
+    gx = gx + w * (tp - tm) * C(ex);
+    gy = gy + w * (tp - tm) * C(ey);
+    lap = lap + w * ((tp + tm) - C(2) * c);
+    const C lp = lam_of(a.ph, at(g, a.rho, x + ex, y + ey)), lm = lam_of(a.ph, at(g, a.rho, x - ex, y - ey));
+    lx = lx + w * (lp - lm) * C(ex);
+    ly = ly + w * (lp - lm) * C(ey);
+    dxux = dxux + w * (at(g, a.ux, x + ex, y + ey) - at(g, a.ux, x - ex, y - ey)) * C(ex);
+    dyuy = dyuy + w * (at(g, a.uy, x + ex, y + ey) - at(g, a.uy, x - ex, y - ey)) * C(ey);
+  }
+  P.gx = gx;
+  P.gy = gy;
+  P.lap = C(2) * lap;
+  P.lx = lx;
+  P.ly = ly;
+  P.divu = dxux + dyuy;
+  return P;
+}
+
+// ---------------------------------------------------------------- kernels
+// Stage-1 temperature T1 = T + L(T) of the forward (Dirichlet at the wall and the inlet).
+template <typename C>
+__global__ void __launch_bounds__(256) k_adj_t1(Args<C> a) {
+  int x, y;
+  if (!node_of_thread(a.g, x, y)) return;
+  const int id = y * a.g.pitch + x;
+  const uint8_t m = a.mask[id];
+  const PhysC<C>& k = pc<C>(a.ph);
+  C t1;
+  if (m & kSolid) {
+    t1 = a.T[id];
+  } else if (!a.g.periodic_x && x == 0) {
+    t1 = k.T_sat;
+  } else {
+    const Parts<C> P = energy_parts(a, a.T, x, y);
+    const C r0 = a.rho[id], T0 = a.T[id], lam0 = lam_of(a.ph, r0);
+    const C conv = a.ux[id] * P.upx + a.uy[id] * P.upy;
+    const C diff = lam0 * P.lap + (P.lx * P.gx + P.ly * P.gy);
+    const C work = T0 * dpdT_eos(a.ph, r0, T0) * P.divu;
+    t1 = T0 + (-conv + fdiv(diff, r0 * k.c_v) - fdiv(work, r0 * k.c_v));
+  }
+  a.T1[id] = t1;
+}
+
+// Sources of the transposed stencils of L at node x, for the seed a_s on L(t)(x):
+// stage 2 (t = T1, a_s = Tb_in / 2) or stage 1 (t = T, a_s = Tb1; plus the heat-flux sample).
+template <typename C, int STAGE>
+__global__ void __launch_bounds__(256) k_adj_src(Args<C> a) {
+  int x, y;
+  if (!node_of_thread(a.g, x, y)) return;
+  const Geo& g = a.g;
+  const int id = y * g.pitch + x;
+  const uint8_t m = a.mask[id];
+  const PhysC<C>& k = pc<C>(a.ph);
+  if (m & kSolid) {
+    // T^{n+1} and T1 at a solid node are its wall temperature
+    a.gw[id] += (double)(STAGE == 2 ? a.Tb_in[id] : a.Tb1[id]);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) a.P[j][id] = C(0);
+#pragma unroll
+    for (int j = 0; j < 5; ++j) a.loc[j][id] = C(0);
+    return;
+  }
+  const C* t = STAGE == 2 ? a.T1 : a.T;
+  C s = C(0);
+  if (interior_T(g, m, x)) s = STAGE == 2 ? C(0.5) * a.Tb_in[id] : a.Tb1[id];
+  const bool hf = STAGE == 1 && a.do_hf && (m & kNearWall);
+  if (s == C(0) && !hf) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) a.P[j][id] = C(0);
+#pragma unroll
+    for (int j = 0; j < 5; ++j) a.loc[j][id] = C(0);
+    return;
+  }
+  const Parts<C> P = energy_parts(a, t, x, y);
+  const C r0 = a.rho[id], T0 = t[id], lam0 = lam_of(a.ph, r0);
+  const C rc = r0 * k.c_v;
+  const Dl<C> dT = pr_dpdT(k, Dl<C>{r0, C(0)}, Dl<C>{T0, C(1)});
+  const Dl<C> dR = pr_dpdT(k, Dl<C>{r0, C(1)}, Dl<C>{T0, C(0)});
+  const C diff = lam0 * P.lap + (P.lx * P.gx + P.ly * P.gy);
+  const C work = T0 * dT.v * P.divu;
+  C p1 = s * fdiv(P.lx, rc), p2 = s * fdiv(P.ly, rc);
+  C llam = s * fdiv(P.lap, rc);
+  if (hf) {
+    // q = -lambda grad T . n at this boundary node (Sec. IV.B)
+    const double dx = x - g.xc, dy = y - g.yc, rr = sqrt(dx * dx + dy * dy);
+    const C nxv = C(dx / rr), nyv = C(dy / rr);
+    p1 = p1 - a.wq * lam0 * nxv;
+    p2 = p2 - a.wq * lam0 * nyv;
+    llam = llam - a.wq * (P.gx * nxv + P.gy * nyv);
+  }
+  a.P[0][id] = s * fdiv(lam0, rc);
+  a.P[1][id] = p1;
+  a.P[2][id] = p2;
+  a.P[3][id] = s * a.ux[id];
+  a.P[4][id] = s * a.uy[id];
+  a.P[5][id] = -s * fdiv(T0 * dT.v, rc);
+  a.P[6][id] = s * fdiv(P.gx, rc);
+  a.P[7][id] = s * fdiv(P.gy, rc);
+  a.loc[0][id] = -s * fdiv(P.divu, rc) * (dT.v + T0 * dT.d);
+  a.loc[1][id] = -s * P.upx;
+  a.loc[2][id] = -s * P.upy;
+  a.loc[3][id] = llam;
+  a.loc[4][id] = s * (-fdiv(diff - work, rc * r0) - fdiv(T0 * P.divu * dR.d, rc));
+}
+
+// Transposed stencils of L: the adjoint of the temperature field the stage read, and the
+// stage's parts of the adjoints of u, lambda and rho.
+template <typename C, int STAGE>
+__global__ void __launch_bounds__(256) k_adj_gather(Args<C> a) {
+  int x, y;
+  if (!node_of_thread(a.g, x, y)) return;
+  const Geo& g = a.g;
+  const int id = y * g.pitch + x;
+  const uint8_t m = a.mask[id];
+  C tb = C(0), ubx = C(0), uby = C(0), lb = C(0);
+  C wsum = C(0);
+#pragma unroll
+  for (int k = 0; k < 12; ++k) wsum = wsum + C(wiso(k));
+  for (int ey = -2; ey <= 2; ++ey) {
+    const int sy = wrap_y(g, y - ey);
+    for (int ex = -2; ex <= 2; ++ex) {
+      int lo, hi;
+      src_cols(g, x, ex, lo, hi);
+      const C w = C(w_of(ex, ey));
+      const C clap = (ex == 0 && ey == 0) ? C(-4) * wsum : C(2) * w;
+      for (int sx = lo; sx <= hi; ++sx) {
+        const int s = sy * g.pitch + sx;
+        tb = tb + clap * a.P[0][s];
+        if (ex != 0 || ey != 0) {
+          tb = tb + w * (C(ex) * a.P[1][s] + C(ey) * a.P[2][s]);
+          ubx = ubx + w * C(ex) * a.P[5][s];
+          uby = uby + w * C(ey) * a.P[5][s];
+          lb = lb + w * (C(ex) * a.P[6][s] + C(ey) * a.P[7][s]);
+        }
+        if (ey == 0) tb = tb - upw_coef<C>(ex, a.ux[s] >= C(0)) * a.P[3][s];
+        if (ex == 0) tb = tb - upw_coef<C>(ey, a.uy[s] >= C(0)) * a.P[4][s];
+      }
+    }
+  }
+  const bool in = interior_T(g, m, x);
+  tb = tb + a.loc[0][id];
+  ubx = ubx + a.loc[1][id];
+  uby = uby + a.loc[2][id];
+  lb = lb + a.loc[3][id];
+  if (STAGE == 2) {
+    a.Tb1[id] = (in ? C(0.5) * a.Tb_in[id] : C(0)) + tb;
+    a.ub[0][id] = ubx;
+    a.ub[1][id] = uby;
+    a.lamb[id] = lb;
+    a.rhob[id] = a.loc[4][id];
+  } else {
+    a.Tb_out[id] = (in ? C(0.5) * a.Tb_in[id] + a.Tb1[id] : C(0)) + tb;
+    a.ub[0][id] = a.ub[0][id] + ubx;
+    a.ub[1][id] = a.ub[1][id] + uby;
+    C rb = a.rhob[id] + a.loc[4][id];
+    if (!(m & kSolid)) rb = rb + dlam(a.ph, a.rho[id]) * (a.lamb[id] + lb);
+    a.rhob[id] = rb;
+  }
+}
+
+// Adjoint of the CM collision at a fluid node (Sec. II.A-B): from the seeds on f*, on u and
+// rho (energy equation), the adjoints of the pulled populations, of F_m and of psi.
+template <typename C>
+__global__ void __launch_bounds__(256) k_adj_collide(Args<C> a) {
+  int x, y;
+  if (!node_of_thread(a.g, x, y)) return;
+  const Geo& g = a.g;
+  const int id = y * g.pitch + x;
+  const uint8_t m = a.mask[id];
+  const PhysC<C>& k = pc<C>(a.ph);
+  if (m & kSolid) {
+#pragma unroll
+    for (int i = 0; i < 9; ++i) a.fpb[i * g.plane + id] = C(0);
+    a.fmb[0][id] = C(0);
+    a.fmb[1][id] = C(0);
+    a.psib[id] = C(0);
+    return;
+  }
+  const C cs2 = C(1.0 / 3.0);
+  C fo[9];
+  pull_node<C, C>(g, a.ph, a.f, a.mask, a.side, nullptr, x, y, m, fo);
+  C rho = fo[0];
+#pragma unroll
+  for (int i = 1; i < 9; ++i) rho = rho + fo[i];
+  const bool multiphase = k.G != C(0);
+  C Fmx = C(0), Fmy = C(0), psi0 = C(0);
+  if (multiphase) {
+    psi0 = a.psi[id];
+    C sx = C(0), sy = C(0);
+#pragma unroll
+    for (int kk = 0; kk < 12; ++kk) {
+      const int ex = exv(kk), ey = eyv(kk);
+      const C d = at(g, a.psi, x + ex, y + ey) - at(g, a.psi, x - ex, y - ey);
+      sx = sx + C(wiso(kk)) * d * C(ex);
+      sy = sy + C(wiso(kk)) * d * C(ey);
+    }
+    Fmx = -k.G * cs2 * psi0 * sx;
+    Fmy = -k.G * cs2 * psi0 * sy;
+  }
+  const C Fx = Fmx - (rho - k.rho_l) * k.g, Fy = Fmy;
+  const C nu = nu_of(a.ph, rho);
+  const C omega = fdiv(C(1), fdiv(nu, cs2) + C(0.5));
+  const C sig = multiphase ? k.sigma : C(0);
+  const C m1 = ((((fo[1] - fo[2]) + fo[5]) - fo[6]) + fo[7]) - fo[8];
+  const C m2 = ((((fo[3] - fo[4]) + fo[5]) - fo[6]) - fo[7]) + fo[8];
+  const C m4 = ((fo[1] + fo[2]) - fo[3]) - fo[4];
+  const C m5 = ((fo[5] + fo[6]) - fo[7]) - fo[8];
+  const C u = fdiv(m1 + C(0.5) * Fx, rho), v = fdiv(m2 + C(0.5) * Fy, rho);
+  const C k4 = (((u * u - v * v) * rho - C(2) * u * m1) + C(2) * v * m2) + m4;
+  const C k5 = (((u * v) * rho - v * m1) - u * m2) + m5;
+  const C alpha = sig != C(0) ? fdiv(sig, psi0 * psi0) : C(0);
+  const C Fm2 = Fmx * Fmx + Fmy * Fmy;
+  // post-collision central moments k*
+  const C K0 = rho, K1 = C(0.5) * Fx, K2 = C(0.5) * Fy;
+  const C K3 = fdiv(C(2) * rho, C(3)) + C(2) * alpha * Fm2;
+  const C K4 = (C(1) - omega) * k4, K5 = (C(1) - omega) * k5;
+  const C K6 = fdiv(Fy, C(6)), K7 = fdiv(Fx, C(6));
+  // seeds on f*; m*-bar = M^{-T} f*-bar (closed form of M^{-1})
+  C fb[9];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) fb[i] = a.fb_in[i * g.plane + id];
+  const C h = C(0.5), q = C(0.25);
+  const C s14 = (fb[1] + fb[2]) + (fb[3] + fb[4]);
+  const C s58 = (fb[5] + fb[6]) + (fb[7] + fb[8]);
+  const C b0 = fb[0];
+  const C b1 = h * (fb[1] - fb[2]);
+  const C b2 = h * (fb[3] - fb[4]);
+  const C b3 = q * s14 - fb[0];
+  const C b4 = q * ((fb[1] + fb[2]) - (fb[3] + fb[4]));
+  const C b5 = q * ((fb[5] + fb[6]) - (fb[7] + fb[8]));
+  const C b6 = h * (fb[4] - fb[3]) + q * ((fb[5] - fb[6]) - (fb[7] - fb[8]));
+  const C b7 = h * (fb[2] - fb[1]) + q * ((fb[5] - fb[6]) + (fb[7] - fb[8]));
+  const C b8 = (fb[0] - h * s14) + q * s58;
+  // m* = N(-u) k*: k*-bar = N(-u)^T m*-bar and the u-derivative of N(-u) k*
+  const C uu = u * u, vv = v * v, uv = u * v;
+  const C kb0 = b0 + u * b1 + v * b2 + (uu + vv) * b3 + (uu - vv) * b4 + uv * b5 + uu * v * b6 + u * vv * b7 +
+                uu * vv * b8;
+  const C kb1 = b1 + C(2) * u * b3 + C(2) * u * b4 + v * b5 + C(2) * uv * b6 + vv * b7 + C(2) * u * vv * b8;
+  const C kb2 = b2 + C(2) * v * b3 - C(2) * v * b4 + u * b5 + uu * b6 + C(2) * uv * b7 + C(2) * uu * v * b8;
+  const C kb3 = b3 + h * v * b6 + h * u * b7 + h * (uu + vv) * b8;
+  const C kb4 = b4 + h * v * b6 - h * u * b7 - h * (uu - vv) * b8;
+  const C kb5 = b5 + C(2) * u * b6 + C(2) * v * b7 + C(4) * uv * b8;
+  const C kb6 = b6 + C(2) * v * b8;
+  const C kb7 = b7 + C(2) * u * b8;
+  const C kb8 = b8;
+  C ubar = b1 * K0 + b3 * (C(2) * u * K0 + C(2) * K1) + b4 * (C(2) * u * K0 + C(2) * K1) + b5 * (v * K0 + K2) +
+           b6 * (C(2) * uv * K0 + C(2) * v * K1 + C(2) * u * K2 + C(2) * K5) +
+           b7 * (vv * K0 + C(2) * v * K2 + h * K3 - h * K4) +
+           b8 * (C(2) * u * vv * K0 + C(2) * vv * K1 + C(4) * uv * K2 + u * K3 - u * K4 + C(4) * v * K5 +
+                 C(2) * K7);
+  C vbar = b2 * K0 + b3 * (C(2) * v * K0 + C(2) * K2) - b4 * (C(2) * v * K0 + C(2) * K2) + b5 * (u * K0 + K1) +
+           b6 * (uu * K0 + C(2) * u * K1 + h * K3 + h * K4) +
+           b7 * (C(2) * uv * K0 + C(2) * v * K1 + C(2) * u * K2 + C(2) * K5) +
+           b8 * (C(2) * uu * v * K0 + C(4) * uv * K1 + C(2) * uu * K2 + v * K3 + v * K4 + C(4) * u * K5 +
+                 C(2) * K6);
+  // k* -> rho, F, alpha |F_m|^2, k4, k5, omega
+  C rb = kb0 + fdiv(C(2) * kb3, C(3)) + fdiv(kb8, C(9));
+  C Fbx = h * kb1 + fdiv(kb7, C(6)), Fby = h * kb2 + fdiv(kb6, C(6));
+  const C Abar = C(2) * kb3 + fdiv(C(2) * kb8, C(3));
+  C Fmbx = Abar * alpha * C(2) * Fmx, Fmby = Abar * alpha * C(2) * Fmy;
+  const C psib = sig != C(0) ? Abar * Fm2 * fdiv(C(-2) * sig, psi0 * psi0 * psi0) : C(0);
+  const C k4b = (C(1) - omega) * kb4, k5b = (C(1) - omega) * kb5;
+  const C omb = -(k4 * kb4 + k5 * kb5);
+  C mb0 = (uu - vv) * k4b + uv * k5b;
+  C mb1 = C(-2) * u * k4b - v * k5b;
+  C mb2 = C(2) * v * k4b - u * k5b;
+  const C mb4 = k4b, mb5 = k5b;
+  ubar = ubar + (C(2) * u * rho - C(2) * m1) * k4b + (v * rho - m2) * k5b;
+  vbar = vbar + (C(2) * m2 - C(2) * v * rho) * k4b + (u * rho - m1) * k5b;
+  // energy-equation seeds on u and rho
+  ubar = ubar + a.ub[0][id];
+  vbar = vbar + a.ub[1][id];
+  // u = (m1 + F/2) / rho
+  mb1 = mb1 + fdiv(ubar, rho);
+  mb2 = mb2 + fdiv(vbar, rho);
+  Fbx = Fbx + fdiv(ubar, C(2) * rho);
+  Fby = Fby + fdiv(vbar, C(2) * rho);
+  rb = rb - fdiv(u * ubar + v * vbar, rho);
+  // omega = 1 / (nu(rho)/cs^2 + 1/2)
+  rb = rb - omb * omega * omega * fdiv(dphase(k, rho) * (k.nu_l - k.nu_v), cs2);
+  // F = F_m + gravity
+  Fmbx = Fmbx + Fbx;
+  Fmby = Fmby + Fby;
+  rb = rb - k.g * Fbx;
+  rb = rb + a.rhob[id];
+  mb0 = mb0 + rb;
+  // f-bar = M^T m-bar (m3, m6, m7, m8 do not reach k4, k5 or u)
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    const int cx = cxv(i), cy = cyv(i);
+    a.fpb[i * g.plane + id] = mb0 + C(cx) * mb1 + C(cy) * mb2 + C(cx * cx - cy * cy) * mb4 + C(cx * cy) * mb5;
+  }
+  a.fmb[0][id] = Fmbx;
+  a.fmb[1][id] = Fmby;
+  a.psib[id] = psib;
+}
+
+// Adjoint of the interaction force (transposed psi stencil) and of psi(rho, T): the psi part
+// of the rho adjoint, and the psi part added to the adjoint of T.
+template <typename C>
+__global__ void __launch_bounds__(256) k_adj_force(Args<C> a) {
+  int x, y;
+  if (!node_of_thread(a.g, x, y)) return;
+  const Geo& g = a.g;
+  const int id = y * g.pitch + x;
+  const uint8_t m = a.mask[id];
+  const PhysC<C>& k = pc<C>(a.ph);
+  if (k.G == C(0)) {
+    a.rhopsi[id] = C(0);
+    return;
+  }
+  const C cs2 = C(1.0 / 3.0), gc = -k.G * cs2;
+  C pb = a.psib[id];
+  if (!(m & kSolid)) {
+    C sx = C(0), sy = C(0);
+#pragma unroll
+    for (int kk = 0; kk < 12; ++kk) {
+      const int ex = exv(kk), ey = eyv(kk);
+      const C d = at(g, a.psi, x + ex, y + ey) - at(g, a.psi, x - ex, y - ey);
+      sx = sx + C(wiso(kk)) * d * C(ex);
+      sy = sy + C(wiso(kk)) * d * C(ey);
+    }
+    pb = pb + gc * (a.fmb[0][id] * sx + a.fmb[1][id] * sy);
+  }
+  for (int ey = -2; ey <= 2; ++ey) {
+    const int sy = wrap_y(g, y - ey);
+    for (int ex = -2; ex <= 2; ++ex) {
+      if (ex == 0 && ey == 0) continue;
+      int lo, hi;
+      src_cols(g, x, ex, lo, hi);
+      const C w = C(w_of(ex, ey));
+      for (int sx = lo; sx <= hi; ++sx) {
+        const int s = sy * g.pitch + sx;
+        pb = pb + gc * a.psi[s] * w * (C(ex) * a.fmb[0][s] + C(ey) * a.fmb[1][s]);
+      }
+    }
+  }
+  // psi = sqrt(rad), rad = k2 (p - rho cs^2), k2 = 2 / (G cs^2)
+  const C r0 = a.rho[id], T0 = a.T[id], psi0 = a.psi[id];
+  const C k2 = fdiv(C(2), k.G * cs2);
+  const C dpr = pr_p(k, Dl<C>{r0, C(1)}, Dl<C>{T0, C(0)}).d;
+  const C dpt = pr_dpdT(k, Dl<C>{r0, C(0)}, Dl<C>{T0, C(0)}).v;
+  const C inv2psi = fdiv(C(1), C(2) * psi0);
+  a.rhopsi[id] = (m & kSolid) ? C(0) : pb * k2 * (dpr - cs2) * inv2psi;
+  a.Tb_out[id] = a.Tb_out[id] + pb * k2 * dpt * inv2psi;
+}
+
+// Adjoint of pulled value i at node z (psi part of rho included; the Zou-He inlet's
+// unknowns folded into its knowns; the outlet's replaced values carry nothing here).
+template <typename C>
+__device__ __forceinline__ C eff_fbar(const Args<C>& a, int zx, int zy, int i) {
+  const Geo& g = a.g;
+  const int id = zy * g.pitch + zx;
+  const C rp = a.rhopsi[id];
+  if (!g.periodic_x && zx == g.nx - 1 && (i == 2 || i == 6 || i == 8)) return C(0);
+  if (!g.periodic_x && zx == 0) {
+    if (i == 1 || i == 5 || i == 7) return C(0);
+    const C u = pc<C>(a.ph).u_in;
+    const C f1 = a.fpb[1 * g.plane + id] + rp, f5 = a.fpb[5 * g.plane + id] + rp, f7 = a.fpb[7 * g.plane + id] + rp;
+    const C rb = u * (fdiv(C(2) * f1, C(3)) + fdiv(f5 + f7, C(6)));
+    const C r1 = fdiv(rb, C(1) - u);
+    C e = a.fpb[i * g.plane + id] + rp;
+    if (i == 0) e = e + r1;
+    else if (i == 3) e = e + r1 - C(0.5) * f5 + C(0.5) * f7;
+    else if (i == 4) e = e + r1 + C(0.5) * f5 - C(0.5) * f7;
+    else if (i == 2) e = e + C(2) * r1 + f1;
+    else if (i == 6) e = e + C(2) * r1 + f5;
+    else e = e + C(2) * r1 + f7;  // i == 8
+    return e;
+  }
+  return a.fpb[i * g.plane + id] + rp;
+}
+
+// Transposed pull-streaming (a push written as a gather): the adjoint of f* entering the
+// step, of the outlet's side values, and the inlet-speed derivative of the Zou-He rows.
+template <typename C>
+__global__ void __launch_bounds__(256) k_adj_pull(Args<C> a) {
+  int x, y;
+  if (!node_of_thread(a.g, x, y)) return;
+  const Geo& g = a.g;
+  const int id = y * g.pitch + x;
+  const uint8_t m = a.mask[id];
+  const PhysC<C>& k = pc<C>(a.ph);
+  if (!g.periodic_x && x == g.nx - 1) {
+    // convective outlet: v = (side + U inner) / (1 + U), also the next side value
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const int i = j == 0 ? 2 : (j == 1 ? 6 : 8);
+      const C sb = a.sb_in[j * g.ny + y];
+      a.sb_out[j * g.ny + y] =
+          (m & kSolid) ? sb : fdiv(a.fpb[i * g.plane + id] + a.rhopsi[id] + sb, C(1) + k.U_out);
+    }
+  }
+  if (m & kSolid) {
+#pragma unroll
+    for (int i = 0; i < 9; ++i) a.fb_out[i * g.plane + id] = C(0);
+    return;
+  }
+  if (!g.periodic_x && x == 0) {
+    // Zou-He: d/du_in of f1, f5, f7 through rho_in u and rho_in = (...)/(1 - u)
+    C fo[9];
+    pull_node<C, C>(g, a.ph, a.f, a.mask, a.side, nullptr, x, y, m, fo);
+    const C u = k.u_in;
+    const C rho_in = fdiv(fo[0] + fo[3] + fo[4] + C(2) * (fo[2] + fo[6] + fo[8]), C(1) - u);
+    const C rp = a.rhopsi[id];
+    const C bsum = fdiv(C(2) * (a.fpb[1 * g.plane + id] + rp), C(3)) +
+                   fdiv((a.fpb[5 * g.plane + id] + rp) + (a.fpb[7 * g.plane + id] + rp), C(6));
+    a.uin[y] += (double)bsum * (double)rho_in / (1.0 - (double)u);
+  }
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    const int cx = cxv(i), cy = cyv(i);
+    C acc = C(0);
+    // z = x + c_i pulls direction i from x (a fluid source: a plain pull), and, when the
+    // wall cuts z's link along -c_i with q < 1/2, its Bouzidi value of direction opp(i)
+    int zx = x + cx;
+    const int zy = wrap_y(g, y + cy);
+    if (g.periodic_x) zx = zx < 0 ? zx + g.nx : (zx >= g.nx ? zx - g.nx : zx);
+    if (zx >= 0 && zx < g.nx && !(a.mask[zy * g.pitch + zx] & kSolid)) {
+      acc = acc + eff_fbar(a, zx, zy, i);
+      int wx = zx + cx;
+      const int wy = wrap_y(g, zy + cy);
+      if (g.periodic_x) wx = wx < 0 ? wx + g.nx : (wx >= g.nx ? wx - g.nx : wx);
+      if (i != 0 && wx >= 0 && wx < g.nx && (a.mask[wy * g.pitch + wx] & kSolid)) {
+        const C qz = C(link_fraction(g, zx, zy, cx, cy));
+        if (qz < C(0.5)) acc = acc + (C(1) - C(2) * qz) * eff_fbar(a, zx, zy, oppv(i));
+      }
+    }
+    if (i != 0) {
+      // Bouzidi at x itself: direction j = opp(i) reads f*(x, i); direction i reads f*(x, i)
+      // when q >= 1/2
+      const int j = oppv(i);
+      int sx = x - cxv(j);
+      const int sy = wrap_y(g, y - cyv(j));
+      if (g.periodic_x) sx = sx < 0 ? sx + g.nx : (sx >= g.nx ? sx - g.nx : sx);
+      if (sx >= 0 && sx < g.nx && (a.mask[sy * g.pitch + sx] & kSolid)) {
+        const C qj = C(link_fraction(g, x, y, -cxv(j), -cyv(j)));
+        C ca;
+        if (qj < C(0.5)) {
+          int nxp = x + cxv(j);
+          const int nyp = wrap_y(g, y + cyv(j));
+          if (g.periodic_x) nxp = nxp < 0 ? nxp + g.nx : (nxp >= g.nx ? nxp - g.nx : nxp);
+          const bool ok = nxp >= 0 && nxp < g.nx && !(a.mask[nyp * g.pitch + nxp] & kSolid);
+          ca = ok ? C(2) * qj : C(1);
+        } else {
+          ca = fdiv(C(1), C(2) * qj);
+        }
+        acc = acc + ca * eff_fbar(a, x, y, j);
+      }
+      int tx = x - cx;
+      const int ty = wrap_y(g, y - cy);
+      if (g.periodic_x) tx = tx < 0 ? tx + g.nx : (tx >= g.nx ? tx - g.nx : tx);
+      if (tx >= 0 && tx < g.nx && (a.mask[ty * g.pitch + tx] & kSolid)) {
+        const C qi = C(link_fraction(g, x, y, -cx, -cy));
+        if (!(qi < C(0.5))) acc = acc + fdiv(C(2) * qi - C(1), C(2) * qi) * eff_fbar(a, x, y, i);
+      }
+    }
+    if (!g.periodic_x && x == g.nx - 1 && (i == 2 || i == 6 || i == 8)) {
+      // the outlet value of row y + c_y(i) reads f*(x, i) as its inner value
+      const int jo = i == 2 ? 0 : (i == 6 ? 1 : 2);
+      const int yo = wrap_y(g, y + cy);
+      const int oid = yo * g.pitch + x;
+      if (!(a.mask[oid] & kSolid)) {
+        const C vb = a.fpb[i * g.plane + oid] + a.rhopsi[oid] + a.sb_in[jo * g.ny + yo];
+        acc = acc + fdiv(k.U_out * vb, C(1) + k.U_out);
+      }
+    }
+    a.fb_out[i * g.plane + id] = acc;
+  }
+}
+
+// The window starts with the solid nodes at their wall temperature.
+template <typename C>
+__global__ void __launch_bounds__(256) k_adj_wall_seed(Geo g, const uint8_t* mask, const C* Tb, double* gw) {
+  int x, y;
+  if (!node_of_thread(g, x, y)) return;
+  const int id = y * g.pitch + x;
+  if (mask[id] & kSolid) gw[id] += (double)Tb[id];
+}
+template <typename C>
+__global__ void __launch_bounds__(256) k_impose_wall(Geo g, const uint8_t* mask, const C* wallT, C* T) {
+  int x, y;
+  if (!node_of_thread(g, x, y)) return;
+  const int id = y * g.pitch + x;
+  if (mask[id] & kSolid) T[id] = wallT[id];
+}
+// Dense [ny][nx] doubles <-> typed [ny][pitch] planes.
+template <typename C>
+__global__ void __launch_bounds__(256) k_dense_to_plane(Geo g, const double* src, C* dst) {
+  int x, y;
+  if (!node_of_thread(g, x, y)) return;
+  dst[y * g.pitch + x] = (C)src[y * g.nx + x];
+}
+template <typename C>
+__global__ void __launch_bounds__(256) k_plane_to_dense(Geo g, const C* src, double* dst) {
+  int x, y;
+  if (!node_of_thread(g, x, y)) return;
+  dst[y * g.nx + x] = (double)src[y * g.pitch + x];
+}
+
+// One reverse step (8 launches).  Returns the number of launches or -1.
+template <typename C>
+int adjoint_step_impl(const Args<C>& a, cudaStream_t s) {
+  const dim3 blk(32, 8), grd((a.g.nx + 31) / 32, (a.g.ny + 7) / 8);
+  k_adj_t1<C><<<grd, blk, 0, s>>>(a);
+  k_adj_src<C, 2><<<grd, blk, 0, s>>>(a);
+  k_adj_gather<C, 2><<<grd, blk, 0, s>>>(a);
+  k_adj_src<C, 1><<<grd, blk, 0, s>>>(a);
+  k_adj_gather<C, 1><<<grd, blk, 0, s>>>(a);
+  k_adj_collide<C><<<grd, blk, 0, s>>>(a);
+  k_adj_force<C><<<grd, blk, 0, s>>>(a);
+  k_adj_pull<C><<<grd, blk, 0, s>>>(a);
+  return cudaPeekAtLastError() == cudaSuccess ? 8 : -1;
+}
+
+}  // namespace adj
+}  // namespace lbm

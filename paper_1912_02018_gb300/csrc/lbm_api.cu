@@ -15,6 +15,7 @@
 
 #include "lbm.h"
 #include "lbm_internal.h"
+#include "lbm_ctx.h"
 
 namespace lbm {
 const char* const kKernelNames[kNumKernels] = {"k_rho_psi", "k_collide", "k_energy", "k_export", "k_import"};
@@ -121,44 +122,7 @@ struct PengRobinson {
   }
 };
 
-// ---------------------------------------------------------------- helpers
-lbm_status fail(lbm_ctx* ctx, lbm_status st, const char* fmt, ...);
-
 }  // namespace
-
-struct lbm_ctx {
-  lbm::Geo geo{};
-  lbm::Phys ph{};
-  lbm::Dev dev{};
-  lbm_domain dom{};
-  lbm_cylinder cyl{};
-  lbm_params prm{};
-  lbm_allocator alloc{};
-  bool has_alloc = false;
-  cudaStream_t stream = nullptr;
-  int device = 0;
-  int cur = 0;   // buffer index of f* and the outlet side values
-  int tcur = 0;  // buffer index of T
-  int64_t steps = 0;
-  int64_t launches = 0;
-  bool f64 = false;
-  double Tc = 0, pc = 0, p_sat = 0, lambda_v = 0;
-  std::vector<void*> blocks;
-  size_t bytes = 0;
-  std::string err = "no error";
-  // per-launch timing
-  struct Pending {
-    int kernel;
-    cudaEvent_t e0, e1;
-  };
-  bool prof = false;
-  std::vector<Pending> pending;
-  std::vector<cudaEvent_t> pool;
-  double prof_ms[lbm::kNumKernels] = {};
-  int64_t prof_n[lbm::kNumKernels] = {};
-  cudaEvent_t open_ev = nullptr;
-  bool batch_owned = false;  // stepped only through its lbm_batch
-};
 
 struct lbm_batch {
   std::vector<lbm_ctx*> ctx;
@@ -180,7 +144,8 @@ struct lbm_batch {
   std::string err = "no error";
 };
 
-namespace {
+namespace lbm {
+namespace host {
 
 lbm_status fail(lbm_ctx* ctx, lbm_status st, const char* fmt, ...) {
   char buf[512];
@@ -192,12 +157,6 @@ lbm_status fail(lbm_ctx* ctx, lbm_status st, const char* fmt, ...) {
   else g_create_error = buf;
   return st;
 }
-
-#define LBM_CUDA(ctx, call)                                                                          \
-  do {                                                                                               \
-    cudaError_t e_ = (call);                                                                         \
-    if (e_ != cudaSuccess) return fail((ctx), LBM_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
-  } while (0)
 
 void* dalloc(lbm_ctx* c, size_t bytes) {
   bytes = (bytes + 255) & ~size_t(255);
@@ -222,7 +181,24 @@ void dfree_all(lbm_ctx* c) {
   }
   c->blocks.clear();
   c->bytes = 0;
+  adjoint_release(c);
 }
+
+lbm_status check_status(lbm_ctx* c) {
+  int st = 0;
+  LBM_CUDA(c, cudaMemcpyAsync(&st, c->dev.status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+  if (st & 1) return fail(c, LBM_EUNSTABLE, "non-finite or non-positive density or velocity in the collision");
+  if (st & 2) return fail(c, LBM_EUNSTABLE, "pseudopotential radicand <= 0 (Eq. potential) at some node");
+  return LBM_OK;
+}
+
+}  // namespace host
+}  // namespace lbm
+
+namespace {
+
+using namespace lbm::host;
 
 void hook_before(void* self, int k) {
   lbm_ctx* c = static_cast<lbm_ctx*>(self);
@@ -251,15 +227,6 @@ void hook_after(void* self, int k) {
   c->pending.push_back({k, c->open_ev, e});
 }
 
-lbm_status check_status(lbm_ctx* c) {
-  int st = 0;
-  LBM_CUDA(c, cudaMemcpyAsync(&st, c->dev.status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
-  LBM_CUDA(c, cudaStreamSynchronize(c->stream));
-  if (st & 1) return fail(c, LBM_EUNSTABLE, "non-finite or non-positive density or velocity in the collision");
-  if (st & 2) return fail(c, LBM_EUNSTABLE, "pseudopotential radicand <= 0 (Eq. potential) at some node");
-  return LBM_OK;
-}
-
 int do_export(lbm_ctx* c, int which, double* dst) {
   return c->f64 ? lbm::export_f64(c->geo, c->ph, c->dev, c->cur, c->tcur, which, dst, c->stream)
                 : lbm::export_f32(c->geo, c->ph, c->dev, c->cur, c->tcur, which, c->prm.storage, dst, c->stream);
@@ -270,6 +237,8 @@ int do_import(lbm_ctx* c, int which, const double* src) {
 }
 
 }  // namespace
+
+using namespace lbm::host;
 
 extern "C" {
 
@@ -495,8 +464,10 @@ lbm_status lbm_create(const lbm_domain* domain, const lbm_cylinder* cyl, const l
   // the wall temperature of the solid nodes when an angular profile is given
   const size_t M = (size_t)g.nx * g.ny;
   std::vector<double> wallT;
+  c->cyl.wall_dT = nullptr;  // the knots are used here only
   if (has_cyl && cyl->n_wall > 0 && cyl->wall_dT) {
     wallT.assign(M, ph.T_wall);
+    c->n_wall = cyl->n_wall;
     const double two_pi = 2.0 * std::acos(-1.0);
     for (int y = 0; y < g.ny; ++y)
       for (int x = 0; x < g.nx; ++x) {
@@ -507,6 +478,10 @@ lbm_status lbm_create(const lbm_domain* domain, const lbm_cylinder* cyl, const l
         const int k0 = ((int)fl) % cyl->n_wall, k1 = (k0 + 1) % cyl->n_wall;
         const double dlt = (1.0 - t) * cyl->wall_dT[k0] + t * cyl->wall_dT[k1];
         wallT[(size_t)y * g.nx + x] = ph.T_wall + dlt * eos.Tc;
+        c->wall_node.push_back(y * g.nx + x);
+        c->wall_k0.push_back(k0);
+        c->wall_k1.push_back(k1);
+        c->wall_t.push_back(t);
       }
   }
   const double* src[6] = {init ? init->rho : nullptr, init ? init->drho : nullptr, init ? init->ux : nullptr,
@@ -526,6 +501,10 @@ lbm_status lbm_create(const lbm_domain* domain, const lbm_cylinder* cyl, const l
   chk(cudaMemcpyAsync(d.f[1], d.f[0], 9 * N * ps, cudaMemcpyDeviceToDevice, c->stream));
   chk(cudaMemcpyAsync(d.T[1], d.T[0], N * es, cudaMemcpyDeviceToDevice, c->stream));
   chk(cudaMemcpyAsync(d.side[1], d.side[0], 3 * g.ny * es, cudaMemcpyDeviceToDevice, c->stream));
+  // the wall temperature of the solid nodes, kept for the adjoint window
+  c->wallT = dalloc(c, N * es);
+  if (c->wallT) chk(cudaMemcpyAsync(c->wallT, d.T[0], N * es, cudaMemcpyDeviceToDevice, c->stream));
+  else chk(cudaErrorMemoryAllocation);
   chk(cudaStreamSynchronize(c->stream));
   if (e != cudaSuccess) {
     std::string m = cudaGetErrorString(e);

@@ -2,6 +2,7 @@
 // stored as FP64, FP32 or shifted FP16.  psi is evaluated in double-float arithmetic by default
 // (IEEE FP64 or plain FP32 on request) and the wall heat flux is accumulated in FP64.
 #include "lbm.h"
+#include "lbm_adjoint.cuh"
 #include "lbm_kernels.cuh"
 
 namespace lbm {
@@ -59,6 +60,19 @@ int batch_step_f32(int variant, const BatchDomain* doms, const int* mp, int np, 
     case 3: return kern::batch_step_impl<float, float, kPsiDF, 16, 8>(doms, mp, np, mc, nc, me, ne, cur, tcur, step, s);
     default: return kern::batch_step_impl<float, float, kPsiDF, 8, 16>(doms, mp, np, mc, nc, me, ne, cur, tcur, step, s);
   }
+}
+
+int adjoint_step_f32(const AdjArgs<float>& a, cudaStream_t s) { return adj::adjoint_step_impl<float>(a, s); }
+int adjoint_aux_f32(int op, const Geo& g, const uint8_t* mask, const void* src, void* dst, cudaStream_t s) {
+  const dim3 blk(32, 8), grd((g.nx + 31) / 32, (g.ny + 7) / 8);
+  switch (op) {
+    case 0: adj::k_impose_wall<float><<<grd, blk, 0, s>>>(g, mask, static_cast<const float*>(src), static_cast<float*>(dst)); break;
+    case 1: adj::k_adj_wall_seed<float><<<grd, blk, 0, s>>>(g, mask, static_cast<const float*>(src), static_cast<double*>(dst)); break;
+    case 2: adj::k_dense_to_plane<float><<<grd, blk, 0, s>>>(g, static_cast<const double*>(src), static_cast<float*>(dst)); break;
+    case 3: adj::k_plane_to_dense<float><<<grd, blk, 0, s>>>(g, static_cast<const float*>(src), static_cast<double*>(dst)); break;
+    default: return -1;
+  }
+  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 
 }  // namespace lbm

@@ -142,4 +142,51 @@ int init_f32(const Geo& g, const Phys& ph, const Dev& d, const double* rho0, con
              const double* uy0, const double* T0, const double* Tw, unsigned long long seed, double amp, int storage,
              cudaStream_t s);
 
+// Arguments of the reverse step (lbm_adjoint.cuh): typed [ny][pitch] planes of one context.
+template <typename C>
+struct AdjArgs {
+  Geo g;
+  Phys ph;
+  const uint8_t* mask;
+  // forward: state entering the step and the fields of its collision
+  const C* f;     // f* (9 planes)
+  const C* T;
+  const C* side;  // [3][ny]
+  const C* rho;
+  const C* psi;
+  const C* ux;
+  const C* uy;
+  C* T1;          // stage-1 temperature (recomputed)
+  // adjoint seeds on the step's outputs, and the results on its inputs
+  const C* fb_in;
+  const C* Tb_in;
+  const C* sb_in;
+  C* fb_out;
+  C* Tb_out;
+  C* sb_out;
+  // work planes
+  C* P[8];        // sources of the transposed stencils
+  C* loc[5];      // local parts: T, u_x, u_y, lambda, rho
+  C* Tb1;         // adjoint of the stage-1 temperature
+  C* ub[2];       // adjoint of u from the energy equation
+  C* lamb;        // adjoint of lambda (stage 2)
+  C* rhob;        // adjoint of rho from the energy equation and lambda
+  C* fpb;         // adjoint of the pulled populations (9 planes, without the psi part)
+  C* fmb[2];      // adjoint of the interaction force F_m
+  C* psib;        // adjoint of psi from the consistency terms
+  C* rhopsi;      // adjoint of rho through psi
+  double* gw;     // dJ/dT_w per node (solid nodes), accumulated
+  double* uin;    // dJ/du_in per inlet row, accumulated
+  C wq;           // weight of this step's heat-flux sample in the objective
+  int do_hf;
+};
+
+// One reverse step of the time step (8 launches); returns the number of launches or -1.
+int adjoint_step_f32(const AdjArgs<float>& a, cudaStream_t s);
+int adjoint_step_f64(const AdjArgs<double>& a, cudaStream_t s);
+// Plane helpers of the adjoint: op 0 T[solid] = wallT (src wallT, dst T); op 1 gw[solid] +=
+// Tb (src Tb, dst gw doubles); op 2 dense doubles -> typed plane; op 3 typed plane -> dense.
+int adjoint_aux_f32(int op, const Geo& g, const uint8_t* mask, const void* src, void* dst, cudaStream_t s);
+int adjoint_aux_f64(int op, const Geo& g, const uint8_t* mask, const void* src, void* dst, cudaStream_t s);
+
 }  // namespace lbm

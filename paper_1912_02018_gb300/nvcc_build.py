@@ -6,6 +6,7 @@ Translation units, compiled in parallel:
   lbm_api.cu  host side of the C ABI (-ffp-contract=off so host FP64 thermodynamics
               round the same on x86-64 and aarch64)
   lbm_noalloc.cu  the allocation-free wall heat flux
+  lbm_adjoint_api.cu  host side of the adjoint window (its kernels sit in the two precision units)
 """
 from __future__ import annotations
 
@@ -30,6 +31,7 @@ UNITS = {
     "lbm_f32.cu": ["--fmad=true"],
     "lbm_api.cu": [],
     "lbm_noalloc.cu": [],
+    "lbm_adjoint_api.cu": [],
 }
 
 

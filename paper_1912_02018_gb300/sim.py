@@ -111,6 +111,7 @@ class Sim:
         N.check(L.lbm_create(C.byref(dom), C.byref(cyl), C.byref(prm), C.byref(ini), alloc_p,
                              C.c_void_p(self.stream.cuda_stream), C.byref(h)))
         self.h = h
+        self.n_wall = len(params.get("wall_dT", ()) or ())
 
     @classmethod
     def from_case(cls, case, f64=False, **kw):
@@ -132,6 +133,7 @@ class Sim:
         self.nx, self.ny, self.D = nx, ny, D
         self._owner = owner
         self._blocks = {}
+        self.n_wall = 0
         self.device = torch.cuda.current_device()
         return self
 
@@ -213,6 +215,39 @@ class Sim:
         inf = N.Info()
         self._chk(N.lib().lbm_info(self.h, C.byref(inf)))
         return {k: getattr(inf, k) for k, _ in N.Info._fields_}
+
+    # ------------------------------------------------------------------ adjoint
+    def adjoint_window(self, n: int, ckpt_every: int = 50, per_node: bool = False) -> dict:
+        """Run n steps and return J (the window's mean wall heat flux) with its gradient with
+        respect to superheat_Tc, u_in (inlet condition only), the wall_dT knots and, with
+        per_node, T_w at every solid node ([ny][nx])."""
+        knots = np.zeros(max(self.n_wall, 1))
+        dTw = np.zeros((self.ny, self.nx)) if per_node else None
+        g = N.WindowGrad()
+        if self.n_wall:
+            g.dJ_dwall_dT = knots.ctypes.data_as(C.POINTER(C.c_double))
+        if dTw is not None:
+            g.dJ_dTw = dTw.ctypes.data_as(C.POINTER(C.c_double))
+        self._chk(N.lib().lbm_adjoint_window(self.h, int(n), int(ckpt_every), C.byref(g)))
+        out = {"J": g.J, "superheat": g.dJ_dsuperheat, "u_in": g.dJ_du_in,
+               "wall_dT": knots[:self.n_wall].copy()}
+        if dTw is not None:
+            out["Tw"] = dTw
+        return out
+
+    def adjoint_step(self, fb=None, Tb=None, sb=None, q_weight: float = 0.0) -> dict:
+        """Vector-Jacobian product of one step at the current state (lbm_adjoint_step)."""
+        n = self.nx * self.ny
+        keep = [_dense(fb, 9 * n), _dense(Tb, n), _dense(sb, 3 * self.ny)]
+        fo = np.empty((9, self.ny, self.nx))
+        To = np.empty((self.ny, self.nx))
+        so = np.empty((3, self.ny))
+        dTw = np.empty((self.ny, self.nx))
+        du = C.c_double()
+        self._chk(N.lib().lbm_adjoint_step(self.h, *[a.ctypes.data if a is not None else None for a in keep],
+                                           float(q_weight), fo.ctypes.data, To.ctypes.data, so.ctypes.data,
+                                           dTw.ctypes.data, C.byref(du)))
+        return {"f": fo, "T": To, "side": so, "Tw": dTw, "u_in": du.value}
 
     # ------------------------------------------------------------------ timing
     def profile(self, enable=True):

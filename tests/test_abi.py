@@ -42,6 +42,13 @@ def test_struct_sizes_match_header_layout():
     assert C.sizeof(N.Params) == 16 * 8 + 8 + 16 + 16
     assert C.sizeof(N.Init) == 40
     assert C.sizeof(N.Info) == 14 * 8 + 4 * 8
+    assert C.sizeof(N.WindowGrad) == 3 * 8 + 2 * 8
+
+
+def test_adjoint_entry_points_reject_null_context(lib):
+    g = N.WindowGrad()
+    assert lib.lbm_adjoint_window(None, 10, 5, C.byref(g)) == N.LBM_EINVAL
+    assert lib.lbm_adjoint_step(None, None, None, None, 0.0, None, None, None, None, None) == N.LBM_EINVAL
 
 
 def _create(lib, dom, cyl, prm):
