@@ -272,7 +272,7 @@ typedef struct {
  * with lbm_step, heat-flux statistics included; T at solid nodes is first reset to T_w) and
  * return J and its gradient.  The reverse pass keeps a checkpoint every ckpt_every steps and
  * recomputes each segment from it: device memory (ckpt_every + 1 states, ckpt_every sets of
- * rho, psi, u, one state per checkpoint, ~40 work planes) is allocated on first use through
+ * rho, psi, u, one state per checkpoint, 30 work planes) is allocated on first use through
  * the context's allocator and kept for later windows.  Synchronises.
  */
 lbm_status lbm_adjoint_window(lbm_ctx *ctx, int64_t n_steps, int32_t ckpt_every, lbm_window_grad *out);

@@ -128,41 +128,36 @@ __device__ __forceinline__ C upw_coef(int k, bool pos) {
   return k == -1 ? C(-1.0 / 3.0) : k == 0 ? C(-0.5) : k == 1 ? C(1) : k == 2 ? C(-1.0 / 6.0) : C(0);
 }
 
-// Stencil parts of Eq. (energy) at (x, y) for the temperature field t.
+// Stencil parts of Eq. (energy) at a point of shared-memory tiles: temperature t (row stride
+// ts), lambda l, velocity u, v (row stride as); stencils reach 2 nodes.
 template <typename C>
 struct Parts {
   C upx, upy, gx, gy, lap, lx, ly, divu;
 };
 template <typename C>
-__device__ __forceinline__ Parts<C> energy_parts(const Args<C>& a, const C* t, int x, int y) {
-  const Geo& g = a.g;
+__device__ __forceinline__ C upwind_d(C m2, C m1, C p1, C p2, C v) {
+  return v >= C(0) ? fdiv(m2 - C(6) * m1 + C(2) * p1, C(6)) : fdiv(-C(2) * m1 + C(6) * p1 - p2, C(6));
+}
+template <typename C>
+__device__ __forceinline__ Parts<C> parts_at(const C* t, int ts, const C* l, const C* u, const C* v, int as) {
   Parts<C> P;
-  const C c = at(g, t, x, y);
-  const C ux0 = at(g, a.ux, x, y), uy0 = at(g, a.uy, x, y);
-  {
-    const C m2 = at(g, t, x - 2, y) - c, m1 = at(g, t, x - 1, y) - c, p1 = at(g, t, x + 1, y) - c,
-            p2 = at(g, t, x + 2, y) - c;
-    P.upx = ux0 >= C(0) ? fdiv(m2 - C(6) * m1 + C(2) * p1, C(6)) : fdiv(-C(2) * m1 + C(6) * p1 - p2, C(6));
-  }
-  {
-    const C m2 = at(g, t, x, y - 2) - c, m1 = at(g, t, x, y - 1) - c, p1 = at(g, t, x, y + 1) - c,
-            p2 = at(g, t, x, y + 2) - c;
-    P.upy = uy0 >= C(0) ? fdiv(m2 - C(6) * m1 + C(2) * p1, C(6)) : fdiv(-C(2) * m1 + C(6) * p1 - p2, C(6));
-  }
+  const C c = t[0];
+  P.upx = upwind_d(t[-2] - c, t[-1] - c, t[1] - c, t[2] - c, u[0]);
+  P.upy = upwind_d(t[-2 * ts] - c, t[-ts] - c, t[ts] - c, t[2 * ts] - c, v[0]);
   C gx = 0, gy = 0, lap = 0, lx = 0, ly = 0, dxux = 0, dyuy = 0;
 #pragma unroll
   for (int k = 0; k < 12; ++k) {
     const int ex = exv(k), ey = eyv(k);
     const C w = C(wiso(k));
-    const C tp = at(g, t, x + ex, y + ey), tm = at(g, t, x - ex, y - ey);
+    const C tp = t[ey * ts + ex], tm = t[-ey * ts - ex];
     gx = gx + w * (tp - tm) * C(ex);
     gy = gy + w * (tp - tm) * C(ey);
     lap = lap + w * ((tp + tm) - C(2) * c);
-    const C lp = lam_of(a.ph, at(g, a.rho, x + ex, y + ey)), lm = lam_of(a.ph, at(g, a.rho, x - ex, y - ey));
-    lx = lx + w * (lp - lm) * C(ex);
-    ly = ly + w * (lp - lm) * C(ey);
-    dxux = dxux + w * (at(g, a.ux, x + ex, y + ey) - at(g, a.ux, x - ex, y - ey)) * C(ex);
-    dyuy = dyuy + w * (at(g, a.uy, x + ex, y + ey) - at(g, a.uy, x - ex, y - ey)) * C(ey);
+    const C dl = l[ey * as + ex] - l[-ey * as - ex];
+    lx = lx + w * dl * C(ex);
+    ly = ly + w * dl * C(ey);
+    if (ex != 0) dxux = dxux + w * (u[ey * as + ex] - u[-ey * as - ex]) * C(ex);
+    if (ey != 0) dyuy = dyuy + w * (v[ey * as + ex] - v[-ey * as - ex]) * C(ey);
   }
   P.gx = gx;
   P.gy = gy;
@@ -173,145 +168,206 @@ __device__ __forceinline__ Parts<C> energy_parts(const Args<C>& a, const C* t, i
   return P;
 }
 
-// ---------------------------------------------------------------- kernels
-// Stage-1 temperature T1 = T + L(T) of the forward (Dirichlet at the wall and the inlet).
-template <typename C>
-__global__ void __launch_bounds__(256) k_adj_t1(Args<C> a) {
-  int x, y;
-  if (!node_of_thread(a.g, x, y)) return;
-  const int id = y * a.g.pitch + x;
-  const uint8_t m = a.mask[id];
-  const PhysC<C>& k = pc<C>(a.ph);
-  C t1;
-  if (m & kSolid) {
-    t1 = a.T[id];
-  } else if (!a.g.periodic_x && x == 0) {
-    t1 = k.T_sat;
-  } else {
-    const Parts<C> P = energy_parts(a, a.T, x, y);
-    const C r0 = a.rho[id], T0 = a.T[id], lam0 = lam_of(a.ph, r0);
-    const C conv = a.ux[id] * P.upx + a.uy[id] * P.upy;
-    const C diff = lam0 * P.lap + (P.lx * P.gx + P.ly * P.gy);
-    const C work = T0 * dpdT_eos(a.ph, r0, T0) * P.divu;
-    t1 = T0 + (-conv + fdiv(diff, r0 * k.c_v) - fdiv(work, r0 * k.c_v));
-  }
-  a.T1[id] = t1;
-}
-
-// Sources of the transposed stencils of L at node x, for the seed a_s on L(t)(x):
-// stage 2 (t = T1, a_s = Tb_in / 2) or stage 1 (t = T, a_s = Tb1; plus the heat-flux sample).
+// ---------------------------------------------------------------- energy adjoint (Heun stages)
+// One kernel per stage, on tiles of 32 x 16 nodes.  Stage 2 (seed Tb_in / 2 on L(T1) at the
+// interior fluid nodes) loads T, rho, lambda, u on the tile + 6, recomputes T1 on the tile + 4,
+// forms the sources of the transposed stencils on the tile + 2 and gathers them at the tile's
+// nodes: Tb1, the adjoint of T1.  Stage 1 (seed Tb1 on L(T), plus the heat-flux sample) does
+// the same from T on the tile + 4 and gives Tb_out, the adjoint of T.  Both add their parts
+// of the adjoints of u (ub), lambda (lamb) and rho (rhob).
+constexpr int kEATX = 32, kEATY = 16, kEANT = 256;
 template <typename C, int STAGE>
-__global__ void __launch_bounds__(256) k_adj_src(Args<C> a) {
-  int x, y;
-  if (!node_of_thread(a.g, x, y)) return;
-  const Geo& g = a.g;
-  const int id = y * g.pitch + x;
-  const uint8_t m = a.mask[id];
-  const PhysC<C>& k = pc<C>(a.ph);
-  if (m & kSolid) {
-    // T^{n+1} and T1 at a solid node are its wall temperature
-    a.gw[id] += (double)(STAGE == 2 ? a.Tb_in[id] : a.Tb1[id]);
-#pragma unroll
-    for (int j = 0; j < 8; ++j) a.P[j][id] = C(0);
-#pragma unroll
-    for (int j = 0; j < 5; ++j) a.loc[j][id] = C(0);
-    return;
-  }
-  const C* t = STAGE == 2 ? a.T1 : a.T;
-  C s = C(0);
-  if (interior_T(g, m, x)) s = STAGE == 2 ? C(0.5) * a.Tb_in[id] : a.Tb1[id];
-  const bool hf = STAGE == 1 && a.do_hf && (m & kNearWall);
-  if (s == C(0) && !hf) {
-#pragma unroll
-    for (int j = 0; j < 8; ++j) a.P[j][id] = C(0);
-#pragma unroll
-    for (int j = 0; j < 5; ++j) a.loc[j][id] = C(0);
-    return;
-  }
-  const Parts<C> P = energy_parts(a, t, x, y);
-  const C r0 = a.rho[id], T0 = t[id], lam0 = lam_of(a.ph, r0);
-  const C rc = r0 * k.c_v;
-  const Dl<C> dT = pr_dpdT(k, Dl<C>{r0, C(0)}, Dl<C>{T0, C(1)});
-  const Dl<C> dR = pr_dpdT(k, Dl<C>{r0, C(1)}, Dl<C>{T0, C(0)});
-  const C diff = lam0 * P.lap + (P.lx * P.gx + P.ly * P.gy);
-  const C work = T0 * dT.v * P.divu;
-  C p1 = s * fdiv(P.lx, rc), p2 = s * fdiv(P.ly, rc);
-  C llam = s * fdiv(P.lap, rc);
-  if (hf) {
-    // q = -lambda grad T . n at this boundary node (Sec. IV.B)
-    const double dx = x - g.xc, dy = y - g.yc, rr = sqrt(dx * dx + dy * dy);
-    const C nxv = C(dx / rr), nyv = C(dy / rr);
-    p1 = p1 - a.wq * lam0 * nxv;
-    p2 = p2 - a.wq * lam0 * nyv;
-    llam = llam - a.wq * (P.gx * nxv + P.gy * nyv);
-  }
-  a.P[0][id] = s * fdiv(lam0, rc);
-  a.P[1][id] = p1;
-  a.P[2][id] = p2;
-  a.P[3][id] = s * a.ux[id];
-  a.P[4][id] = s * a.uy[id];
-  a.P[5][id] = -s * fdiv(T0 * dT.v, rc);
-  a.P[6][id] = s * fdiv(P.gx, rc);
-  a.P[7][id] = s * fdiv(P.gy, rc);
-  a.loc[0][id] = -s * fdiv(P.divu, rc) * (dT.v + T0 * dT.d);
-  a.loc[1][id] = -s * P.upx;
-  a.loc[2][id] = -s * P.upy;
-  a.loc[3][id] = llam;
-  a.loc[4][id] = s * (-fdiv(diff - work, rc * r0) - fdiv(T0 * P.divu * dR.d, rc));
-}
+struct EAdjLayout {
+  static constexpr int H = STAGE == 2 ? 6 : 4;
+  static constexpr int AX = kEATX + 2 * H, AY = kEATY + 2 * H, A = AX * AY;  // loaded fields
+  static constexpr int BX = kEATX + 8, BY = kEATY + 8, B = STAGE == 2 ? BX * BY : 0;  // T1
+  static constexpr int PX = kEATX + 4, PY = kEATY + 4, PN = PX * PY;                  // sources
+  static constexpr int NN = kEATX * kEATY;
+  static constexpr size_t bytes = sizeof(C) * (5 * (size_t)A + B + 8 * (size_t)PN + 5 * (size_t)NN) + A;
+};
 
-// Transposed stencils of L: the adjoint of the temperature field the stage read, and the
-// stage's parts of the adjoints of u, lambda and rho.
 template <typename C, int STAGE>
-__global__ void __launch_bounds__(256) k_adj_gather(Args<C> a) {
-  int x, y;
-  if (!node_of_thread(a.g, x, y)) return;
+__global__ void __launch_bounds__(kEANT) k_adj_energy(Args<C> a) {
+  using Lay = EAdjLayout<C, STAGE>;
+  constexpr int H = Lay::H, AX = Lay::AX, A = Lay::A, BX = Lay::BX, PX = Lay::PX, PN = Lay::PN, NN = Lay::NN;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* sT = reinterpret_cast<C*>(smem_raw);
+  C* sR = sT + A;
+  C* sL = sR + A;
+  C* sU = sL + A;
+  C* sV = sU + A;
+  C* sT1 = sV + A;
+  C* sP = sT1 + Lay::B;
+  C* sLoc = sP + 8 * PN;
+  uint8_t* sM = reinterpret_cast<uint8_t*>(sLoc + 5 * NN);
   const Geo& g = a.g;
-  const int id = y * g.pitch + x;
-  const uint8_t m = a.mask[id];
-  C tb = C(0), ubx = C(0), uby = C(0), lb = C(0);
-  C wsum = C(0);
-#pragma unroll
-  for (int k = 0; k < 12; ++k) wsum = wsum + C(wiso(k));
-  for (int ey = -2; ey <= 2; ++ey) {
-    const int sy = wrap_y(g, y - ey);
-    for (int ex = -2; ex <= 2; ++ex) {
-      int lo, hi;
-      src_cols(g, x, ex, lo, hi);
-      const C w = C(w_of(ex, ey));
-      const C clap = (ex == 0 && ey == 0) ? C(-4) * wsum : C(2) * w;
-      for (int sx = lo; sx <= hi; ++sx) {
-        const int s = sy * g.pitch + sx;
-        tb = tb + clap * a.P[0][s];
-        if (ex != 0 || ey != 0) {
-          tb = tb + w * (C(ex) * a.P[1][s] + C(ey) * a.P[2][s]);
-          ubx = ubx + w * C(ex) * a.P[5][s];
-          uby = uby + w * C(ey) * a.P[5][s];
-          lb = lb + w * (C(ex) * a.P[6][s] + C(ey) * a.P[7][s]);
+  const PhysC<C>& k = pc<C>(a.ph);
+  const int tid = threadIdx.x;
+  const int x0 = blockIdx.x * kEATX, y0 = blockIdx.y * kEATY;
+  for (int p = tid; p < A; p += kEANT) {
+    const int id = map_y(g, y0 + p / AX - H) * g.pitch + map_x(g, x0 + p % AX - H);
+    const C r = a.rho[id];
+    sT[p] = a.T[id];
+    sR[p] = r;
+    sL[p] = lam_of(a.ph, r);
+    sU[p] = a.ux[id];
+    sV[p] = a.uy[id];
+    sM[p] = a.mask[id];
+  }
+  __syncthreads();
+  if constexpr (STAGE == 2) {
+    // T1 = T + L(T) with the forward's Dirichlet values; columns past a non-periodic edge
+    // take the edge column's value (the forward's zero-gradient ghost)
+    for (int p = tid; p < Lay::B; p += kEANT) {
+      const int bx = p % BX, by = p / BX, gx = x0 + bx - 4;
+      const int ai = (by + 2) * AX + bx + 2;
+      C t1 = C(0);
+      if (g.periodic_x || (gx >= 0 && gx < g.nx)) {
+        if (sM[ai] & kSolid) {
+          t1 = sT[ai];
+        } else if (!g.periodic_x && gx == 0) {
+          t1 = k.T_sat;
+        } else {
+          const Parts<C> P = parts_at(&sT[ai], AX, &sL[ai], &sU[ai], &sV[ai], AX);
+          const C r0 = sR[ai], T0 = sT[ai];
+          const C conv = sU[ai] * P.upx + sV[ai] * P.upy;
+          const C diff = sL[ai] * P.lap + (P.lx * P.gx + P.ly * P.gy);
+          const C work = T0 * dpdT_eos(a.ph, r0, T0) * P.divu;
+          t1 = T0 + (-conv + fdiv(diff, r0 * k.c_v) - fdiv(work, r0 * k.c_v));
         }
-        if (ey == 0) tb = tb - upw_coef<C>(ex, a.ux[s] >= C(0)) * a.P[3][s];
-        if (ex == 0) tb = tb - upw_coef<C>(ey, a.uy[s] >= C(0)) * a.P[4][s];
       }
+      sT1[p] = t1;
+    }
+    __syncthreads();
+    if (!g.periodic_x && (x0 < 4 || x0 + kEATX + 4 > g.nx)) {
+      for (int p = tid; p < Lay::B; p += kEANT) {
+        const int bx = p % BX, by = p / BX, gx = x0 + bx - 4;
+        if (gx < 0 || gx >= g.nx) sT1[p] = sT1[by * BX + (map_x(g, gx) - x0 + 4)];
+      }
+      __syncthreads();
     }
   }
-  const bool in = interior_T(g, m, x);
-  tb = tb + a.loc[0][id];
-  ubx = ubx + a.loc[1][id];
-  uby = uby + a.loc[2][id];
-  lb = lb + a.loc[3][id];
-  if (STAGE == 2) {
-    a.Tb1[id] = (in ? C(0.5) * a.Tb_in[id] : C(0)) + tb;
-    a.ub[0][id] = ubx;
-    a.ub[1][id] = uby;
-    a.lamb[id] = lb;
-    a.rhob[id] = a.loc[4][id];
-  } else {
-    a.Tb_out[id] = (in ? C(0.5) * a.Tb_in[id] + a.Tb1[id] : C(0)) + tb;
-    a.ub[0][id] = a.ub[0][id] + ubx;
-    a.ub[1][id] = a.ub[1][id] + uby;
-    C rb = a.rhob[id] + a.loc[4][id];
-    if (!(m & kSolid)) rb = rb + dlam(a.ph, a.rho[id]) * (a.lamb[id] + lb);
-    a.rhob[id] = rb;
+  // sources of the transposed stencils on the tile + 2; local parts of the tile's nodes
+  for (int p = tid; p < PN; p += kEANT) {
+    const int px = p % PX, py = p / PX;
+    const int gx = x0 + px - 2, gy = y0 + py - 2;
+    const int ai = (py + H - 2) * AX + px + H - 2;
+    const bool own = px >= 2 && px < kEATX + 2 && py >= 2 && py < kEATY + 2;
+    C Pv[8], Lv[5];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) Pv[j] = C(0);
+#pragma unroll
+    for (int j = 0; j < 5; ++j) Lv[j] = C(0);
+    const uint8_t m = sM[ai];
+    if ((g.periodic_x || (gx >= 0 && gx < g.nx)) && !(m & kSolid)) {
+      const int mx = map_x(g, gx);
+      const int gid = map_y(g, gy) * g.pitch + mx;
+      C s = C(0);
+      if (g.periodic_x || mx != 0) s = STAGE == 2 ? C(0.5) * a.Tb_in[gid] : a.Tb1[gid];
+      const bool hf = STAGE == 1 && a.do_hf && (m & kNearWall);
+      if (s != C(0) || hf) {
+        const C* t = STAGE == 2 ? &sT1[(py + 2) * BX + px + 2] : &sT[ai];
+        const int ts = STAGE == 2 ? BX : AX;
+        const Parts<C> P = parts_at(t, ts, &sL[ai], &sU[ai], &sV[ai], AX);
+        const C r0 = sR[ai], T0 = t[0], lam0 = sL[ai];
+        const C rc = r0 * k.c_v;
+        const Dl<C> dT = pr_dpdT(k, Dl<C>{r0, C(0)}, Dl<C>{T0, C(1)});
+        const Dl<C> dR = pr_dpdT(k, Dl<C>{r0, C(1)}, Dl<C>{T0, C(0)});
+        const C diff = lam0 * P.lap + (P.lx * P.gx + P.ly * P.gy);
+        const C work = T0 * dT.v * P.divu;
+        C p1 = s * fdiv(P.lx, rc), p2 = s * fdiv(P.ly, rc);
+        C llam = s * fdiv(P.lap, rc);
+        if (hf) {
+          // q = -lambda grad T . n at this boundary node (Sec. IV.B)
+          const double dx = mx - g.xc, dy = map_y(g, gy) - g.yc, rr = sqrt(dx * dx + dy * dy);
+          const C nxv = C(dx / rr), nyv = C(dy / rr);
+          p1 = p1 - a.wq * lam0 * nxv;
+          p2 = p2 - a.wq * lam0 * nyv;
+          llam = llam - a.wq * (P.gx * nxv + P.gy * nyv);
+        }
+        Pv[0] = s * fdiv(lam0, rc);
+        Pv[1] = p1;
+        Pv[2] = p2;
+        Pv[3] = s * sU[ai];
+        Pv[4] = s * sV[ai];
+        Pv[5] = -s * fdiv(T0 * dT.v, rc);
+        Pv[6] = s * fdiv(P.gx, rc);
+        Pv[7] = s * fdiv(P.gy, rc);
+        Lv[0] = -s * fdiv(P.divu, rc) * (dT.v + T0 * dT.d);
+        Lv[1] = -s * P.upx;
+        Lv[2] = -s * P.upy;
+        Lv[3] = llam;
+        Lv[4] = s * (-fdiv(diff - work, rc * r0) - fdiv(T0 * P.divu * dR.d, rc));
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) sP[j * PN + p] = Pv[j];
+    if (own) {
+#pragma unroll
+      for (int j = 0; j < 5; ++j) sLoc[j * NN + (py - 2) * kEATX + px - 2] = Lv[j];
+    }
+  }
+  __syncthreads();
+  // gather: every source whose stencil reads the node, clamped columns included
+  C wsum = C(0);
+#pragma unroll
+  for (int kk = 0; kk < 12; ++kk) wsum = wsum + C(wiso(kk));
+  for (int q = tid; q < NN; q += kEANT) {
+    const int tx = q % kEATX, ty = q / kEATX;
+    const int x = x0 + tx, y = y0 + ty;
+    if (x >= g.nx || y >= g.ny) continue;
+    const int id = y * g.pitch + x;
+    const uint8_t m = sM[(ty + H) * AX + tx + H];
+    C tb = C(0), ubx = C(0), uby = C(0), lb = C(0);
+#pragma unroll
+    for (int ey = -2; ey <= 2; ++ey) {
+#pragma unroll
+      for (int ex = -2; ex <= 2; ++ex) {
+        const C w = C(w_of(ex, ey));
+        const C clap = (ex == 0 && ey == 0) ? C(-4) * wsum : C(2) * w;
+        int lo, hi;
+        if (g.periodic_x) {
+          lo = hi = x - ex;
+        } else {
+          src_cols(g, x, ex, lo, hi);
+        }
+        const int prow = (ty + 2 - ey) * PX - x0 + 2;
+        const int arow = (ty + H - ey) * AX - x0 + H;
+        for (int sx = lo; sx <= hi; ++sx) {
+          const int pp = prow + sx;
+          tb = tb + clap * sP[pp];
+          if (ex != 0 || ey != 0) {
+            tb = tb + w * (C(ex) * sP[PN + pp] + C(ey) * sP[2 * PN + pp]);
+            ubx = ubx + w * C(ex) * sP[5 * PN + pp];
+            uby = uby + w * C(ey) * sP[5 * PN + pp];
+            lb = lb + w * (C(ex) * sP[6 * PN + pp] + C(ey) * sP[7 * PN + pp]);
+          }
+          if (ey == 0) tb = tb - upw_coef<C>(ex, sU[arow + sx] >= C(0)) * sP[3 * PN + pp];
+          if (ex == 0) tb = tb - upw_coef<C>(ey, sV[arow + sx] >= C(0)) * sP[4 * PN + pp];
+        }
+      }
+    }
+    const bool in = interior_T(g, m, x);
+    tb = tb + sLoc[q];
+    ubx = ubx + sLoc[NN + q];
+    uby = uby + sLoc[2 * NN + q];
+    lb = lb + sLoc[3 * NN + q];
+    if (STAGE == 2) {
+      if (m & kSolid) a.gw[id] += (double)a.Tb_in[id];  // T^{n+1} at a solid node is T_w
+      a.Tb1[id] = (in ? C(0.5) * a.Tb_in[id] : C(0)) + tb;
+      a.ub[0][id] = ubx;
+      a.ub[1][id] = uby;
+      a.lamb[id] = lb;
+      a.rhob[id] = sLoc[4 * NN + q];
+    } else {
+      if (m & kSolid) a.gw[id] += (double)a.Tb1[id];  // so is T1
+      a.Tb_out[id] = (in ? C(0.5) * a.Tb_in[id] + a.Tb1[id] : C(0)) + tb;
+      a.ub[0][id] = a.ub[0][id] + ubx;
+      a.ub[1][id] = a.ub[1][id] + uby;
+      C rb = a.rhob[id] + sLoc[4 * NN + q];
+      if (!(m & kSolid)) rb = rb + dlam(a.ph, sR[(ty + H) * AX + tx + H]) * (a.lamb[id] + lb);
+      a.rhob[id] = rb;
+    }
   }
 }
 
@@ -452,8 +508,11 @@ __global__ void __launch_bounds__(256) k_adj_collide(Args<C> a) {
   a.psib[id] = psib;
 }
 
-// Adjoint of the interaction force (transposed psi stencil) and of psi(rho, T): the psi part
-// of the rho adjoint, and the psi part added to the adjoint of T.
+// Adjoint of the interaction force (transposed psi stencil) and of psi(rho, T): the psi part of
+// the rho adjoint goes into the node's pulled-population adjoints (rho = sum of them), the
+// psi part of the T adjoint into Tb_out.  Then, at the Zou-He inlet, the adjoints of the
+// unknowns f1, f5, f7 are folded into their knowns (and d/du_in is accumulated), so that fpb
+// holds the adjoint of every value the pull read.
 template <typename C>
 __global__ void __launch_bounds__(256) k_adj_force(Args<C> a) {
   int x, y;
@@ -462,74 +521,73 @@ __global__ void __launch_bounds__(256) k_adj_force(Args<C> a) {
   const int id = y * g.pitch + x;
   const uint8_t m = a.mask[id];
   const PhysC<C>& k = pc<C>(a.ph);
-  if (k.G == C(0)) {
-    a.rhopsi[id] = C(0);
-    return;
-  }
   const C cs2 = C(1.0 / 3.0), gc = -k.G * cs2;
-  C pb = a.psib[id];
-  if (!(m & kSolid)) {
-    C sx = C(0), sy = C(0);
+  C rp = C(0);
+  if (k.G != C(0)) {
+    C pb = a.psib[id];
+    if (!(m & kSolid)) {
+      C sx = C(0), sy = C(0);
 #pragma unroll
-    for (int kk = 0; kk < 12; ++kk) {
-      const int ex = exv(kk), ey = eyv(kk);
-      const C d = at(g, a.psi, x + ex, y + ey) - at(g, a.psi, x - ex, y - ey);
-      sx = sx + C(wiso(kk)) * d * C(ex);
-      sy = sy + C(wiso(kk)) * d * C(ey);
+      for (int kk = 0; kk < 12; ++kk) {
+        const int ex = exv(kk), ey = eyv(kk);
+        const C d = at(g, a.psi, x + ex, y + ey) - at(g, a.psi, x - ex, y - ey);
+        sx = sx + C(wiso(kk)) * d * C(ex);
+        sy = sy + C(wiso(kk)) * d * C(ey);
+      }
+      pb = pb + gc * (a.fmb[0][id] * sx + a.fmb[1][id] * sy);
     }
-    pb = pb + gc * (a.fmb[0][id] * sx + a.fmb[1][id] * sy);
-  }
-  for (int ey = -2; ey <= 2; ++ey) {
-    const int sy = wrap_y(g, y - ey);
-    for (int ex = -2; ex <= 2; ++ex) {
-      if (ex == 0 && ey == 0) continue;
-      int lo, hi;
-      src_cols(g, x, ex, lo, hi);
-      const C w = C(w_of(ex, ey));
-      for (int sx = lo; sx <= hi; ++sx) {
-        const int s = sy * g.pitch + sx;
-        pb = pb + gc * a.psi[s] * w * (C(ex) * a.fmb[0][s] + C(ey) * a.fmb[1][s]);
+#pragma unroll
+    for (int ey = -2; ey <= 2; ++ey) {
+      const int sy = wrap_y(g, y - ey);
+#pragma unroll
+      for (int ex = -2; ex <= 2; ++ex) {
+        if (ex == 0 && ey == 0) continue;
+        int lo, hi;
+        src_cols(g, x, ex, lo, hi);
+        const C w = C(w_of(ex, ey));
+        for (int sx = lo; sx <= hi; ++sx) {
+          const int s = sy * g.pitch + sx;
+          pb = pb + gc * a.psi[s] * w * (C(ex) * a.fmb[0][s] + C(ey) * a.fmb[1][s]);
+        }
       }
     }
+    // psi = sqrt(rad), rad = k2 (p - rho cs^2), k2 = 2 / (G cs^2)
+    const C r0 = a.rho[id], T0 = a.T[id], psi0 = a.psi[id];
+    const C k2 = fdiv(C(2), k.G * cs2);
+    const C dpr = pr_p(k, Dl<C>{r0, C(1)}, Dl<C>{T0, C(0)}).d;
+    const C dpt = dpdT_eos(a.ph, r0, T0);
+    const C inv2psi = fdiv(C(1), C(2) * psi0);
+    if (!(m & kSolid)) rp = pb * k2 * (dpr - cs2) * inv2psi;
+    a.Tb_out[id] = a.Tb_out[id] + pb * k2 * dpt * inv2psi;
   }
-  // psi = sqrt(rad), rad = k2 (p - rho cs^2), k2 = 2 / (G cs^2)
-  const C r0 = a.rho[id], T0 = a.T[id], psi0 = a.psi[id];
-  const C k2 = fdiv(C(2), k.G * cs2);
-  const C dpr = pr_p(k, Dl<C>{r0, C(1)}, Dl<C>{T0, C(0)}).d;
-  const C dpt = pr_dpdT(k, Dl<C>{r0, C(0)}, Dl<C>{T0, C(0)}).v;
-  const C inv2psi = fdiv(C(1), C(2) * psi0);
-  a.rhopsi[id] = (m & kSolid) ? C(0) : pb * k2 * (dpr - cs2) * inv2psi;
-  a.Tb_out[id] = a.Tb_out[id] + pb * k2 * dpt * inv2psi;
-}
-
-// Adjoint of pulled value i at node z (psi part of rho included; the Zou-He inlet's
-// unknowns folded into its knowns; the outlet's replaced values carry nothing here).
-template <typename C>
-__device__ __forceinline__ C eff_fbar(const Args<C>& a, int zx, int zy, int i) {
-  const Geo& g = a.g;
-  const int id = zy * g.pitch + zx;
-  const C rp = a.rhopsi[id];
-  if (!g.periodic_x && zx == g.nx - 1 && (i == 2 || i == 6 || i == 8)) return C(0);
-  if (!g.periodic_x && zx == 0) {
-    if (i == 1 || i == 5 || i == 7) return C(0);
-    const C u = pc<C>(a.ph).u_in;
-    const C f1 = a.fpb[1 * g.plane + id] + rp, f5 = a.fpb[5 * g.plane + id] + rp, f7 = a.fpb[7 * g.plane + id] + rp;
-    const C rb = u * (fdiv(C(2) * f1, C(3)) + fdiv(f5 + f7, C(6)));
-    const C r1 = fdiv(rb, C(1) - u);
-    C e = a.fpb[i * g.plane + id] + rp;
-    if (i == 0) e = e + r1;
-    else if (i == 3) e = e + r1 - C(0.5) * f5 + C(0.5) * f7;
-    else if (i == 4) e = e + r1 + C(0.5) * f5 - C(0.5) * f7;
-    else if (i == 2) e = e + C(2) * r1 + f1;
-    else if (i == 6) e = e + C(2) * r1 + f5;
-    else e = e + C(2) * r1 + f7;  // i == 8
-    return e;
+  if (m & kSolid) return;
+  C fb[9];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) fb[i] = a.fpb[i * g.plane + id] + rp;
+  if (!g.periodic_x && x == 0) {
+    // Zou-He: f1 = f2 + (2/3) rho_in u, f5 = f6 - (f3 - f4)/2 + rho_in u / 6, f7 = f8 + (f3 - f4)/2
+    // + rho_in u / 6, rho_in = (f0 + f3 + f4 + 2 (f2 + f6 + f8)) / (1 - u)
+    const C u = k.u_in;
+    const C bsum = fdiv(C(2) * fb[1], C(3)) + fdiv(fb[5] + fb[7], C(6));
+    const C r1 = fdiv(u * bsum, C(1) - u);
+    C fo[9];
+    pull_node<C, C>(g, a.ph, a.f, a.mask, a.side, nullptr, x, y, m, fo);
+    const C rho_in = fdiv(fo[0] + fo[3] + fo[4] + C(2) * (fo[2] + fo[6] + fo[8]), C(1) - u);
+    a.uin[y] += (double)bsum * (double)rho_in / (1.0 - (double)u);
+    fb[0] = fb[0] + r1;
+    fb[3] = fb[3] + r1 - C(0.5) * fb[5] + C(0.5) * fb[7];
+    fb[4] = fb[4] + r1 + C(0.5) * fb[5] - C(0.5) * fb[7];
+    fb[2] = fb[2] + C(2) * r1 + fb[1];
+    fb[6] = fb[6] + C(2) * r1 + fb[5];
+    fb[8] = fb[8] + C(2) * r1 + fb[7];
+    fb[1] = fb[5] = fb[7] = C(0);
   }
-  return a.fpb[i * g.plane + id] + rp;
+#pragma unroll
+  for (int i = 0; i < 9; ++i) a.fpb[i * g.plane + id] = fb[i];
 }
 
 // Transposed pull-streaming (a push written as a gather): the adjoint of f* entering the
-// step, of the outlet's side values, and the inlet-speed derivative of the Zou-He rows.
+// step and of the outlet's side values, from the adjoints of the pulled values (fpb).
 template <typename C>
 __global__ void __launch_bounds__(256) k_adj_pull(Args<C> a) {
   int x, y;
@@ -544,25 +602,13 @@ __global__ void __launch_bounds__(256) k_adj_pull(Args<C> a) {
     for (int j = 0; j < 3; ++j) {
       const int i = j == 0 ? 2 : (j == 1 ? 6 : 8);
       const C sb = a.sb_in[j * g.ny + y];
-      a.sb_out[j * g.ny + y] =
-          (m & kSolid) ? sb : fdiv(a.fpb[i * g.plane + id] + a.rhopsi[id] + sb, C(1) + k.U_out);
+      a.sb_out[j * g.ny + y] = (m & kSolid) ? sb : fdiv(a.fpb[i * g.plane + id] + sb, C(1) + k.U_out);
     }
   }
   if (m & kSolid) {
 #pragma unroll
     for (int i = 0; i < 9; ++i) a.fb_out[i * g.plane + id] = C(0);
     return;
-  }
-  if (!g.periodic_x && x == 0) {
-    // Zou-He: d/du_in of f1, f5, f7 through rho_in u and rho_in = (...)/(1 - u)
-    C fo[9];
-    pull_node<C, C>(g, a.ph, a.f, a.mask, a.side, nullptr, x, y, m, fo);
-    const C u = k.u_in;
-    const C rho_in = fdiv(fo[0] + fo[3] + fo[4] + C(2) * (fo[2] + fo[6] + fo[8]), C(1) - u);
-    const C rp = a.rhopsi[id];
-    const C bsum = fdiv(C(2) * (a.fpb[1 * g.plane + id] + rp), C(3)) +
-                   fdiv((a.fpb[5 * g.plane + id] + rp) + (a.fpb[7 * g.plane + id] + rp), C(6));
-    a.uin[y] += (double)bsum * (double)rho_in / (1.0 - (double)u);
   }
 #pragma unroll
   for (int i = 0; i < 9; ++i) {
@@ -574,13 +620,13 @@ __global__ void __launch_bounds__(256) k_adj_pull(Args<C> a) {
     const int zy = wrap_y(g, y + cy);
     if (g.periodic_x) zx = zx < 0 ? zx + g.nx : (zx >= g.nx ? zx - g.nx : zx);
     if (zx >= 0 && zx < g.nx && !(a.mask[zy * g.pitch + zx] & kSolid)) {
-      acc = acc + eff_fbar(a, zx, zy, i);
+      acc = acc + a.fpb[i * g.plane + zy * g.pitch + zx];
       int wx = zx + cx;
       const int wy = wrap_y(g, zy + cy);
       if (g.periodic_x) wx = wx < 0 ? wx + g.nx : (wx >= g.nx ? wx - g.nx : wx);
       if (i != 0 && wx >= 0 && wx < g.nx && (a.mask[wy * g.pitch + wx] & kSolid)) {
         const C qz = C(link_fraction(g, zx, zy, cx, cy));
-        if (qz < C(0.5)) acc = acc + (C(1) - C(2) * qz) * eff_fbar(a, zx, zy, oppv(i));
+        if (qz < C(0.5)) acc = acc + (C(1) - C(2) * qz) * a.fpb[oppv(i) * g.plane + zy * g.pitch + zx];
       }
     }
     if (i != 0) {
@@ -602,14 +648,14 @@ __global__ void __launch_bounds__(256) k_adj_pull(Args<C> a) {
         } else {
           ca = fdiv(C(1), C(2) * qj);
         }
-        acc = acc + ca * eff_fbar(a, x, y, j);
+        acc = acc + ca * a.fpb[j * g.plane + id];
       }
       int tx = x - cx;
       const int ty = wrap_y(g, y - cy);
       if (g.periodic_x) tx = tx < 0 ? tx + g.nx : (tx >= g.nx ? tx - g.nx : tx);
       if (tx >= 0 && tx < g.nx && (a.mask[ty * g.pitch + tx] & kSolid)) {
         const C qi = C(link_fraction(g, x, y, -cx, -cy));
-        if (!(qi < C(0.5))) acc = acc + fdiv(C(2) * qi - C(1), C(2) * qi) * eff_fbar(a, x, y, i);
+        if (!(qi < C(0.5))) acc = acc + fdiv(C(2) * qi - C(1), C(2) * qi) * a.fpb[i * g.plane + id];
       }
     }
     if (!g.periodic_x && x == g.nx - 1 && (i == 2 || i == 6 || i == 8)) {
@@ -618,7 +664,7 @@ __global__ void __launch_bounds__(256) k_adj_pull(Args<C> a) {
       const int yo = wrap_y(g, y + cy);
       const int oid = yo * g.pitch + x;
       if (!(a.mask[oid] & kSolid)) {
-        const C vb = a.fpb[i * g.plane + oid] + a.rhopsi[oid] + a.sb_in[jo * g.ny + yo];
+        const C vb = a.fpb[i * g.plane + oid] + a.sb_in[jo * g.ny + yo];
         acc = acc + fdiv(k.U_out * vb, C(1) + k.U_out);
       }
     }
@@ -655,19 +701,27 @@ __global__ void __launch_bounds__(256) k_plane_to_dense(Geo g, const C* src, dou
   dst[y * g.nx + x] = (double)src[y * g.pitch + x];
 }
 
-// One reverse step (8 launches).  Returns the number of launches or -1.
+// One reverse step (5 launches).  Returns the number of launches or -1.
+template <typename C, int STAGE>
+void launch_energy_adj(const Args<C>& a, cudaStream_t s) {
+  using Lay = EAdjLayout<C, STAGE>;
+  static bool attr = false;  // one attribute call per instantiation (the size is a constant)
+  if (!attr) {
+    cudaFuncSetAttribute(k_adj_energy<C, STAGE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Lay::bytes);
+    attr = true;
+  }
+  const dim3 grd((a.g.nx + kEATX - 1) / kEATX, (a.g.ny + kEATY - 1) / kEATY);
+  k_adj_energy<C, STAGE><<<grd, kEANT, Lay::bytes, s>>>(a);
+}
 template <typename C>
 int adjoint_step_impl(const Args<C>& a, cudaStream_t s) {
   const dim3 blk(32, 8), grd((a.g.nx + 31) / 32, (a.g.ny + 7) / 8);
-  k_adj_t1<C><<<grd, blk, 0, s>>>(a);
-  k_adj_src<C, 2><<<grd, blk, 0, s>>>(a);
-  k_adj_gather<C, 2><<<grd, blk, 0, s>>>(a);
-  k_adj_src<C, 1><<<grd, blk, 0, s>>>(a);
-  k_adj_gather<C, 1><<<grd, blk, 0, s>>>(a);
+  launch_energy_adj<C, 2>(a, s);
+  launch_energy_adj<C, 1>(a, s);
   k_adj_collide<C><<<grd, blk, 0, s>>>(a);
   k_adj_force<C><<<grd, blk, 0, s>>>(a);
   k_adj_pull<C><<<grd, blk, 0, s>>>(a);
-  return cudaPeekAtLastError() == cudaSuccess ? 8 : -1;
+  return cudaPeekAtLastError() == cudaSuccess ? 5 : -1;
 }
 
 }  // namespace adj

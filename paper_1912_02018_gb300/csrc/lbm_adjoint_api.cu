@@ -7,7 +7,7 @@
 // pass takes the segments last to first: it recomputes the segment from its checkpoint into
 // K + 1 state slots (keeping rho, psi and u of every collision), then runs the reverse steps
 // last to first.  Memory: (K + 1) states, K sets of collision fields, one state per
-// checkpoint and about 40 adjoint work planes.
+// checkpoint and 30 adjoint work planes.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -27,8 +27,8 @@ struct lbm_adjoint_work {
   std::vector<void*> arho, apsi, aux, auy;  // K sets of collision fields
   std::vector<void*> cf, cT, cside;         // nseg checkpoints
   void *fb[2] = {}, *Tb[2] = {}, *sb[2] = {};
-  void *T1 = nullptr, *P[8] = {}, *loc[5] = {}, *Tb1 = nullptr, *ub[2] = {}, *lamb = nullptr, *rhob = nullptr;
-  void *fpb = nullptr, *fmb[2] = {}, *psib = nullptr, *rhopsi = nullptr;
+  void *Tb1 = nullptr, *ub[2] = {}, *lamb = nullptr, *rhob = nullptr;
+  void *fpb = nullptr, *fmb[2] = {}, *psib = nullptr;
   double *gw = nullptr, *uin = nullptr, *hf = nullptr;
 };
 
@@ -86,15 +86,11 @@ lbm_status prepare(lbm_ctx* c, int K, int nseg) {
     w->ub[k] = A(plane);
     w->fmb[k] = A(plane);
   }
-  w->T1 = A(plane);
-  for (auto& p : w->P) p = A(plane);
-  for (auto& p : w->loc) p = A(plane);
   w->Tb1 = A(plane);
   w->lamb = A(plane);
   w->rhob = A(plane);
   w->fpb = A(fs);
   w->psib = A(plane);
-  w->rhopsi = A(plane);
   w->gw = static_cast<double*>(A((size_t)c->geo.plane * sizeof(double)));
   w->uin = static_cast<double*>(A((size_t)c->geo.ny * sizeof(double)));
   w->hf = static_cast<double*>(A(4 * sizeof(double)));
@@ -139,15 +135,12 @@ lbm::AdjArgs<C> make_args(lbm_ctx* c, lbm_adjoint_work* w, int j, int ping, doub
   a.psi = static_cast<const C*>(w->apsi[j]);
   a.ux = static_cast<const C*>(w->aux[j]);
   a.uy = static_cast<const C*>(w->auy[j]);
-  a.T1 = static_cast<C*>(w->T1);
   a.fb_in = static_cast<const C*>(w->fb[ping]);
   a.Tb_in = static_cast<const C*>(w->Tb[ping]);
   a.sb_in = static_cast<const C*>(w->sb[ping]);
   a.fb_out = static_cast<C*>(w->fb[ping ^ 1]);
   a.Tb_out = static_cast<C*>(w->Tb[ping ^ 1]);
   a.sb_out = static_cast<C*>(w->sb[ping ^ 1]);
-  for (int k = 0; k < 8; ++k) a.P[k] = static_cast<C*>(w->P[k]);
-  for (int k = 0; k < 5; ++k) a.loc[k] = static_cast<C*>(w->loc[k]);
   a.Tb1 = static_cast<C*>(w->Tb1);
   a.ub[0] = static_cast<C*>(w->ub[0]);
   a.ub[1] = static_cast<C*>(w->ub[1]);
@@ -157,7 +150,6 @@ lbm::AdjArgs<C> make_args(lbm_ctx* c, lbm_adjoint_work* w, int j, int ping, doub
   a.fmb[0] = static_cast<C*>(w->fmb[0]);
   a.fmb[1] = static_cast<C*>(w->fmb[1]);
   a.psib = static_cast<C*>(w->psib);
-  a.rhopsi = static_cast<C*>(w->rhopsi);
   a.gw = w->gw;
   a.uin = w->uin;
   a.wq = (C)wq;
@@ -361,7 +353,7 @@ lbm_status lbm_adjoint_window(lbm_ctx* c, int64_t n, int32_t ckpt_every, lbm_win
       if (reverse_slot(c, w, j, ping, wq) < 0) return fail(c, LBM_ECUDA, "reverse step failed");
       ping ^= 1;
     }
-    c->launches += 11 * (int64_t)len;
+    c->launches += 8 * (int64_t)len;
   }
   if (aux(c, 1, w->Tb[ping], w->gw) < 0) return fail(c, LBM_ECUDA, "wall seed failed");
   std::vector<double> gw;

@@ -156,7 +156,6 @@ struct AdjArgs {
   const C* psi;
   const C* ux;
   const C* uy;
-  C* T1;          // stage-1 temperature (recomputed)
   // adjoint seeds on the step's outputs, and the results on its inputs
   const C* fb_in;
   const C* Tb_in;
@@ -165,16 +164,13 @@ struct AdjArgs {
   C* Tb_out;
   C* sb_out;
   // work planes
-  C* P[8];        // sources of the transposed stencils
-  C* loc[5];      // local parts: T, u_x, u_y, lambda, rho
   C* Tb1;         // adjoint of the stage-1 temperature
   C* ub[2];       // adjoint of u from the energy equation
   C* lamb;        // adjoint of lambda (stage 2)
   C* rhob;        // adjoint of rho from the energy equation and lambda
-  C* fpb;         // adjoint of the pulled populations (9 planes, without the psi part)
+  C* fpb;         // adjoint of the pulled populations (9 planes)
   C* fmb[2];      // adjoint of the interaction force F_m
   C* psib;        // adjoint of psi from the consistency terms
-  C* rhopsi;      // adjoint of rho through psi
   double* gw;     // dJ/dT_w per node (solid nodes), accumulated
   double* uin;    // dJ/du_in per inlet row, accumulated
   C wq;           // weight of this step's heat-flux sample in the objective

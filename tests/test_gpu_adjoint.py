@@ -199,3 +199,39 @@ def test_torch_autograd_function_gives_the_window_gradient(sub_case):
     assert float(sh.grad) == pytest.approx(3.0 * g["superheat"], rel=1e-14)
     assert float(ui.grad) == pytest.approx(3.0 * g["u_in"], rel=1e-14)
     assert np.allclose(kn.grad.numpy(), 3.0 * g["wall_dT"], rtol=1e-14, atol=0)
+
+
+def test_full_size_window_512x256_against_central_differences():
+    # the adjoint workload: 512 x 256, D = 32, Re = 300, 200 knots, a 500-step window checkpointed
+    # every 50 steps from the state after a 2000-step spin-up; FP64 adjoint against central
+    # differences (h = 1e-4) of the FP64 forward, and the FP32 adjoint against the FP64 one
+    from paper_1912_02018_gb300 import Sim
+
+    case = _fixed(si.ADJOINT.replace(wall_dT=tuple(0.01 * si.uniform_pm1(9, 200))))
+    state = _spun_up(case, 2000)
+    nw = 500
+    out = {}
+    for f64 in (True, False):
+        sim = Sim.from_case(case, f64=f64)
+        sim.set_state(*state)
+        out[f64] = sim.adjoint_window(nw, ckpt_every=50)
+        sim.close()
+    got = out[True]
+    h = 1e-4
+    checks = {"superheat": ("superheat_Tc", case.superheat_Tc), "u_in": ("u_in", case.u_in)}
+    for key, (field, v) in checks.items():
+        fd = (_window_J(case.replace(**{field: v + h}), state, nw) -
+              _window_J(case.replace(**{field: v - h}), state, nw)) / (2 * h)
+        assert got[key] == pytest.approx(fd, rel=1e-4), key
+    kn = np.array(case.wall_dT)
+    for k in np.argsort(-np.abs(got["wall_dT"]))[:3]:
+        p, m = kn.copy(), kn.copy()
+        p[k] += h
+        m[k] -= h
+        fd = (_window_J(case.replace(wall_dT=tuple(p)), state, nw) -
+              _window_J(case.replace(wall_dT=tuple(m)), state, nw)) / (2 * h)
+        assert got["wall_dT"][k] == pytest.approx(fd, rel=1e-4), k
+    a = out[False]
+    errs = {k: abs(a[k] - got[k]) / abs(got[k]) for k in ("J", "superheat", "u_in")}
+    errs["wall_dT"] = _rel(a["wall_dT"], got["wall_dT"])
+    assert max(errs.values()) < 1e-2, errs
