@@ -279,8 +279,8 @@ __global__ void __launch_bounds__(kEANT) k_adj_energy(Args<C> a) {
         C llam = s * fdiv(P.lap, rc);
         if (hf) {
           // q = -lambda grad T . n at this boundary node (Sec. IV.B)
-          const double dx = mx - g.xc, dy = map_y(g, gy) - g.yc, rr = sqrt(dx * dx + dy * dy);
-          const C nxv = C(dx / rr), nyv = C(dy / rr);
+          const double* nv = &g.wall_n[2 * g.wall_idx[gid]];
+          const C nxv = C(nv[0]), nyv = C(nv[1]);
           p1 = p1 - a.wq * lam0 * nxv;
           p2 = p2 - a.wq * lam0 * nyv;
           llam = llam - a.wq * (P.gx * nxv + P.gy * nyv);
@@ -515,44 +515,57 @@ __global__ void __launch_bounds__(256) k_adj_collide(Args<C> a) {
 // holds the adjoint of every value the pull read.
 template <typename C>
 __global__ void __launch_bounds__(256) k_adj_force(Args<C> a) {
-  int x, y;
-  if (!node_of_thread(a.g, x, y)) return;
+  constexpr int HX = 36, HY = 12;  // 32 x 8 tile + 2 nodes
+  __shared__ C sPsi[HX * HY], sFx[HX * HY], sFy[HX * HY];
   const Geo& g = a.g;
+  const PhysC<C>& k = pc<C>(a.ph);
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int x0 = blockIdx.x * 32, y0 = blockIdx.y * 8;
+  const bool multiphase = k.G != C(0);
+  if (multiphase) {
+    for (int p = ty * 32 + tx; p < HX * HY; p += 256) {
+      const int id = map_y(g, y0 + p / HX - 2) * g.pitch + map_x(g, x0 + p % HX - 2);
+      sPsi[p] = a.psi[id];
+      sFx[p] = a.fmb[0][id];
+      sFy[p] = a.fmb[1][id];
+    }
+    __syncthreads();
+  }
+  const int x = x0 + tx, y = y0 + ty;
+  if (x >= g.nx || y >= g.ny) return;
   const int id = y * g.pitch + x;
   const uint8_t m = a.mask[id];
-  const PhysC<C>& k = pc<C>(a.ph);
   const C cs2 = C(1.0 / 3.0), gc = -k.G * cs2;
   C rp = C(0);
-  if (k.G != C(0)) {
+  if (multiphase) {
+    const int c = (ty + 2) * HX + tx + 2;
     C pb = a.psib[id];
     if (!(m & kSolid)) {
-      C sx = C(0), sy = C(0);
-#pragma unroll
-      for (int kk = 0; kk < 12; ++kk) {
-        const int ex = exv(kk), ey = eyv(kk);
-        const C d = at(g, a.psi, x + ex, y + ey) - at(g, a.psi, x - ex, y - ey);
-        sx = sx + C(wiso(kk)) * d * C(ex);
-        sy = sy + C(wiso(kk)) * d * C(ey);
-      }
-      pb = pb + gc * (a.fmb[0][id] * sx + a.fmb[1][id] * sy);
+      C sx, sy;
+      grad_t(&sPsi[c], HX, sx, sy);
+      pb = pb + gc * (sFx[c] * sx + sFy[c] * sy);
     }
 #pragma unroll
     for (int ey = -2; ey <= 2; ++ey) {
-      const int sy = wrap_y(g, y - ey);
 #pragma unroll
       for (int ex = -2; ex <= 2; ++ex) {
         if (ex == 0 && ey == 0) continue;
         int lo, hi;
-        src_cols(g, x, ex, lo, hi);
+        if (g.periodic_x) {
+          lo = hi = x - ex;
+        } else {
+          src_cols(g, x, ex, lo, hi);
+        }
         const C w = C(w_of(ex, ey));
+        const int row = (ty + 2 - ey) * HX - x0 + 2;
         for (int sx = lo; sx <= hi; ++sx) {
-          const int s = sy * g.pitch + sx;
-          pb = pb + gc * a.psi[s] * w * (C(ex) * a.fmb[0][s] + C(ey) * a.fmb[1][s]);
+          const int s = row + sx;
+          pb = pb + gc * sPsi[s] * w * (C(ex) * sFx[s] + C(ey) * sFy[s]);
         }
       }
     }
     // psi = sqrt(rad), rad = k2 (p - rho cs^2), k2 = 2 / (G cs^2)
-    const C r0 = a.rho[id], T0 = a.T[id], psi0 = a.psi[id];
+    const C r0 = a.rho[id], T0 = a.T[id], psi0 = sPsi[c];
     const C k2 = fdiv(C(2), k.G * cs2);
     const C dpr = pr_p(k, Dl<C>{r0, C(1)}, Dl<C>{T0, C(0)}).d;
     const C dpt = dpdT_eos(a.ph, r0, T0);
@@ -610,6 +623,16 @@ __global__ void __launch_bounds__(256) k_adj_pull(Args<C> a) {
     for (int i = 0; i < 9; ++i) a.fb_out[i * g.plane + id] = C(0);
     return;
   }
+  if (!(m & kNear2) && (g.periodic_x || (x >= 1 && x <= g.nx - 2))) {
+    // no solid node within two nodes and no open boundary next door: plain pulls only
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      int zx = x + cxv(i);
+      if (g.periodic_x) zx = zx < 0 ? zx + g.nx : (zx >= g.nx ? zx - g.nx : zx);
+      a.fb_out[i * g.plane + id] = a.fpb[i * g.plane + wrap_y(g, y + cyv(i)) * g.pitch + zx];
+    }
+    return;
+  }
 #pragma unroll
   for (int i = 0; i < 9; ++i) {
     const int cx = cxv(i), cy = cyv(i);
@@ -625,7 +648,7 @@ __global__ void __launch_bounds__(256) k_adj_pull(Args<C> a) {
       const int wy = wrap_y(g, zy + cy);
       if (g.periodic_x) wx = wx < 0 ? wx + g.nx : (wx >= g.nx ? wx - g.nx : wx);
       if (i != 0 && wx >= 0 && wx < g.nx && (a.mask[wy * g.pitch + wx] & kSolid)) {
-        const C qz = C(link_fraction(g, zx, zy, cx, cy));
+        const C qz = link_q<C>(g, zx, zy, oppv(i));
         if (qz < C(0.5)) acc = acc + (C(1) - C(2) * qz) * a.fpb[oppv(i) * g.plane + zy * g.pitch + zx];
       }
     }
@@ -637,7 +660,7 @@ __global__ void __launch_bounds__(256) k_adj_pull(Args<C> a) {
       const int sy = wrap_y(g, y - cyv(j));
       if (g.periodic_x) sx = sx < 0 ? sx + g.nx : (sx >= g.nx ? sx - g.nx : sx);
       if (sx >= 0 && sx < g.nx && (a.mask[sy * g.pitch + sx] & kSolid)) {
-        const C qj = C(link_fraction(g, x, y, -cxv(j), -cyv(j)));
+        const C qj = link_q<C>(g, x, y, j);
         C ca;
         if (qj < C(0.5)) {
           int nxp = x + cxv(j);
@@ -654,7 +677,7 @@ __global__ void __launch_bounds__(256) k_adj_pull(Args<C> a) {
       const int ty = wrap_y(g, y - cy);
       if (g.periodic_x) tx = tx < 0 ? tx + g.nx : (tx >= g.nx ? tx - g.nx : tx);
       if (tx >= 0 && tx < g.nx && (a.mask[ty * g.pitch + tx] & kSolid)) {
-        const C qi = C(link_fraction(g, x, y, -cx, -cy));
+        const C qi = link_q<C>(g, x, y, i);
         if (!(qi < C(0.5))) acc = acc + fdiv(C(2) * qi - C(1), C(2) * qi) * a.fpb[i * g.plane + id];
       }
     }

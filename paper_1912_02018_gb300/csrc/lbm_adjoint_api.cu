@@ -115,6 +115,7 @@ int forward_slot(lbm_ctx* c, lbm_adjoint_work* w, int j) {
   v.ux = w->aux[j];
   v.uy = w->auy[j];
   v.hf = w->hf;
+  v.nb = 0;  // the recompute needs no heat-flux sample
   int flipped = 0;
   const int k = c->f64 ? lbm::step_f64(c->geo, c->ph, v, 0, 0, 1, 1, c->prm.psi_mode, c->stream, nullptr, &flipped)
                        : lbm::step_f32(c->geo, c->ph, v, 0, 0, 1, 1, c->prm.psi_mode, c->prm.storage, c->stream,

@@ -411,6 +411,47 @@ lbm_status lbm_create(const lbm_domain* domain, const lbm_cylinder* cyl, const l
       }
     }
 
+  // link fractions of the near-wall nodes (Bouzidi), in double with the device's operation order
+  std::vector<int> widx(plane, -1);
+  std::vector<double> wq;
+  for (int y = 0; y < g.ny; ++y)
+    for (int x = 0; x < g.nx; ++x) {
+      const long long id = (long long)y * g.pitch + x;
+      if (!(mask[id] & lbm::kNearWall)) continue;
+      widx[id] = (int)(wq.size() / 8);
+      for (int i = 1; i < 9; ++i) {
+        int sx = x - CX[i], sy = (y - CY[i] + g.ny) % g.ny;
+        if (g.periodic_x) sx = (sx + g.nx) % g.nx;
+        double q = -1.0;
+        if (sx >= 0 && sx < g.nx && (mask[(long long)sy * g.pitch + sx] & lbm::kSolid)) {
+          const int cx = -CX[i], cy = -CY[i];
+          const double dx = x - g.xc, dy = y - g.yc, r = g.r;
+          const double A = (double)(cx * cx + cy * cy);
+          const double B = dx * cx + dy * cy;
+          const double C0 = dx * dx + dy * dy - r * r;
+          q = (-B - std::sqrt(B * B - A * C0)) / A;
+        }
+        wq.push_back(q);
+      }
+    }
+
+  // fluid nodes with a solid node within 2 nodes in x and y (the adjoint's slow pull path)
+  for (int y = 0; y < g.ny; ++y)
+    for (int x = 0; x < g.nx; ++x) {
+      const long long id = (long long)y * g.pitch + x;
+      if (mask[id] & lbm::kSolid) continue;
+      bool near2 = false;
+      for (int dy = -2; dy <= 2 && !near2; ++dy)
+        for (int dx = -2; dx <= 2 && !near2; ++dx) {
+          int sx = x + dx;
+          const int sy = ((y + dy) % g.ny + g.ny) % g.ny;
+          if (g.periodic_x) sx = ((sx % g.nx) + g.nx) % g.nx;
+          if (sx < 0 || sx >= g.nx) continue;
+          near2 = (mask[(long long)sy * g.pitch + sx] & lbm::kSolid) != 0;
+        }
+      if (near2) mask[id] |= lbm::kNear2;
+    }
+
   // device memory
   const size_t es = c->f64 ? sizeof(double) : sizeof(float);  // compute-type fields
   const size_t ps = P.storage == LBM_STORE_F64 ? 8 : (P.storage == LBM_STORE_F16S ? 2 : 4);  // populations
@@ -437,9 +478,16 @@ lbm_status lbm_create(const lbm_domain* domain, const lbm_cylinder* cyl, const l
   d.bn = dbv;
   d.hf = static_cast<double*>(dalloc(c, 4 * sizeof(double)));
   d.status = static_cast<int*>(dalloc(c, sizeof(int)));
+  int* dwidx = static_cast<int*>(dalloc(c, sizeof(int) * N));
+  void* dwq = dalloc(c, es * (wq.size() + 8));
+  double* dwn = static_cast<double*>(dalloc(c, sizeof(double) * (2 * bnode.size() + 2)));
+  g.wall_idx = dwidx;
+  g.wall_q = dwq;
+  g.wall_n = dwn;
   d.stage = static_cast<double*>(dalloc(c, sizeof(double) * (size_t)g.nx * g.ny * 6));
   if (!d.f[0] || !d.f[1] || !d.T[0] || !d.T[1] || !d.psi || !d.rho || !d.ux || !d.uy || !d.side[0] ||
-      !d.side[1] || !d.partial || !d.counter || !dmask || !dbn || !dbv || !d.hf || !d.status || !d.stage) {
+      !d.side[1] || !d.partial || !d.counter || !dmask || !dbn || !dbv || !d.hf || !d.status || !d.stage ||
+      !dwidx || !dwq || !dwn) {
     dfree_all(c);
     delete c;
     return fail(nullptr, LBM_ENOMEM, "device allocation failed");
@@ -456,6 +504,17 @@ lbm_status lbm_create(const lbm_domain* domain, const lbm_cylinder* cyl, const l
   chk(cudaMemsetAsync(d.status, 0, sizeof(int), c->stream));
   chk(cudaMemsetAsync(d.counter, 0, sizeof(unsigned), c->stream));
   chk(cudaMemcpyAsync(dmask, mask.data(), N, cudaMemcpyHostToDevice, c->stream));
+  chk(cudaMemcpyAsync(dwidx, widx.data(), sizeof(int) * N, cudaMemcpyHostToDevice, c->stream));
+  std::vector<double> wn;  // near-wall rows are the boundary list in the same order
+  for (size_t b = 0; b < bnode.size(); ++b) {
+    wn.push_back(bnx[b]);
+    wn.push_back(bny[b]);
+  }
+  if (!wn.empty()) chk(cudaMemcpyAsync(dwn, wn.data(), sizeof(double) * wn.size(), cudaMemcpyHostToDevice, c->stream));
+  std::vector<float> wqf(wq.begin(), wq.end());
+  if (!wq.empty())
+    chk(cudaMemcpyAsync(dwq, c->f64 ? (const void*)wq.data() : (const void*)wqf.data(), es * wq.size(),
+                        cudaMemcpyHostToDevice, c->stream));
   if (!bnode.empty()) {
     chk(cudaMemcpyAsync(dbn, bnode.data(), sizeof(int) * bnode.size(), cudaMemcpyHostToDevice, c->stream));
     chk(cudaMemcpyAsync(dbv, bnv.data(), sizeof(double) * bnv.size(), cudaMemcpyHostToDevice, c->stream));

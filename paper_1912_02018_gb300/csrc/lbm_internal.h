@@ -10,12 +10,20 @@ namespace lbm {
 // Node-type bits of the uint8 mask.
 constexpr uint8_t kSolid = 1;     // inside the cylinder
 constexpr uint8_t kNearWall = 2;  // fluid node with a D2Q9 neighbour inside the cylinder
+constexpr uint8_t kNear2 = 4;     // fluid node with a solid node at most 2 nodes away in x and y
 
 // Lattice geometry.  Arrays are [ny][pitch], pitch >= nx a multiple of 32 elements.
 struct Geo {
   int nx, ny, pitch, periodic_x;
   int plane;        // elements per population plane = ny * pitch (9 * plane < 2^31)
   double xc, yc, r; // cylinder centre and radius (r <= 0: none)
+  // link fractions of the near-wall nodes, tabulated on the host: wall_idx[y * pitch + x] is
+  // the node's row (-1 away from the wall); wall_q[row * 8 + i - 1] (compute type) is the
+  // fraction of the link from the node along -c_i that lies in the fluid, -1 where the pull
+  // source of direction i is fluid
+  const int* wall_idx;
+  const void* wall_q;
+  const double* wall_n;  // [row][2]: outward unit normal (from the centre) of the near-wall node
 };
 
 // A double-float value hi + lo (two FP32 words, |lo| <= ulp(hi)/2).

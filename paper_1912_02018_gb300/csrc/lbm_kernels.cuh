@@ -343,13 +343,11 @@ __device__ __forceinline__ C energy_rhs_t(const Phys& ph, const C* t, int ts, co
 }
 
 // ---------------------------------------------------------------- streaming (Sec. IV.A BCs)
-// Fraction q of the link from fluid node (x, y) along (cx, cy) that lies in the fluid.
-__device__ __forceinline__ double link_fraction(const Geo& g, int x, int y, int cx, int cy) {
-  double dx = x - g.xc, dy = y - g.yc, r = g.r;
-  double A = (double)(cx * cx + cy * cy);
-  double B = dx * cx + dy * cy;
-  double C0 = dx * dx + dy * dy - r * r;
-  return (-B - sqrt(B * B - A * C0)) / A;
+// Link fraction q of direction i at a near-wall node: the fraction of the link from the node
+// along -c_i that lies in the fluid (smallest root of |d + t c|^2 = r^2, tabulated at creation).
+template <typename C>
+__device__ __forceinline__ C link_q(const Geo& g, int x, int y, int i) {
+  return static_cast<const C*>(g.wall_q)[g.wall_idx[y * g.pitch + x] * 8 + i - 1];
 }
 
 // Pull with substitutions for nodes next to the wall, the inlet or the outlet: linear
@@ -371,7 +369,7 @@ __device__ __forceinline__ void pull_slow(const Geo& g, const Phys& ph, const S*
     } else if (mask[sy * g.pitch + sx] & kSolid) {
       // linear interpolated bounce-back; the wall lies along c_opp(i)
       const int io = oppv(i);
-      const C q = C(link_fraction(g, x, y, -cx, -cy));
+      const C q = link_q<C>(g, x, y, i);
       const C a = ldf<C>(g, ph, f, io, y, x);
       if (q < C(0.5)) {
         int nxp = x + cx;
@@ -837,9 +835,8 @@ __device__ __forceinline__ void energy_tile(const Geo& g, const Phys& ph, const 
         // wall heat flux -lambda grad T . n at this boundary node, from T^n (Sec. IV.B)
         C gx, gy;
         grad_t(&sT[a + k], AX, gx, gy);
-        const double dx = x - g.xc, dy = y - g.yc, rr = sqrt(dx * dx + dy * dy);
-        const double nxv = dx / rr, nyv = dy / rr;
-        q += -(double)sL[a + k] * ((double)gx * nxv + (double)gy * nyv);
+        const double* nv = &g.wall_n[2 * g.wall_idx[y * g.pitch + x]];
+        q += -(double)sL[a + k] * ((double)gx * nv[0] + (double)gy * nv[1]);
       }
     }
   }
