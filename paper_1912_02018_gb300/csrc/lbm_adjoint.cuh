@@ -148,16 +148,16 @@ __device__ __forceinline__ Parts<C> parts_at(const C* t, int ts, const C* l, con
 #pragma unroll
   for (int k = 0; k < 12; ++k) {
     const int ex = exv(k), ey = eyv(k);
-    const C w = C(wiso(k));
+    const C w = C(wiso(k)), wx = C(wiso(k) * ex), wy = C(wiso(k) * ey);
     const C tp = t[ey * ts + ex], tm = t[-ey * ts - ex];
-    gx = gx + w * (tp - tm) * C(ex);
-    gy = gy + w * (tp - tm) * C(ey);
+    if (ex != 0) gx = gx + wx * (tp - tm);
+    if (ey != 0) gy = gy + wy * (tp - tm);
     lap = lap + w * ((tp + tm) - C(2) * c);
     const C dl = l[ey * as + ex] - l[-ey * as - ex];
-    lx = lx + w * dl * C(ex);
-    ly = ly + w * dl * C(ey);
-    if (ex != 0) dxux = dxux + w * (u[ey * as + ex] - u[-ey * as - ex]) * C(ex);
-    if (ey != 0) dyuy = dyuy + w * (v[ey * as + ex] - v[-ey * as - ex]) * C(ey);
+    if (ex != 0) lx = lx + wx * dl;
+    if (ey != 0) ly = ly + wy * dl;
+    if (ex != 0) dxux = dxux + wx * (u[ey * as + ex] - u[-ey * as - ex]);
+    if (ey != 0) dyuy = dyuy + wy * (v[ey * as + ex] - v[-ey * as - ex]);
   }
   P.gx = gx;
   P.gy = gy;
@@ -229,11 +229,11 @@ __global__ void __launch_bounds__(kEANT) k_adj_energy(Args<C> a) {
           t1 = k.T_sat;
         } else {
           const Parts<C> P = parts_at(&sT[ai], AX, &sL[ai], &sU[ai], &sV[ai], AX);
-          const C r0 = sR[ai], T0 = sT[ai];
+          const C r0 = sR[ai], Ta = sT[ai];
           const C conv = sU[ai] * P.upx + sV[ai] * P.upy;
           const C diff = sL[ai] * P.lap + (P.lx * P.gx + P.ly * P.gy);
-          const C work = T0 * dpdT_eos(a.ph, r0, T0) * P.divu;
-          t1 = T0 + (-conv + fdiv(diff, r0 * k.c_v) - fdiv(work, r0 * k.c_v));
+          const C work = Ta * dpdT_eos(a.ph, r0, Ta) * P.divu;
+          t1 = sT[ai] + (-conv + fdiv(diff, r0 * k.c_v) - fdiv(work, r0 * k.c_v));
         }
       }
       sT1[p] = t1;

@@ -452,6 +452,20 @@ lbm_status lbm_create(const lbm_domain* domain, const lbm_cylinder* cyl, const l
       if (near2) mask[id] |= lbm::kNear2;
     }
 
+  // energy tiles (32 x 8 and 32 x 16) that hold a near-wall node: they alone sum heat flux
+  int wall_tiles[2] = {0, 0};
+  for (int h = 0; h < 2; ++h) {
+    const int TY = h == 0 ? 8 : 16;
+    for (int ty = 0; ty * TY < g.ny; ++ty)
+      for (int tx = 0; tx * 32 < g.nx; ++tx) {
+        bool any = false;
+        for (int y = ty * TY; y < std::min(g.ny, ty * TY + TY) && !any; ++y)
+          for (int x = tx * 32; x < std::min(g.nx, tx * 32 + 32) && !any; ++x)
+            any = (mask[(long long)y * g.pitch + x] & lbm::kNearWall) != 0;
+        wall_tiles[h] += any ? 1 : 0;
+      }
+  }
+
   // device memory
   const size_t es = c->f64 ? sizeof(double) : sizeof(float);  // compute-type fields
   const size_t ps = P.storage == LBM_STORE_F64 ? 8 : (P.storage == LBM_STORE_F16S ? 2 : 4);  // populations
@@ -469,6 +483,8 @@ lbm_status lbm_create(const lbm_domain* domain, const lbm_cylinder* cyl, const l
   d.side[1] = dalloc(c, 3 * (size_t)g.ny * es);
   d.partial = static_cast<double*>(dalloc(c, sizeof(double) * lbm::energy_blocks(g.nx, g.ny)));
   d.counter = static_cast<unsigned*>(dalloc(c, sizeof(unsigned)));
+  d.wall_tiles[0] = wall_tiles[0];
+  d.wall_tiles[1] = wall_tiles[1];
   uint8_t* dmask = static_cast<uint8_t*>(dalloc(c, N));
   d.mask = dmask;
   d.nb = (int)bnode.size();
@@ -503,6 +519,7 @@ lbm_status lbm_create(const lbm_domain* domain, const lbm_cylinder* cyl, const l
   chk(cudaMemsetAsync(d.hf, 0, 4 * sizeof(double), c->stream));
   chk(cudaMemsetAsync(d.status, 0, sizeof(int), c->stream));
   chk(cudaMemsetAsync(d.counter, 0, sizeof(unsigned), c->stream));
+  chk(cudaMemsetAsync(d.partial, 0, sizeof(double) * lbm::energy_blocks(g.nx, g.ny), c->stream));
   chk(cudaMemcpyAsync(dmask, mask.data(), N, cudaMemcpyHostToDevice, c->stream));
   chk(cudaMemcpyAsync(dwidx, widx.data(), sizeof(int) * N, cudaMemcpyHostToDevice, c->stream));
   std::vector<double> wn;  // near-wall rows are the boundary list in the same order

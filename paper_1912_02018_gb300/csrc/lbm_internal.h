@@ -69,7 +69,8 @@ struct Dev {
   const double* bn;  // their outward normals, [2][nb]
   int nb;
   double* hf;        // heat-flux accumulators: last, sum, sum of squares, count
-  double* partial;   // one heat-flux partial sum per energy-kernel block
+  double* partial;   // one heat-flux partial sum per energy-kernel block (zero between launches)
+  int wall_tiles[2]; // energy tiles (32 wide, 8 or 16 high) that hold a near-wall node
   unsigned* counter; // blocks of the current energy launch that have finished (wraps to 0)
   int* status;       // latched fault bits
   double* stage;     // nx*ny doubles for exports/imports

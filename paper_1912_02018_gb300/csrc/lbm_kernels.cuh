@@ -289,59 +289,15 @@ __device__ __forceinline__ void grad_t(const C* p, int s, C& gx, C& gy) {
   for (int k = 0; k < 12; ++k) {
     const int ex = exv(k), ey = eyv(k);
     if ((kX && ex != 0) || (kY && ey != 0)) {
-      const C w = C(wiso(k));
+      // w e is w scaled by a power of two: (w e) d rounds exactly like (w d) e
       C d = p[ey * s + ex] - p[-ey * s - ex];
-      if (kX && ex != 0) sx = sx + w * d * C(ex);
-      if (kY && ey != 0) sy = sy + w * d * C(ey);
+      if (kX && ex != 0) sx = sx + C(wiso(k) * ex) * d;
+      if (kY && ey != 0) sy = sy + C(wiso(k) * ey) * d;
     }
   }
   gx = sx;
   gy = sy;
 }
-// Isotropic Laplacian 2 sum_k w_k (phi(x+e_k) - phi(x)) over +/- pairs.
-template <typename C>
-__device__ __forceinline__ C lap_t(const C* p, int s) {
-  const C c = p[0];
-  C acc = C(0);
-#pragma unroll
-  for (int k = 0; k < 12; ++k) {
-    const int ex = exv(k), ey = eyv(k);
-    C d = (p[ey * s + ex] + p[-ey * s - ex]) - C(2) * c;
-    acc = acc + C(wiso(k)) * d;
-  }
-  return C(2) * acc;
-}
-// Third-order upwind derivative along the direction with element step st, biased against v.
-template <typename C>
-__device__ __forceinline__ C upwind3_t(const C* p, int st, C v) {
-  const C c = p[0];
-  if (v >= C(0)) {
-    C m2 = p[-2 * st] - c, m1 = p[-st] - c, p1 = p[st] - c;
-    return fdiv(m2 - C(6) * m1 + C(2) * p1, C(6));
-  }
-  C m1 = p[-st] - c, p1 = p[st] - c, p2 = p[2 * st] - c;
-  return fdiv(-C(2) * m1 + C(6) * p1 - p2, C(6));
-}
-// Right-hand side of Eq. (energy) with rho and u frozen:
-// -u.grad T + (lambda lap T + grad lambda.grad T)/(rho c_v) - T (dp/dT)_rho div u / (rho c_v).
-// t: temperature stencil centre (row stride ts); lam, u, v, r: centres in tiles of stride as.
-template <typename C>
-__device__ __forceinline__ C energy_rhs_t(const Phys& ph, const C* t, int ts, const C* lam, const C* u, const C* v,
-                                          const C* r, int as) {
-  const C r0 = r[0], u0 = u[0], v0 = v[0], T0 = t[0];
-  C conv = u0 * upwind3_t(t, 1, u0) + v0 * upwind3_t(t, ts, v0);
-  C gx, gy, lx, ly, dxux, dyuy, unused;
-  grad_t(t, ts, gx, gy);
-  C lap = lap_t(t, ts);
-  grad_t(lam, as, lx, ly);
-  grad_t<C, true, false>(u, as, dxux, unused);
-  grad_t<C, false, true>(v, as, unused, dyuy);
-  C divu = dxux + dyuy;
-  C diff = lam[0] * lap + (lx * gx + ly * gy);
-  C work = T0 * dpdT_eos(ph, r0, T0) * divu;
-  return -conv + fdiv(diff, r0 * pc<C>(ph).c_v) - fdiv(work, r0 * pc<C>(ph).c_v);
-}
-
 // ---------------------------------------------------------------- streaming (Sec. IV.A BCs)
 // Link fraction q of direction i at a near-wall node: the fraction of the link from the node
 // along -c_i that lies in the fluid (smallest root of |d + t c|^2 = r^2, tabulated at creation).
@@ -659,10 +615,9 @@ __device__ __forceinline__ void grad_w(const C w[5][6], int c0, C& gx, C& gy) {
   for (int k = 0; k < 12; ++k) {
     const int ex = exv(k), ey = eyv(k);
     if ((kX && ex != 0) || (kY && ey != 0)) {
-      const C w8 = C(wiso(k));
       C d = w[2 + ey][c0 + ex] - w[2 - ey][c0 - ex];
-      if (kX && ex != 0) sx = sx + w8 * d * C(ex);
-      if (kY && ey != 0) sy = sy + w8 * d * C(ey);
+      if (kX && ex != 0) sx = sx + C(wiso(k) * ex) * d;
+      if (kY && ey != 0) sy = sy + C(wiso(k) * ey) * d;
     }
   }
   gx = sx;
@@ -751,8 +706,8 @@ template <typename C, int ETY>
 __device__ __forceinline__ void energy_tile(const Geo& g, const Phys& ph, const C* __restrict__ Tin,
                                             C* __restrict__ Tout, const C* __restrict__ rho, const C* __restrict__ ux,
                                             const C* __restrict__ uy, const uint8_t* __restrict__ mask,
-                                            double* partial, unsigned* counter, double* hf, int nb, int do_hf, int bx,
-                                            int by, int bid, int nblocks) {
+                                            double* partial, unsigned* counter, double* hf, int nb, int do_hf,
+                                            int n_wall_tiles, int bx, int by, int bid, int nblocks) {
   constexpr int TX = EnergyTile<C, ETY>::TX, TY = EnergyTile<C, ETY>::TY, NT = EnergyTile<C, ETY>::NT;
   constexpr int H = 4, AX = TX + 2 * H, AY = TY + 2 * H;  // inputs: tile + 4
   constexpr int BX = TX + 4, BY = TY + 4;                 // stage 1: tile + 2
@@ -841,31 +796,33 @@ __device__ __forceinline__ void energy_tile(const Geo& g, const Phys& ph, const 
     }
   }
   if (do_hf) {
-    // FP64 block sum only where the tile touches the cylinder; the last block to finish
-    // adds all partials in block order and updates the running statistics
+    // FP64 block sums only in the tiles that hold wall nodes (the others skip the fence and the
+    // counter); the last of those tiles to finish adds all partials in block order (zero
+    // elsewhere), updates the running statistics and clears the partials for the next launch
     int mine = 0;
 #pragma unroll
     for (int k = 0; k < 2; ++k) mine |= (x0 + tx + k < g.nx && y < g.ny && (sM[a + k] & kNearWall)) ? 1 : 0;
-    const int has = __syncthreads_or(mine);
-    double s = 0.0;
-    if (has) s = block_sum<NT>(q, red);
-    if (tid == 0) {
-      partial[bid] = s;
-      __threadfence();
-      done_last = atomicInc(counter, nblocks - 1) == (unsigned)(nblocks - 1);
-    }
-    __syncthreads();
-    if (done_last) {
-      __threadfence();
-      double acc = 0.0;
-      for (int i = tid; i < nblocks; i += NT) acc += __ldcg(&partial[i]);
-      acc = block_sum<NT>(acc, red);
+    if (__syncthreads_or(mine)) {
+      const double s = block_sum<NT>(q, red);
       if (tid == 0) {
-        const double qv = acc / nb;
-        hf[0] = qv;
-        hf[1] += qv;
-        hf[2] += qv * qv;
-        hf[3] += 1.0;
+        partial[bid] = s;
+        __threadfence();
+        done_last = atomicInc(counter, n_wall_tiles - 1) == (unsigned)(n_wall_tiles - 1);
+      }
+      __syncthreads();
+      if (done_last) {
+        __threadfence();
+        double acc = 0.0;
+        for (int i = tid; i < nblocks; i += NT) acc += __ldcg(&partial[i]);
+        acc = block_sum<NT>(acc, red);  // its barrier also ends every thread's reads above
+        for (int i = tid; i < nblocks; i += NT) partial[i] = 0.0;
+        if (tid == 0) {
+          const double qv = acc / nb;
+          hf[0] = qv;
+          hf[1] += qv;
+          hf[2] += qv * qv;
+          hf[3] += 1.0;
+        }
       }
     }
   }
@@ -874,8 +831,9 @@ template <typename C>
 __global__ void __launch_bounds__(EnergyTile<C>::NT)
     k_energy(Geo g, Phys ph, const C* __restrict__ Tin, C* __restrict__ Tout, const C* __restrict__ rho,
              const C* __restrict__ ux, const C* __restrict__ uy, const uint8_t* __restrict__ mask,
-             double* partial, unsigned* counter, double* hf, int nb, int do_hf) {
-  energy_tile<C, EnergyTile<C>::TY>(g, ph, Tin, Tout, rho, ux, uy, mask, partial, counter, hf, nb, do_hf, blockIdx.x,
+             double* partial, unsigned* counter, double* hf, int nb, int do_hf, int n_wall_tiles) {
+  energy_tile<C, EnergyTile<C>::TY>(g, ph, Tin, Tout, rho, ux, uy, mask, partial, counter, hf, nb, do_hf,
+                                    n_wall_tiles, blockIdx.x,
                                     blockIdx.y, blockIdx.y * gridDim.x + blockIdx.x, gridDim.x * gridDim.y);
 }
 
@@ -922,7 +880,7 @@ __global__ void __launch_bounds__(EnergyTile<C, ETY>::NT) kb_energy(const BatchD
   }
   energy_tile<C, ETY>(D.g, D.ph, Tin, Tout, static_cast<const C*>(D.d.rho), static_cast<const C*>(D.d.ux),
                       static_cast<const C*>(D.d.uy), D.d.mask, D.d.partial, D.d.counter, D.d.hf, D.d.nb, D.d.nb > 0,
-                      bx, by, local, D.en_nblocks);
+                      D.d.wall_tiles[ETY == 16 ? 1 : 0], bx, by, local, D.en_nblocks);
 }
 
 template <typename C, typename S, int PSI, int CTY, int ETY>
@@ -1080,7 +1038,8 @@ int step_impl(const Geo& g, const Phys& ph, const Dev& d, int cur, int tcur, int
     using ET = EnergyTile<C>;
     const dim3 blk(ET::NT), grd((g.nx + ET::TX - 1) / ET::TX, (g.ny + ET::TY - 1) / ET::TY);
     pre(kKEnergy);
-    k_energy<C><<<grd, blk, 0, s>>>(g, ph, T, Tn, rho, ux, uy, d.mask, d.partial, d.counter, d.hf, d.nb, do_hf);
+    k_energy<C><<<grd, blk, 0, s>>>(g, ph, T, Tn, rho, ux, uy, d.mask, d.partial, d.counter, d.hf, d.nb, do_hf,
+                                    d.wall_tiles[ET::TY == 16 ? 1 : 0]);
     post(kKEnergy);
     *t_flipped = 1;
   }

@@ -1,9 +1,12 @@
 """Long runs: the time-averaged wall Nusselt number of the FP32 CUDA path against the FP64 oracle.
 
 Pointwise fields of two precisions decorrelate in an unsteady run; the time average of the wall
-heat flux (Sec. IV.B) over the second half of the run is the comparable quantity, and must agree
-within 2%.  Cases: the 128 x 64 parity case extended to 50,000 steps (Re = 30, steady wake), and
-256 x 128 with D = 32 at Re = 300 for 50,000 steps (periodic vortex shedding).
+heat flux (Sec. IV.B) over a long window is the comparable quantity, and must agree within 2%.
+Cases: the 128 x 64 parity case extended to 50,000 steps (Re = 30, steady wake; average over
+the second half), and 256 x 128 with D = 32 at Re = 300 and superheat 0.2 T_c (unsteady wake
+over a strongly superheated wall; average over steps 25,000 to 75,000).  The same lattice at
+superheat 0.05 T_c is still in a slow transient at 100,000 steps (the heat flux climbs by 20%
+between successive 25,000-step windows), so its windowed means are not a precision measure.
 """
 import pytest
 
@@ -27,10 +30,10 @@ def _built():
     torch.cuda.set_device(0)
 
 
-CASES = {
-    "128x64_D16_Re30_50k": si.SMALL,
-    "256x128_D32_Re300_50k": si.cylinder_case(256, 128, 32.0, Re=300.0, superheat_Tc=0.05,
-                                              name="256x128_D32_Re300"),
+CASES = {  # case, steps before the averaging window, window length
+    "128x64_D16_Re30_50k": (si.SMALL, 25_000, 25_000),
+    "256x128_D32_Re300_dT0.2Tc_75k": (si.cylinder_case(256, 128, 32.0, Re=300.0, superheat_Tc=0.2,
+                                                       name="256x128_D32_Re300_dT0.2"), 25_000, 50_000),
 }
 
 
@@ -38,14 +41,13 @@ CASES = {
 def test_fp32_time_averaged_nusselt_within_2_percent_of_oracle(name):
     from paper_1912_02018_gb300 import Sim
 
-    case = CASES[name]
-    steps, half = 50_000, 25_000
+    case, start, half = CASES[name]
     drho = case.drho()
-    sim = Sim.from_case(case, f64=False, init={"drho": drho}).step(steps - half)
+    sim = Sim.from_case(case, f64=False, init={"drho": drho}).step(start)
     sim.reset_heat_flux()
     sim.step(half)
     got = sim.heat_flux()
-    ref = Oracle(case, drho=drho).step(steps - half)
+    ref = Oracle(case, drho=drho).step(start)
     before = ref.heat_flux()
     ref.step(half)
     after = ref.heat_flux()
