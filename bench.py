@@ -55,7 +55,8 @@ POP = {"f32": 4, "f64": 8, "f16s": 2}[next((a.split("=", 1)[1] for a in sys.argv
 ALG_BYTES = {
     "k_rho_psi": 9 * POP + 4 + 4,           # f, T in; psi out
     "k_collide": 9 * POP + 4 + 9 * POP + 12,  # f, psi in; f*, rho, ux, uy out
-    "k_energy": 4 * 4 + 4,               # T, rho, ux, uy in; T out
+    # T, rho, ux, uy in; T out; and psi of the next step: the new populations in, psi out
+    "k_energy": 4 * 4 + 4 + 9 * POP + 4,
 }
 STEP_ALG_BYTES = 9 * POP * 2 + 4 * 2      # the whole step: populations and T in and out
 KERNEL_SRC = os.path.join(ROOT, "paper_1912_02018_gb300", "csrc", "lbm_kernels.cuh")

@@ -175,7 +175,7 @@ __device__ __forceinline__ Parts<C> parts_at(const C* t, int ts, const C* l, con
 // nodes: Tb1, the adjoint of T1.  Stage 1 (seed Tb1 on L(T), plus the heat-flux sample) does
 // the same from T on the tile + 4 and gives Tb_out, the adjoint of T.  Both add their parts
 // of the adjoints of u (ub), lambda (lamb) and rho (rhob).
-constexpr int kEATX = 32, kEATY = 16, kEANT = 256;
+constexpr int kEATX = 32, kEATY = 16, kEANT = 512;
 template <typename C, int STAGE>
 struct EAdjLayout {
   static constexpr int H = STAGE == 2 ? 6 : 4;
@@ -319,33 +319,38 @@ __global__ void __launch_bounds__(kEANT) k_adj_energy(Args<C> a) {
     const int id = y * g.pitch + x;
     const uint8_t m = sM[(ty + H) * AX + tx + H];
     C tb = C(0), ubx = C(0), uby = C(0), lb = C(0);
-#pragma unroll
-    for (int ey = -2; ey <= 2; ++ey) {
-#pragma unroll
-      for (int ex = -2; ex <= 2; ++ex) {
-        const C w = C(w_of(ex, ey));
-        const C clap = (ex == 0 && ey == 0) ? C(-4) * wsum : C(2) * w;
-        int lo, hi;
-        if (g.periodic_x) {
-          lo = hi = x - ex;
-        } else {
-          src_cols(g, x, ex, lo, hi);
-        }
-        const int prow = (ty + 2 - ey) * PX - x0 + 2;
-        const int arow = (ty + H - ey) * AX - x0 + H;
-        for (int sx = lo; sx <= hi; ++sx) {
-          const int pp = prow + sx;
-          tb = tb + clap * sP[pp];
-          if (ex != 0 || ey != 0) {
-            tb = tb + w * (C(ex) * sP[PN + pp] + C(ey) * sP[2 * PN + pp]);
-            ubx = ubx + w * C(ex) * sP[5 * PN + pp];
-            uby = uby + w * C(ey) * sP[5 * PN + pp];
-            lb = lb + w * (C(ex) * sP[6 * PN + pp] + C(ey) * sP[7 * PN + pp]);
-          }
-          if (ey == 0) tb = tb - upw_coef<C>(ex, sU[arow + sx] >= C(0)) * sP[3 * PN + pp];
-          if (ex == 0) tb = tb - upw_coef<C>(ey, sV[arow + sx] >= C(0)) * sP[4 * PN + pp];
-        }
+    // contribution of the source at P-tile index pp (A-tile index ap) through offset (ex, ey)
+    auto add = [&](int ex, int ey, int pp, int ap) {
+      const C w = C(w_of(ex, ey));
+      const C clap = (ex == 0 && ey == 0) ? C(-4) * wsum : C(2) * w;
+      tb = tb + clap * sP[pp];
+      if (ex != 0 || ey != 0) {
+        tb = tb + w * (C(ex) * sP[PN + pp] + C(ey) * sP[2 * PN + pp]);
+        ubx = ubx + w * C(ex) * sP[5 * PN + pp];
+        uby = uby + w * C(ey) * sP[5 * PN + pp];
+        lb = lb + w * (C(ex) * sP[6 * PN + pp] + C(ey) * sP[7 * PN + pp]);
       }
+      if (ey == 0) tb = tb - upw_coef<C>(ex, sU[ap] >= C(0)) * sP[3 * PN + pp];
+      if (ex == 0) tb = tb - upw_coef<C>(ey, sV[ap] >= C(0)) * sP[4 * PN + pp];
+    };
+    if (g.periodic_x || (x > 0 && x < g.nx - 1)) {
+      // one source position per offset (positions past an edge hold zero sources)
+#pragma unroll
+      for (int ey = -2; ey <= 2; ++ey)
+#pragma unroll
+        for (int ex = -2; ex <= 2; ++ex)
+          add(ex, ey, (ty + 2 - ey) * PX + tx + 2 - ex, (ty + H - ey) * AX + tx + H - ex);
+    } else {
+      // an open edge column: every source whose clamped stencil reads it
+#pragma unroll 1
+      for (int ey = -2; ey <= 2; ++ey)
+#pragma unroll 1
+        for (int ex = -2; ex <= 2; ++ex) {
+          int lo, hi;
+          src_cols(g, x, ex, lo, hi);
+          for (int sx = lo; sx <= hi; ++sx)
+            add(ex, ey, (ty + 2 - ey) * PX + sx - x0 + 2, (ty + H - ey) * AX + sx - x0 + H);
+        }
     }
     const bool in = interior_T(g, m, x);
     tb = tb + sLoc[q];
@@ -524,10 +529,12 @@ __global__ void __launch_bounds__(256) k_adj_force(Args<C> a) {
   const bool multiphase = k.G != C(0);
   if (multiphase) {
     for (int p = ty * 32 + tx; p < HX * HY; p += 256) {
-      const int id = map_y(g, y0 + p / HX - 2) * g.pitch + map_x(g, x0 + p % HX - 2);
+      const int gx = x0 + p % HX - 2;
+      const int id = map_y(g, y0 + p / HX - 2) * g.pitch + map_x(g, gx);
+      const bool real = g.periodic_x || (gx >= 0 && gx < g.nx);  // a ghost column is no source
       sPsi[p] = a.psi[id];
-      sFx[p] = a.fmb[0][id];
-      sFy[p] = a.fmb[1][id];
+      sFx[p] = real ? a.fmb[0][id] : C(0);
+      sFy[p] = real ? a.fmb[1][id] : C(0);
     }
     __syncthreads();
   }
@@ -545,24 +552,26 @@ __global__ void __launch_bounds__(256) k_adj_force(Args<C> a) {
       grad_t(&sPsi[c], HX, sx, sy);
       pb = pb + gc * (sFx[c] * sx + sFy[c] * sy);
     }
+    auto add = [&](int ex, int ey, int s) {
+      pb = pb + gc * sPsi[s] * C(w_of(ex, ey)) * (C(ex) * sFx[s] + C(ey) * sFy[s]);
+    };
+    if (g.periodic_x || (x > 0 && x < g.nx - 1)) {
+      // one source position per offset (ghost positions carry no F_m adjoint)
 #pragma unroll
-    for (int ey = -2; ey <= 2; ++ey) {
+      for (int ey = -2; ey <= 2; ++ey)
 #pragma unroll
-      for (int ex = -2; ex <= 2; ++ex) {
-        if (ex == 0 && ey == 0) continue;
-        int lo, hi;
-        if (g.periodic_x) {
-          lo = hi = x - ex;
-        } else {
+        for (int ex = -2; ex <= 2; ++ex)
+          if (ex != 0 || ey != 0) add(ex, ey, (ty + 2 - ey) * HX + tx + 2 - ex);
+    } else {
+#pragma unroll 1
+      for (int ey = -2; ey <= 2; ++ey)
+#pragma unroll 1
+        for (int ex = -2; ex <= 2; ++ex) {
+          if (ex == 0 && ey == 0) continue;
+          int lo, hi;
           src_cols(g, x, ex, lo, hi);
+          for (int sx = lo; sx <= hi; ++sx) add(ex, ey, (ty + 2 - ey) * HX + sx - x0 + 2);
         }
-        const C w = C(w_of(ex, ey));
-        const int row = (ty + 2 - ey) * HX - x0 + 2;
-        for (int sx = lo; sx <= hi; ++sx) {
-          const int s = row + sx;
-          pb = pb + gc * sPsi[s] * w * (C(ex) * sFx[s] + C(ey) * sFy[s]);
-        }
-      }
     }
     // psi = sqrt(rad), rad = k2 (p - rho cs^2), k2 = 2 / (G cs^2)
     const C r0 = a.rho[id], T0 = a.T[id], psi0 = sPsi[c];
@@ -725,14 +734,18 @@ __global__ void __launch_bounds__(256) k_plane_to_dense(Geo g, const C* src, dou
 }
 
 // One reverse step (5 launches).  Returns the number of launches or -1.
+// Shared-memory opt-in of the energy stages on the current device (before any launch or capture).
+template <typename C>
+int adjoint_setup_impl() {
+  cudaFuncSetAttribute(k_adj_energy<C, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)EAdjLayout<C, 2>::bytes);
+  cudaFuncSetAttribute(k_adj_energy<C, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)EAdjLayout<C, 1>::bytes);
+  return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
+}
 template <typename C, int STAGE>
 void launch_energy_adj(const Args<C>& a, cudaStream_t s) {
   using Lay = EAdjLayout<C, STAGE>;
-  static bool attr = false;  // one attribute call per instantiation (the size is a constant)
-  if (!attr) {
-    cudaFuncSetAttribute(k_adj_energy<C, STAGE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Lay::bytes);
-    attr = true;
-  }
   const dim3 grd((a.g.nx + kEATX - 1) / kEATX, (a.g.ny + kEATY - 1) / kEATY);
   k_adj_energy<C, STAGE><<<grd, kEANT, Lay::bytes, s>>>(a);
 }

@@ -6,12 +6,14 @@
 // copies its state (f*, T, outlet side values) at the start of each segment.  The reverse
 // pass takes the segments last to first: it recomputes the segment from its checkpoint into
 // K + 1 state slots (keeping rho, psi and u of every collision), then runs the reverse steps
-// last to first.  Memory: (K + 1) states, K sets of collision fields, one state per
+// last to first.  Memory: (K + 1) states and psi fields, K sets of rho and u, one state per
 // checkpoint and 30 adjoint work planes.
 #include <cuda_runtime.h>
 
 #include <cmath>
 #include <cstring>
+#include <map>
+#include <tuple>
 #include <vector>
 
 #include "lbm.h"
@@ -30,6 +32,12 @@ struct lbm_adjoint_work {
   void *Tb1 = nullptr, *ub[2] = {}, *lamb = nullptr, *rhob = nullptr;
   void *fpb = nullptr, *fmb[2] = {}, *psib = nullptr;
   double *gw = nullptr, *uin = nullptr, *hf = nullptr;
+  // a segment's recompute and reverse steps replayed from a CUDA graph on a private stream,
+  // ordered after and before the context's stream by events; one graph per (length, starting
+  // ping-pong parity, heat-flux weight)
+  cudaStream_t gs = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  std::map<std::tuple<int, int, double>, cudaGraphExec_t> graphs;
 };
 
 namespace {
@@ -70,10 +78,10 @@ lbm_status prepare(lbm_ctx* c, int K, int nseg) {
   }
   for (int j = 0; j < K; ++j) {
     w->arho.push_back(A(plane));
-    w->apsi.push_back(A(plane));
     w->aux.push_back(A(plane));
     w->auy.push_back(A(plane));
   }
+  for (int j = 0; j <= K; ++j) w->apsi.push_back(A(plane));  // psi of slot K comes from the last energy pass
   for (int s = 0; s < nseg; ++s) {
     w->cf.push_back(A(fs));
     w->cT.push_back(A(plane));
@@ -98,11 +106,15 @@ lbm_status prepare(lbm_ctx* c, int K, int nseg) {
     adjoint_release(c);
     return fail(c, LBM_ENOMEM, "device allocation for the adjoint (K = %d, %d checkpoints) failed", K, nseg);
   }
+  if ((c->f64 ? lbm::adjoint_setup_f64() : lbm::adjoint_setup_f32()) < 0)
+    return fail(c, LBM_ECUDA, "adjoint kernel set-up failed: %s", cudaGetErrorString(cudaGetLastError()));
   return LBM_OK;
 }
 
-// Forward step of slot j into slot j + 1, keeping the collision fields of slot j.
-int forward_slot(lbm_ctx* c, lbm_adjoint_work* w, int j) {
+// Forward step of slot j into slot j + 1, keeping the collision fields of slot j.  Within a
+// segment the energy pass of step j makes psi of step j + 1, so only the first step runs the psi
+// pass.
+int forward_slot(lbm_ctx* c, lbm_adjoint_work* w, int j, cudaStream_t st) {
   lbm::Dev v = c->dev;
   v.f[0] = w->sf[j];
   v.f[1] = w->sf[j + 1];
@@ -112,14 +124,16 @@ int forward_slot(lbm_ctx* c, lbm_adjoint_work* w, int j) {
   v.side[1] = w->sside[j + 1];
   v.rho = w->arho[j];
   v.psi = w->apsi[j];
+  v.psi_next = w->apsi[j + 1];
   v.ux = w->aux[j];
   v.uy = w->auy[j];
   v.hf = w->hf;
   v.nb = 0;  // the recompute needs no heat-flux sample
   int flipped = 0;
-  const int k = c->f64 ? lbm::step_f64(c->geo, c->ph, v, 0, 0, 1, 1, c->prm.psi_mode, c->stream, nullptr, &flipped)
-                       : lbm::step_f32(c->geo, c->ph, v, 0, 0, 1, 1, c->prm.psi_mode, c->prm.storage, c->stream,
-                                       nullptr, &flipped);
+  lbm::PsiChain chain{j > 0 ? 1 : 0, 1, 0};
+  const int k = c->f64 ? lbm::step_f64(c->geo, c->ph, v, 0, 0, 1, 1, c->prm.psi_mode, st, nullptr, &flipped, &chain)
+                       : lbm::step_f32(c->geo, c->ph, v, 0, 0, 1, 1, c->prm.psi_mode, c->prm.storage, st, nullptr,
+                                       &flipped, &chain);
   return k < 0 || !flipped ? -1 : k;
 }
 
@@ -158,9 +172,53 @@ lbm::AdjArgs<C> make_args(lbm_ctx* c, lbm_adjoint_work* w, int j, int ping, doub
   return a;
 }
 
-int reverse_slot(lbm_ctx* c, lbm_adjoint_work* w, int j, int ping, double wq) {
-  return c->f64 ? lbm::adjoint_step_f64(make_args<double>(c, w, j, ping, wq), c->stream)
-                : lbm::adjoint_step_f32(make_args<float>(c, w, j, ping, wq), c->stream);
+int reverse_slot(lbm_ctx* c, lbm_adjoint_work* w, int j, int ping, double wq, cudaStream_t st) {
+  return c->f64 ? lbm::adjoint_step_f64(make_args<double>(c, w, j, ping, wq), st)
+                : lbm::adjoint_step_f32(make_args<float>(c, w, j, ping, wq), st);
+}
+
+// Recompute a segment of len steps from state slot 0 and run its reverse steps, the first with
+// adjoint buffers [ping]; on stream st.  Returns false on a launch error.
+bool segment_launches(lbm_ctx* c, lbm_adjoint_work* w, int len, int ping, double wq, cudaStream_t st) {
+  for (int j = 0; j < len; ++j)
+    if (forward_slot(c, w, j, st) < 0) return false;
+  for (int j = len - 1; j >= 0; --j) {
+    if (reverse_slot(c, w, j, ping, wq, st) < 0) return false;
+    ping ^= 1;
+  }
+  return true;
+}
+
+// The same from a cached CUDA graph (captured on first use).
+lbm_status segment_graph(lbm_ctx* c, lbm_adjoint_work* w, int len, int ping, double wq) {
+  if (!w->gs) {
+    LBM_CUDA(c, cudaStreamCreateWithFlags(&w->gs, cudaStreamNonBlocking));
+    LBM_CUDA(c, cudaEventCreateWithFlags(&w->ev_in, cudaEventDisableTiming));
+    LBM_CUDA(c, cudaEventCreateWithFlags(&w->ev_out, cudaEventDisableTiming));
+  }
+  const auto key = std::make_tuple(len, ping, wq);
+  auto it = w->graphs.find(key);
+  if (it == w->graphs.end()) {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    LBM_CUDA(c, cudaStreamBeginCapture(w->gs, cudaStreamCaptureModeThreadLocal));
+    const bool ok = segment_launches(c, w, len, ping, wq, w->gs);
+    const cudaError_t e = cudaStreamEndCapture(w->gs, &graph);
+    if (!ok || e != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      return fail(c, LBM_ECUDA, "capture of the adjoint segment failed: %s", cudaGetErrorString(cudaGetLastError()));
+    }
+    const cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ei != cudaSuccess) return fail(c, LBM_ECUDA, "graph instantiation failed: %s", cudaGetErrorString(ei));
+    it = w->graphs.emplace(key, exec).first;
+  }
+  LBM_CUDA(c, cudaEventRecord(w->ev_in, c->stream));
+  LBM_CUDA(c, cudaStreamWaitEvent(w->gs, w->ev_in, 0));
+  LBM_CUDA(c, cudaGraphLaunch(it->second, w->gs));
+  LBM_CUDA(c, cudaEventRecord(w->ev_out, w->gs));
+  LBM_CUDA(c, cudaStreamWaitEvent(c->stream, w->ev_out, 0));
+  return LBM_OK;
 }
 int aux(lbm_ctx* c, int op, const void* src, void* dst) {
   return c->f64 ? lbm::adjoint_aux_f64(op, c->geo, c->dev.mask, src, dst, c->stream)
@@ -283,6 +341,13 @@ namespace host {
 void adjoint_release(lbm_ctx* c) {
   if (!c->adjw) return;
   cudaStreamSynchronize(c->stream);
+  for (auto& kv : c->adjw->graphs) cudaGraphExecDestroy(kv.second);
+  if (c->adjw->gs) {
+    cudaStreamSynchronize(c->adjw->gs);
+    cudaStreamDestroy(c->adjw->gs);
+  }
+  if (c->adjw->ev_in) cudaEventDestroy(c->adjw->ev_in);
+  if (c->adjw->ev_out) cudaEventDestroy(c->adjw->ev_out);
   for (void* p : c->adjw->blocks) {
     if (c->has_alloc) c->alloc.free(p, c->alloc.user);
     else cudaFree(p);
@@ -303,13 +368,13 @@ lbm_status lbm_adjoint_step(lbm_ctx* c, const double* fb, const double* Tb, cons
   if ((st = prepare(c, 1, 0)) != LBM_OK) return st;
   lbm_adjoint_work* w = c->adjw;
   if ((st = copy_state(c, w->sf[0], w->sT[0], w->sside[0], false)) != LBM_OK) return st;
-  if (forward_slot(c, w, 0) < 0) return fail(c, LBM_ECUDA, "forward step of the adjoint failed");
+  if (forward_slot(c, w, 0, c->stream) < 0) return fail(c, LBM_ECUDA, "forward step of the adjoint failed");
   if ((st = zero_adjoint(c, w, 0)) != LBM_OK) return st;
   if ((st = upload_planes(c, fb, w->fb[0], 9)) != LBM_OK) return st;
   if ((st = upload_planes(c, Tb, w->Tb[0], 1)) != LBM_OK) return st;
   if (sb && (st = side_io(c, w->sb[0], const_cast<double*>(sb), true)) != LBM_OK) return st;
   const double wq = c->dev.nb > 0 ? q_weight / c->dev.nb : 0.0;
-  if (reverse_slot(c, w, 0, 0, wq) < 0) return fail(c, LBM_ECUDA, "reverse step failed");
+  if (reverse_slot(c, w, 0, 0, wq, c->stream) < 0) return fail(c, LBM_ECUDA, "reverse step failed");
   if ((st = download_planes(c, w->fb[1], fb_out, 9)) != LBM_OK) return st;
   if ((st = download_planes(c, w->Tb[1], Tb_out, 1)) != LBM_OK) return st;
   if (sb_out && (st = side_io(c, w->sb[1], sb_out, false)) != LBM_OK) return st;
@@ -332,6 +397,7 @@ lbm_status lbm_adjoint_window(lbm_ctx* c, int64_t n, int32_t ckpt_every, lbm_win
   lbm_adjoint_work* w = c->adjw;
   // forward: the wall at its temperature, then the segments with their checkpoints
   if (aux(c, 0, c->wallT, c->dev.T[c->tcur]) < 0) return fail(c, LBM_ECUDA, "wall reset failed");
+  c->psi_pending = 0;  // T at the wall may have changed
   double hf0[4], hf1[4];
   LBM_CUDA(c, cudaMemcpyAsync(hf0, c->dev.hf, sizeof(hf0), cudaMemcpyDeviceToHost, c->stream));
   for (int s = 0; s < nseg; ++s) {
@@ -348,13 +414,9 @@ lbm_status lbm_adjoint_window(lbm_ctx* c, int64_t n, int32_t ckpt_every, lbm_win
   for (int s = nseg - 1; s >= 0; --s) {
     const int len = (int)std::min<int64_t>(K, n - (int64_t)s * K);
     if ((st = copy_slot(c, w->sf[0], w->sT[0], w->sside[0], w->cf[s], w->cT[s], w->cside[s])) != LBM_OK) return st;
-    for (int j = 0; j < len; ++j)
-      if (forward_slot(c, w, j) < 0) return fail(c, LBM_ECUDA, "recompute of segment %d failed", s);
-    for (int j = len - 1; j >= 0; --j) {
-      if (reverse_slot(c, w, j, ping, wq) < 0) return fail(c, LBM_ECUDA, "reverse step failed");
-      ping ^= 1;
-    }
-    c->launches += 8 * (int64_t)len;
+    if ((st = segment_graph(c, w, len, ping, wq)) != LBM_OK) return st;
+    ping ^= len & 1;
+    c->launches += 7 * (int64_t)len + 1;
   }
   if (aux(c, 1, w->Tb[ping], w->gw) < 0) return fail(c, LBM_ECUDA, "wall seed failed");
   std::vector<double> gw;

@@ -476,6 +476,7 @@ lbm_status lbm_create(const lbm_domain* domain, const lbm_cylinder* cyl, const l
   d.T[0] = dalloc(c, N * es);
   d.T[1] = dalloc(c, N * es);
   d.psi = dalloc(c, N * es);
+  d.psi_next = dalloc(c, N * es);
   d.rho = dalloc(c, N * es);
   d.ux = dalloc(c, N * es);
   d.uy = dalloc(c, N * es);
@@ -501,7 +502,7 @@ lbm_status lbm_create(const lbm_domain* domain, const lbm_cylinder* cyl, const l
   g.wall_q = dwq;
   g.wall_n = dwn;
   d.stage = static_cast<double*>(dalloc(c, sizeof(double) * (size_t)g.nx * g.ny * 6));
-  if (!d.f[0] || !d.f[1] || !d.T[0] || !d.T[1] || !d.psi || !d.rho || !d.ux || !d.uy || !d.side[0] ||
+  if (!d.f[0] || !d.f[1] || !d.T[0] || !d.T[1] || !d.psi || !d.psi_next || !d.rho || !d.ux || !d.uy || !d.side[0] ||
       !d.side[1] || !d.partial || !d.counter || !dmask || !dbn || !dbv || !d.hf || !d.status || !d.stage ||
       !dwidx || !dwq || !dwn) {
     dfree_all(c);
@@ -515,6 +516,7 @@ lbm_status lbm_create(const lbm_domain* domain, const lbm_cylinder* cyl, const l
     if (e == cudaSuccess && r != cudaSuccess) e = r;
   };
   chk(cudaMemsetAsync(d.psi, 0, N * es, c->stream));
+  chk(cudaMemsetAsync(d.psi_next, 0, N * es, c->stream));
   for (void* p : {d.side[0], d.side[1]}) chk(cudaMemsetAsync(p, 0, 3 * g.ny * es, c->stream));
   chk(cudaMemsetAsync(d.hf, 0, 4 * sizeof(double), c->stream));
   chk(cudaMemsetAsync(d.status, 0, sizeof(int), c->stream));
@@ -602,10 +604,14 @@ lbm_status lbm_step(lbm_ctx* c, int64_t n) {
   for (int64_t s = 0; s < n; ++s) {
     const int forcing = c->steps >= c->prm.warmup_steps;
     int flipped = 0;
+    // psi of this step may already have been made by the last energy pass (into psi_next)
+    if (c->psi_pending) std::swap(c->dev.psi, c->dev.psi_next);
+    lbm::PsiChain chain{c->psi_pending, 1, 0};
     const int k = c->f64 ? lbm::step_f64(c->geo, c->ph, c->dev, c->cur, c->tcur, forcing, c->prm.energy,
-                                         c->prm.psi_mode, c->stream, hk, &flipped)
+                                         c->prm.psi_mode, c->stream, hk, &flipped, &chain)
                          : lbm::step_f32(c->geo, c->ph, c->dev, c->cur, c->tcur, forcing, c->prm.energy,
-                                         c->prm.psi_mode, c->prm.storage, c->stream, hk, &flipped);
+                                         c->prm.psi_mode, c->prm.storage, c->stream, hk, &flipped, &chain);
+    c->psi_pending = chain.made;
     if (k < 0) return fail(c, LBM_ECUDA, "kernel launch failed: %s", cudaGetErrorString(cudaGetLastError()));
     c->launches += k;
     c->cur ^= 1;
@@ -690,6 +696,7 @@ lbm_status lbm_get_state(lbm_ctx* c, double* f, double* T, double* side, int64_t
 }
 
 lbm_status lbm_set_state(lbm_ctx* c, const double* f, const double* T, const double* side, int64_t steps) {
+  if (c) c->psi_pending = 0;  // the state changes: psi of the next step is no longer known
   if (!c) return LBM_EINVAL;
   const size_t M = (size_t)c->geo.nx * c->geo.ny;
   if (f)

@@ -25,6 +25,7 @@ struct lbm_ctx {
   int device = 0;
   int cur = 0;   // buffer index of f* and the outlet side values
   int tcur = 0;  // buffer index of T
+  int psi_pending = 0;  // dev.psi_next holds psi of the next step (made by the last energy pass)
   int64_t steps = 0;
   int64_t launches = 0;
   bool f64 = false;

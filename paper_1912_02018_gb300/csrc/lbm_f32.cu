@@ -10,21 +10,21 @@ namespace lbm {
 namespace {
 template <typename S>
 int step_s(const Geo& g, const Phys& ph, const Dev& d, int cur, int tcur, int forcing, int energy, int psi_mode,
-           cudaStream_t s, const LaunchHook* hook, int* t_flipped) {
+           cudaStream_t s, const LaunchHook* hook, int* t_flipped, PsiChain* chain) {
   switch (psi_mode) {
-    case kPsiF64: return step_impl<float, S, kPsiF64>(g, ph, d, cur, tcur, forcing, energy, s, hook, t_flipped);
-    case kPsiF32: return step_impl<float, S, kPsiF32>(g, ph, d, cur, tcur, forcing, energy, s, hook, t_flipped);
-    default: return step_impl<float, S, kPsiDF>(g, ph, d, cur, tcur, forcing, energy, s, hook, t_flipped);
+    case kPsiF64: return step_impl<float, S, kPsiF64>(g, ph, d, cur, tcur, forcing, energy, s, hook, t_flipped, chain);
+    case kPsiF32: return step_impl<float, S, kPsiF32>(g, ph, d, cur, tcur, forcing, energy, s, hook, t_flipped, chain);
+    default: return step_impl<float, S, kPsiDF>(g, ph, d, cur, tcur, forcing, energy, s, hook, t_flipped, chain);
   }
 }
 }  // namespace
 
 int step_f32(const Geo& g, const Phys& ph, const Dev& d, int cur, int tcur, int forcing, int energy, int psi_mode,
-             int storage, cudaStream_t s, const LaunchHook* hook, int* t_flipped) {
+             int storage, cudaStream_t s, const LaunchHook* hook, int* t_flipped, PsiChain* chain) {
   switch (storage) {
-    case LBM_STORE_F64: return step_s<double>(g, ph, d, cur, tcur, forcing, energy, psi_mode, s, hook, t_flipped);
-    case LBM_STORE_F16S: return step_s<__half>(g, ph, d, cur, tcur, forcing, energy, psi_mode, s, hook, t_flipped);
-    default: return step_s<float>(g, ph, d, cur, tcur, forcing, energy, psi_mode, s, hook, t_flipped);
+    case LBM_STORE_F64: return step_s<double>(g, ph, d, cur, tcur, forcing, energy, psi_mode, s, hook, t_flipped, chain);
+    case LBM_STORE_F16S: return step_s<__half>(g, ph, d, cur, tcur, forcing, energy, psi_mode, s, hook, t_flipped, chain);
+    default: return step_s<float>(g, ph, d, cur, tcur, forcing, energy, psi_mode, s, hook, t_flipped, chain);
   }
 }
 int export_f32(const Geo& g, const Phys& ph, const Dev& d, int cur, int tcur, int which, int storage, double* dst,
@@ -63,6 +63,7 @@ int batch_step_f32(int variant, const BatchDomain* doms, const int* mp, int np, 
 }
 
 int adjoint_step_f32(const AdjArgs<float>& a, cudaStream_t s) { return adj::adjoint_step_impl<float>(a, s); }
+int adjoint_setup_f32() { return adj::adjoint_setup_impl<float>(); }
 int adjoint_aux_f32(int op, const Geo& g, const uint8_t* mask, const void* src, void* dst, cudaStream_t s) {
   const dim3 blk(32, 8), grd((g.nx + 31) / 32, (g.ny + 7) / 8);
   switch (op) {

@@ -7,9 +7,9 @@
 namespace lbm {
 
 int step_f64(const Geo& g, const Phys& ph, const Dev& d, int cur, int tcur, int forcing, int energy, int psi_mode,
-             cudaStream_t s, const LaunchHook* hook, int* t_flipped) {
+             cudaStream_t s, const LaunchHook* hook, int* t_flipped, PsiChain* chain) {
   (void)psi_mode;  // the FP64 build always evaluates psi in IEEE FP64
-  return step_impl<double, double, kPsiF64>(g, ph, d, cur, tcur, forcing, energy, s, hook, t_flipped);
+  return step_impl<double, double, kPsiF64>(g, ph, d, cur, tcur, forcing, energy, s, hook, t_flipped, chain);
 }
 int export_f64(const Geo& g, const Phys& ph, const Dev& d, int cur, int tcur, int which, double* dst, cudaStream_t s) {
   return export_impl<double, double>(g, ph, d, cur, tcur, which, dst, s);
@@ -32,6 +32,7 @@ int batch_step_f64(int variant, const BatchDomain* doms, const int* mp, int np, 
 }
 
 int adjoint_step_f64(const AdjArgs<double>& a, cudaStream_t s) { return adj::adjoint_step_impl<double>(a, s); }
+int adjoint_setup_f64() { return adj::adjoint_setup_impl<double>(); }
 int adjoint_aux_f64(int op, const Geo& g, const uint8_t* mask, const void* src, void* dst, cudaStream_t s) {
   const dim3 blk(32, 8), grd((g.nx + 31) / 32, (g.ny + 7) / 8);
   switch (op) {

@@ -60,6 +60,7 @@ struct Dev {
   void* f[2];        // populations, 9 planes each (ping-pong)
   void* T[2];        // temperature (ping-pong)
   void* psi;         // pseudopotential of the current step
+  void* psi_next;    // pseudopotential of the next step, when the energy pass computed it
   void* rho;         // density of the last collision
   void* ux;          // velocity of the last collision
   void* uy;
@@ -120,15 +121,22 @@ struct LaunchHook {
   void* self;
 };
 
+// psi of the next step from the energy pass: have = d.psi already holds psi of this step (no
+// psi pass), want = the energy pass should write psi of the next step into d.psi_next; made is
+// set when it did.
+struct PsiChain {
+  int have, want, made;
+};
+
 // Step launchers (one per precision build).  cur: index of the buffers holding f* and the
 // outlet side values; tcur: index of the temperature buffer.  The step writes f*, side into
 // [cur ^ 1] and, when it runs the energy equation, T into [tcur ^ 1] (*t_flipped = 1).
 // Returns the number of kernels launched, or -1 on a launch error.
 int step_f64(const Geo& g, const Phys& ph, const Dev& d, int cur, int tcur, int forcing, int energy, int psi_mode,
-             cudaStream_t s, const LaunchHook* hook, int* t_flipped);
+             cudaStream_t s, const LaunchHook* hook, int* t_flipped, PsiChain* chain = nullptr);
 // FP32 compute with population storage `storage` (lbm_storage: 0 FP64, 1 FP32, 2 shifted FP16).
 int step_f32(const Geo& g, const Phys& ph, const Dev& d, int cur, int tcur, int forcing, int energy, int psi_mode,
-             int storage, cudaStream_t s, const LaunchHook* hook, int* t_flipped);
+             int storage, cudaStream_t s, const LaunchHook* hook, int* t_flipped, PsiChain* chain = nullptr);
 
 // Field export: copy a typed [ny][pitch] field (which: 0 rho, 1 ux, 2 uy, 3 T, 4 psi, 5 solid,
 // 10+i population plane i of buffer cur, 20+j outlet side row j of buffer cur) into a dense
@@ -189,6 +197,9 @@ struct AdjArgs {
 // One reverse step of the time step (8 launches); returns the number of launches or -1.
 int adjoint_step_f32(const AdjArgs<float>& a, cudaStream_t s);
 int adjoint_step_f64(const AdjArgs<double>& a, cudaStream_t s);
+// Per-device set-up of the adjoint kernels (shared-memory opt-in); 0 or -1.
+int adjoint_setup_f32();
+int adjoint_setup_f64();
 // Plane helpers of the adjoint: op 0 T[solid] = wallT (src wallT, dst T); op 1 gw[solid] +=
 // Tb (src Tb, dst gw doubles); op 2 dense doubles -> typed plane; op 3 typed plane -> dense.
 int adjoint_aux_f32(int op, const Geo& g, const uint8_t* mask, const void* src, void* dst, cudaStream_t s);

@@ -368,17 +368,17 @@ template <typename C, typename S>
 __device__ __forceinline__ void pull_node(const Geo& g, const Phys& ph, const S* __restrict__ f,
                                           const uint8_t* __restrict__ mask, const C* __restrict__ side_in,
                                           C* __restrict__ side_out, int x, int y, uint8_t m, C fo[9]) {
-  const bool edge = !g.periodic_x && (x == 0 || x == g.nx - 1);
-  if ((m & kNearWall) || edge) {
-    pull_slow<C, S>(g, ph, f, mask, side_in, side_out, x, y, fo);
-    return;
-  }
+  // the plain pulls are issued before the node type is tested (columns clamped at an open
+  // edge), so they overlap the mask read; wall and edge nodes then redo the pull
   const int ym = y == 0 ? g.ny - 1 : y - 1;
   const int yp = y == g.ny - 1 ? 0 : y + 1;
   int xm = x - 1, xp = x + 1;
   if (g.periodic_x) {
     xm = xm < 0 ? g.nx - 1 : xm;
     xp = xp >= g.nx ? 0 : xp;
+  } else {
+    xm = xm < 0 ? 0 : xm;
+    xp = xp >= g.nx ? g.nx - 1 : xp;
   }
   fo[0] = ldf<C>(g, ph, f, 0, y, x);
   fo[1] = ldf<C>(g, ph, f, 1, y, xm);
@@ -389,6 +389,8 @@ __device__ __forceinline__ void pull_node(const Geo& g, const Phys& ph, const S*
   fo[6] = ldf<C>(g, ph, f, 6, yp, xp);
   fo[7] = ldf<C>(g, ph, f, 7, yp, xm);
   fo[8] = ldf<C>(g, ph, f, 8, ym, xp);
+  const bool edge = !g.periodic_x && (x == 0 || x == g.nx - 1);
+  if ((m & kNearWall) || edge) pull_slow<C, S>(g, ph, f, mask, side_in, side_out, x, y, fo);
 }
 
 // psi at node (x, y): pull, rho = sum f, Eq. (potential); solid nodes use rho_s.
@@ -398,17 +400,14 @@ __device__ __forceinline__ C psi_node(const Geo& g, const Phys& ph, const S* __r
                                       const C* __restrict__ side_in, int x, int y, int* status) {
   const int id = y * g.pitch + x;
   const uint8_t m = mask[id];
-  C rho;
-  if (m & kSolid) {
-    rho = pc<C>(ph).rho_s;
-  } else {
-    C fo[9];
-    pull_node<C, S>(g, ph, f, mask, side_in, nullptr, x, y, m, fo);
-    rho = fo[0];
+  const C t = T[id];
+  C fo[9];
+  pull_node<C, S>(g, ph, f, mask, side_in, nullptr, x, y, m, fo);
+  C rho = fo[0];
 #pragma unroll
-    for (int i = 1; i < 9; ++i) rho = rho + fo[i];
-  }
-  return psi_of<C, PSI>(ph, rho, T[id], status);
+  for (int i = 1; i < 9; ++i) rho = rho + fo[i];
+  if (m & kSolid) rho = pc<C>(ph).rho_s;
+  return psi_of<C, PSI>(ph, rho, t, status);
 }
 
 // ---------------------------------------------------------------- CM collision (Sec. II.A-B)
@@ -702,12 +701,17 @@ struct EnergyTile {
 
 // Both Heun stages on tile (bx, by); bid, nblocks: this tile's index among the domain's
 // nblocks tiles (for the heat-flux partials and the last-block reduction).
-template <typename C, int ETY>
+// With FUSE, and psi_out set, the tile also evaluates psi of the next step at its nodes: the
+// pull of the populations this step's collision wrote (fnew, side_new), rho their sum (rho_s
+// in the solid), T the new temperature (Eq. potential) -- the next step then needs no psi pass.
+template <typename C, int ETY, typename S = C, int PSI = kPsiF64, bool FUSE = false>
 __device__ __forceinline__ void energy_tile(const Geo& g, const Phys& ph, const C* __restrict__ Tin,
                                             C* __restrict__ Tout, const C* __restrict__ rho, const C* __restrict__ ux,
                                             const C* __restrict__ uy, const uint8_t* __restrict__ mask,
                                             double* partial, unsigned* counter, double* hf, int nb, int do_hf,
-                                            int n_wall_tiles, int bx, int by, int bid, int nblocks) {
+                                            int n_wall_tiles, int bx, int by, int bid, int nblocks,
+                                            const S* __restrict__ fnew = nullptr, const C* __restrict__ side_new = nullptr,
+                                            C* __restrict__ psi_out = nullptr, int* status = nullptr) {
   constexpr int TX = EnergyTile<C, ETY>::TX, TY = EnergyTile<C, ETY>::TY, NT = EnergyTile<C, ETY>::NT;
   constexpr int H = 4, AX = TX + 2 * H, AY = TY + 2 * H;  // inputs: tile + 4
   constexpr int BX = TX + 4, BY = TY + 4;                 // stage 1: tile + 2
@@ -777,6 +781,7 @@ __device__ __forceinline__ void energy_tile(const Geo& g, const Phys& ph, const 
   energy_rhs_pair(ph, &sT1[b], BX, &sU[a], &sV[a], &sR[a], fz, L);
   double q = 0.0;
   const int y = y0 + ty;
+  C tnew[2];
 #pragma unroll
   for (int k = 0; k < 2; ++k) {
     const int x = x0 + tx + k;
@@ -786,12 +791,31 @@ __device__ __forceinline__ void energy_tile(const Geo& g, const Phys& ph, const 
       else if (!g.periodic_x && x == 0) out = pc<C>(ph).T_sat;
       else out = ((sT[a + k] + sT1[b + k]) + L[k]) * C(0.5);
       Tout[y * g.pitch + x] = out;
+      tnew[k] = out;
       if (do_hf && (sM[a + k] & kNearWall)) {
         // wall heat flux -lambda grad T . n at this boundary node, from T^n (Sec. IV.B)
         C gx, gy;
         grad_t(&sT[a + k], AX, gx, gy);
         const double* nv = &g.wall_n[2 * g.wall_idx[y * g.pitch + x]];
         q += -(double)sL[a + k] * ((double)gx * nv[0] + (double)gy * nv[1]);
+      }
+    }
+  }
+  if constexpr (FUSE) {
+    if (psi_out) {
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        const int x = x0 + tx + k;
+        if (x < g.nx && y < g.ny) {
+          const uint8_t m = sM[a + k];
+          C fo[9];
+          pull_node<C, S>(g, ph, fnew, mask, side_new, nullptr, x, y, m, fo);
+          C r = fo[0];
+#pragma unroll
+          for (int i = 1; i < 9; ++i) r = r + fo[i];
+          if (m & kSolid) r = pc<C>(ph).rho_s;
+          psi_out[y * g.pitch + x] = psi_of<C, PSI>(ph, r, tnew[k], status);
+        }
       }
     }
   }
@@ -827,14 +851,15 @@ __device__ __forceinline__ void energy_tile(const Geo& g, const Phys& ph, const 
     }
   }
 }
-template <typename C>
+template <typename C, typename S, int PSI>
 __global__ void __launch_bounds__(EnergyTile<C>::NT)
     k_energy(Geo g, Phys ph, const C* __restrict__ Tin, C* __restrict__ Tout, const C* __restrict__ rho,
              const C* __restrict__ ux, const C* __restrict__ uy, const uint8_t* __restrict__ mask,
-             double* partial, unsigned* counter, double* hf, int nb, int do_hf, int n_wall_tiles) {
-  energy_tile<C, EnergyTile<C>::TY>(g, ph, Tin, Tout, rho, ux, uy, mask, partial, counter, hf, nb, do_hf,
-                                    n_wall_tiles, blockIdx.x,
-                                    blockIdx.y, blockIdx.y * gridDim.x + blockIdx.x, gridDim.x * gridDim.y);
+             double* partial, unsigned* counter, double* hf, int nb, int do_hf, int n_wall_tiles,
+             const S* __restrict__ fnew, const C* __restrict__ side_new, C* __restrict__ psi_out, int* status) {
+  energy_tile<C, EnergyTile<C>::TY, S, PSI, true>(g, ph, Tin, Tout, rho, ux, uy, mask, partial, counter, hf, nb,
+                                                   do_hf, n_wall_tiles, blockIdx.x,
+                                    blockIdx.y, blockIdx.y * gridDim.x + blockIdx.x, gridDim.x * gridDim.y, fnew, side_new, psi_out, status);
 }
 
 // ---------------------------------------------------------------- batched passes
@@ -1003,7 +1028,7 @@ __global__ void k_import(Geo g, E* __restrict__ dst, int dst_pitch, int rows, co
 // ---------------------------------------------------------------- launchers
 template <typename C, typename S, int PSI>
 int step_impl(const Geo& g, const Phys& ph, const Dev& d, int cur, int tcur, int forcing, int energy, cudaStream_t s,
-              const LaunchHook* hook, int* t_flipped) {
+              const LaunchHook* hook, int* t_flipped, PsiChain* chain) {
   using namespace kern;
   const S* f = static_cast<const S*>(d.f[cur]);
   S* fn = static_cast<S*>(d.f[cur ^ 1]);
@@ -1024,7 +1049,7 @@ int step_impl(const Geo& g, const Phys& ph, const Dev& d, int cur, int tcur, int
     ++n;
   };
   const dim3 blk(kCollTX, kCollTY), grd((g.nx + kCollTX - 1) / kCollTX, (g.ny + kCollTY - 1) / kCollTY);
-  if (ph.d.G != 0.0) {
+  if (ph.d.G != 0.0 && !(chain && chain->have)) {
     pre(kKRhoPsi);
     k_rho_psi<C, S, PSI><<<grd, blk, 0, s>>>(g, ph, f, T, d.mask, side_in, psi, d.status);
     post(kKRhoPsi);
@@ -1038,10 +1063,15 @@ int step_impl(const Geo& g, const Phys& ph, const Dev& d, int cur, int tcur, int
     using ET = EnergyTile<C>;
     const dim3 blk(ET::NT), grd((g.nx + ET::TX - 1) / ET::TX, (g.ny + ET::TY - 1) / ET::TY);
     pre(kKEnergy);
-    k_energy<C><<<grd, blk, 0, s>>>(g, ph, T, Tn, rho, ux, uy, d.mask, d.partial, d.counter, d.hf, d.nb, do_hf,
-                                    d.wall_tiles[ET::TY == 16 ? 1 : 0]);
+    const bool fuse = chain && chain->want && ph.d.G != 0.0;
+    k_energy<C, S, PSI><<<grd, blk, 0, s>>>(g, ph, T, Tn, rho, ux, uy, d.mask, d.partial, d.counter, d.hf, d.nb,
+                                            do_hf, d.wall_tiles[ET::TY == 16 ? 1 : 0], fuse ? fn : nullptr,
+                                            side_out, fuse ? static_cast<C*>(d.psi_next) : nullptr, d.status);
     post(kKEnergy);
     *t_flipped = 1;
+    if (chain) chain->made = fuse ? 1 : 0;
+  } else if (chain) {
+    chain->made = 0;
   }
   return cudaPeekAtLastError() == cudaSuccess ? n : -1;
 }
