@@ -217,6 +217,23 @@ def run_batch(args):
     return 0
 
 
+def max_over_ranks(x: float, world: int, device: str = "cuda") -> float:
+    """The largest of the ranks' values (replica timing: the job is as slow as its slowest rank)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_mlups(nodes: int, steps: int, world: int, seconds: float) -> float:
+    """Whole-job throughput of `world` replicas that each updated `nodes` nodes `steps` times."""
+    return nodes * steps * world / seconds / 1e6
+
+
 def adjoint_cost(window=500, ckpt_every=50, spin_up=2000):
     """Cost of the adjoint window against the forward steps it differentiates, on the
     512 x 256 lattice, D = 32, Re = 300 (FP32 forward and adjoint fields, FP64 parameter
@@ -302,11 +319,8 @@ def run_ours(args):
     prof = sim.profile_read()
     sim.profile(False)
     launches = sim.info()["kernel_launches"] - launches0
-    if world > 1:
-        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = nodes * args.steps * world / (ms / 1e3) / 1e6
+    ms = max_over_ranks(ms, world)
+    value = aggregate_mlups(nodes, args.steps, world, ms / 1e3)
 
     # end to end through the C ABI with pinned host buffers
     f0, T0, side0, n0 = sim.get_state()
@@ -329,11 +343,8 @@ def run_ours(args):
         N.check(L.lbm_fields(sim.h, N.FIELD_BITS["T"], out_h.data_ptr(), out_h.numel() * 8, 0), sim.h)
         sim.heat_flux()
     e2e_s = time.perf_counter() - t
-    if world > 1:
-        tt = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_s = float(tt.item())
-    e2e = {"value": nodes * e2e_steps * world / e2e_s / 1e6, "unit": UNIT,
+    e2e_s = max_over_ranks(e2e_s, world)
+    e2e = {"value": aggregate_mlups(nodes, e2e_steps, world, e2e_s), "unit": UNIT,
            "h2d_bytes_per_step": int(f_h.numel() * 8 + T_h.numel() * 8),
            "d2h_bytes_per_step": int(out_h.numel() * 8 + 5 * 8), "steps": e2e_steps}
 
