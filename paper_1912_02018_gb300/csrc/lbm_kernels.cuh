@@ -692,6 +692,108 @@ __device__ __forceinline__ void energy_rhs_pair(const Phys& ph, const C* t, int 
   }
 }
 
+// FP32: the two nodes of a pair are one packed float2 throughout the stencil sums (sm_100+
+// FFMA2/FADD2/FMUL2), halving the FP32 instructions of the energy pass.  The window of a pair
+// is kept as aligned column pairs A[r][j] = (c_2j, c_2j+1) and shifted pairs B[r][j] =
+// (c_2j+1, c_2j+2); the value pair at offset ex is A[r][1 + ex/2] for even ex, B[r][(1 + ex)/2]
+// for odd ex.  Each packed operation rounds like the scalar one it replaces.
+struct Win2 {
+  float2 A[5][3], B[5][2];
+};
+__device__ __forceinline__ void load_win2(const float* p, int s, Win2& W) {
+#pragma unroll
+  for (int r = 0; r < 5; ++r) {
+    const float2* q = reinterpret_cast<const float2*>(p + (r - 2) * s - 2);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) W.A[r][c] = q[c];
+    W.B[r][0] = make_float2(W.A[r][0].y, W.A[r][1].x);
+    W.B[r][1] = make_float2(W.A[r][1].y, W.A[r][2].x);
+  }
+}
+__device__ __forceinline__ float2 win_at(const Win2& W, int r, int ex) {
+  return (ex & 1) ? W.B[r][(1 + ex) / 2] : W.A[r][1 + ex / 2];
+}
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
+template <bool kX = true, bool kY = true>
+__device__ __forceinline__ void grad_w2(const Win2& W, float2& gx, float2& gy) {
+  float2 sx = f2(0.f), sy = f2(0.f);
+#pragma unroll
+  for (int k = 0; k < 12; ++k) {
+    const int ex = exv(k), ey = eyv(k);
+    if ((kX && ex != 0) || (kY && ey != 0)) {
+      const float2 d = sub2(win_at(W, 2 + ey, ex), win_at(W, 2 - ey, -ex));
+      if (kX && ex != 0) sx = __ffma2_rn(f2(float(wiso(k) * ex)), d, sx);
+      if (kY && ey != 0) sy = __ffma2_rn(f2(float(wiso(k) * ey)), d, sy);
+    }
+  }
+  gx = sx;
+  gy = sy;
+}
+__device__ __forceinline__ float2 lap_w2(const Win2& W) {
+  const float2 c = W.A[2][1];
+  float2 acc = f2(0.f);
+#pragma unroll
+  for (int k = 0; k < 12; ++k) {
+    const int ex = exv(k), ey = eyv(k);
+    const float2 d = __ffma2_rn(c, f2(-2.f), __fadd2_rn(win_at(W, 2 + ey, ex), win_at(W, 2 - ey, -ex)));
+    acc = __ffma2_rn(f2(float(wiso(k))), d, acc);
+  }
+  return __fmul2_rn(f2(2.f), acc);
+}
+// Third-order upwind derivative of the pair along x (row 2) or y (column pair 1), each node
+// biased against the sign of its own velocity v.
+__device__ __forceinline__ float2 upwind_w2(const Win2& W, bool along_x, float2 v) {
+  float2 q[5];
+#pragma unroll
+  for (int o = -2; o <= 2; ++o) q[o + 2] = along_x ? win_at(W, 2, o) : W.A[2 + o][1];
+  const float2 c = q[2];
+  const float2 m2 = sub2(q[0], c), m1 = sub2(q[1], c), p1 = sub2(q[3], c), p2 = sub2(q[4], c);
+  const float2 pos = __ffma2_rn(f2(2.f), p1, __ffma2_rn(f2(-6.f), m1, m2));
+  const float2 neg = sub2(__ffma2_rn(f2(6.f), p1, __fmul2_rn(f2(-2.f), m1)), p2);
+  return make_float2(__fdividef(v.x >= 0.f ? pos.x : neg.x, 6.f), __fdividef(v.y >= 0.f ? pos.y : neg.y, 6.f));
+}
+template <>
+__device__ __forceinline__ void frozen_pair<float>(const float* lam, const float* u, const float* v, int as,
+                                                   Frozen<float> fz[2]) {
+  Win2 W;
+  float2 lx, ly, dxux, dyuy, unused;
+  load_win2(lam, as, W);
+  fz[0].lam0 = W.A[2][1].x;
+  fz[1].lam0 = W.A[2][1].y;
+  grad_w2(W, lx, ly);
+  load_win2(u, as, W);
+  grad_w2<true, false>(W, dxux, unused);
+  load_win2(v, as, W);
+  grad_w2<false, true>(W, unused, dyuy);
+  const float2 dv = __fadd2_rn(dxux, dyuy);
+  fz[0].lx = lx.x, fz[0].ly = ly.x, fz[0].divu = dv.x;
+  fz[1].lx = lx.y, fz[1].ly = ly.y, fz[1].divu = dv.y;
+}
+template <>
+__device__ __forceinline__ void energy_rhs_pair<float>(const Phys& ph, const float* t, int ts, const float* u,
+                                                       const float* v, const float* r, const Frozen<float> fz[2],
+                                                       float L[2]) {
+  Win2 W;
+  load_win2(t, ts, W);
+  const float2 u2 = make_float2(u[0], u[1]), v2 = make_float2(v[0], v[1]);
+  const float2 conv = __ffma2_rn(u2, upwind_w2(W, true, u2), __fmul2_rn(v2, upwind_w2(W, false, v2)));
+  float2 gx, gy;
+  grad_w2(W, gx, gy);
+  const float2 lap = lap_w2(W);
+  const float2 diff = __ffma2_rn(make_float2(fz[0].lam0, fz[1].lam0), lap,
+                                 __ffma2_rn(make_float2(fz[0].lx, fz[1].lx), gx,
+                                            __fmul2_rn(make_float2(fz[0].ly, fz[1].ly), gy)));
+  const float c_v = ph.f.c_v;
+  const float T0[2] = {W.A[2][1].x, W.A[2][1].y};
+  const float cv[2] = {conv.x, conv.y}, df[2] = {diff.x, diff.y};
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const float work = T0[k] * dpdT_eos(ph, r[k], T0[k]) * fz[k].divu;
+    L[k] = -cv[k] + __fdividef(df[k], r[k] * c_v) - __fdividef(work, r[k] * c_v);
+  }
+}
+
 template <typename C, int TY_ = (sizeof(C) == 8 ? 8 : kEnergyTY)>
 struct EnergyTile {
   static constexpr int TX = kEnergyTX;
