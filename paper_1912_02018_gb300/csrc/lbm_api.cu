@@ -501,7 +501,8 @@ lbm_status lbm_create(const lbm_domain* domain, const lbm_cylinder* cyl, const l
   g.wall_idx = dwidx;
   g.wall_q = dwq;
   g.wall_n = dwn;
-  d.stage = static_cast<double*>(dalloc(c, sizeof(double) * (size_t)g.nx * g.ny * 6));
+  // staging planes for host I/O: a whole state (9 populations, T) and the outlet rows in one copy
+  d.stage = static_cast<double*>(dalloc(c, sizeof(double) * ((size_t)g.nx * g.ny * 10 + 3 * (size_t)g.ny)));
   if (!d.f[0] || !d.f[1] || !d.T[0] || !d.T[1] || !d.psi || !d.psi_next || !d.rho || !d.ux || !d.uy || !d.side[0] ||
       !d.side[1] || !d.partial || !d.counter || !dmask || !dbn || !dbv || !d.hf || !d.status || !d.stage ||
       !dwidx || !dwq || !dwn) {
@@ -659,64 +660,64 @@ lbm_status lbm_fields(lbm_ctx* c, uint32_t mask, void* dst, size_t bytes, int ds
   for (int b = 0; b < 6; ++b) planes += (mask >> b) & 1u;
   if (mask >> 6) return fail(c, LBM_EINVAL, "unknown field bits 0x%x", mask);
   if (bytes < planes * M * sizeof(double)) return fail(c, LBM_EINVAL, "dst too small for %d planes", planes);
-  double* out = static_cast<double*>(dst);
+  // every requested field into its staging plane, then one copy
+  int k = 0;
   for (int b = 0; b < 6; ++b) {
     if (!((mask >> b) & 1u)) continue;
-    if (do_export(c, b, c->dev.stage) < 0) return fail(c, LBM_ECUDA, "export kernel failed");
+    if (do_export(c, b, c->dev.stage + k * M) < 0) return fail(c, LBM_ECUDA, "export kernel failed");
     c->launches++;
-    LBM_CUDA(c, cudaMemcpyAsync(out, c->dev.stage, M * sizeof(double),
-                                dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
-    out += M;
+    ++k;
   }
+  if (k)
+    LBM_CUDA(c, cudaMemcpyAsync(dst, c->dev.stage, k * M * sizeof(double),
+                                dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
   return check_status(c);
 }
 
 lbm_status lbm_get_state(lbm_ctx* c, double* f, double* T, double* side, int64_t* steps) {
   if (!c) return LBM_EINVAL;
   const size_t M = (size_t)c->geo.nx * c->geo.ny;
-  if (f)
-    for (int i = 0; i < 9; ++i) {
-      if (do_export(c, 10 + i, c->dev.stage) < 0) return fail(c, LBM_ECUDA, "export kernel failed");
-      LBM_CUDA(c, cudaMemcpyAsync(f + i * M, c->dev.stage, M * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-      LBM_CUDA(c, cudaStreamSynchronize(c->stream));
-    }
-  if (T) {
-    if (do_export(c, 3, c->dev.stage) < 0) return fail(c, LBM_ECUDA, "export kernel failed");
-    LBM_CUDA(c, cudaMemcpyAsync(T, c->dev.stage, M * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  double* st = c->dev.stage;
+  if (f) {
+    for (int i = 0; i < 9; ++i)
+      if (do_export(c, 10 + i, st + i * M) < 0) return fail(c, LBM_ECUDA, "export kernel failed");
+    LBM_CUDA(c, cudaMemcpyAsync(f, st, 9 * M * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   }
-  if (side)
-    for (int j = 0; j < 3; ++j) {
-      if (do_export(c, 20 + j, c->dev.stage) < 0) return fail(c, LBM_ECUDA, "export kernel failed");
-      LBM_CUDA(c, cudaMemcpyAsync(side + j * c->geo.ny, c->dev.stage, c->geo.ny * sizeof(double),
-                                  cudaMemcpyDeviceToHost, c->stream));
-      LBM_CUDA(c, cudaStreamSynchronize(c->stream));
-    }
+  if (T) {
+    if (do_export(c, 3, st + 9 * M) < 0) return fail(c, LBM_ECUDA, "export kernel failed");
+    LBM_CUDA(c, cudaMemcpyAsync(T, st + 9 * M, M * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  }
+  if (side) {
+    for (int j = 0; j < 3; ++j)
+      if (do_export(c, 20 + j, st + 10 * M + j * c->geo.ny) < 0) return fail(c, LBM_ECUDA, "export kernel failed");
+    LBM_CUDA(c, cudaMemcpyAsync(side, st + 10 * M, 3 * c->geo.ny * sizeof(double), cudaMemcpyDeviceToHost,
+                                c->stream));
+  }
   if (steps) *steps = c->steps;
   return check_status(c);
 }
 
 lbm_status lbm_set_state(lbm_ctx* c, const double* f, const double* T, const double* side, int64_t steps) {
-  if (c) c->psi_pending = 0;  // the state changes: psi of the next step is no longer known
   if (!c) return LBM_EINVAL;
+  c->psi_pending = 0;  // the state changes: psi of the next step is no longer known
   const size_t M = (size_t)c->geo.nx * c->geo.ny;
-  if (f)
-    for (int i = 0; i < 9; ++i) {
-      LBM_CUDA(c, cudaMemcpyAsync(c->dev.stage, f + i * M, M * sizeof(double), cudaMemcpyHostToDevice, c->stream));
-      if (do_import(c, 10 + i, c->dev.stage) < 0) return fail(c, LBM_ECUDA, "import kernel failed");
-      LBM_CUDA(c, cudaStreamSynchronize(c->stream));
-    }
-  if (T) {
-    LBM_CUDA(c, cudaMemcpyAsync(c->dev.stage, T, M * sizeof(double), cudaMemcpyHostToDevice, c->stream));
-    if (do_import(c, 3, c->dev.stage) < 0) return fail(c, LBM_ECUDA, "import kernel failed");
-    LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+  double* st = c->dev.stage;
+  // one copy per part into the staging planes, then the conversions; the stream orders them
+  if (f) {
+    LBM_CUDA(c, cudaMemcpyAsync(st, f, 9 * M * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    for (int i = 0; i < 9; ++i)
+      if (do_import(c, 10 + i, st + i * M) < 0) return fail(c, LBM_ECUDA, "import kernel failed");
   }
-  if (side)
-    for (int j = 0; j < 3; ++j) {
-      LBM_CUDA(c, cudaMemcpyAsync(c->dev.stage, side + j * c->geo.ny, c->geo.ny * sizeof(double),
-                                  cudaMemcpyHostToDevice, c->stream));
-      if (do_import(c, 20 + j, c->dev.stage) < 0) return fail(c, LBM_ECUDA, "import kernel failed");
-      LBM_CUDA(c, cudaStreamSynchronize(c->stream));
-    }
+  if (T) {
+    LBM_CUDA(c, cudaMemcpyAsync(st + 9 * M, T, M * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    if (do_import(c, 3, st + 9 * M) < 0) return fail(c, LBM_ECUDA, "import kernel failed");
+  }
+  if (side) {
+    LBM_CUDA(c, cudaMemcpyAsync(st + 10 * M, side, 3 * c->geo.ny * sizeof(double), cudaMemcpyHostToDevice,
+                                c->stream));
+    for (int j = 0; j < 3; ++j)
+      if (do_import(c, 20 + j, st + 10 * M + j * c->geo.ny) < 0) return fail(c, LBM_ECUDA, "import kernel failed");
+  }
   if (steps >= 0) c->steps = steps;
   return check_status(c);
 }
