@@ -9,8 +9,8 @@ stages of the temperature equation).  Default workload: the paper-shaped single 
   value      MLUPS over the K timed steps, inputs resident in HBM, L2 flushed (a 256 MB
              write) before every timed step; CUDA events on the library's stream.
   e2e        the same metric through the C ABI with host buffers: each step restores the
-             state from pinned host memory (lbm_set_state), steps once and reads T back
-             (lbm_fields) plus the heat flux.
+             state from pinned host memory (lbm_set_state_native, the context's own formats),
+             steps once and reads T back (lbm_fields, doubles) plus the heat flux.
   roofline   the dominant kernel's algorithmic bytes per launch / its mean event-timed
              duration, against the measured HBM copy bandwidth.
   adjoint    cost of the checkpointed adjoint window (512 x 256, D = 32, 500 steps,
@@ -322,8 +322,9 @@ def run_ours(args):
     ms = max_over_ranks(ms, world)
     value = aggregate_mlups(nodes, args.steps, world, ms / 1e3)
 
-    # end to end through the C ABI with pinned host buffers
-    f0, T0, side0, n0 = sim.get_state()
+    # end to end through the C ABI with pinned host buffers: the state in the context's own
+    # formats (lbm_set_state_native), T read back as doubles (lbm_fields)
+    f0, T0, side0, n0 = sim.get_state_native()
     f_h = torch.from_numpy(f0).pin_memory()
     T_h = torch.from_numpy(T0).pin_memory()
     out_h = torch.empty((case.ny, case.nx), dtype=torch.float64).pin_memory()
@@ -338,14 +339,14 @@ def run_ours(args):
         dist.barrier()
     t = time.perf_counter()
     for _ in range(e2e_steps):
-        N.check(L.lbm_set_state(sim.h, f_h.data_ptr(), T_h.data_ptr(), None, -1), sim.h)
+        N.check(L.lbm_set_state_native(sim.h, f_h.data_ptr(), T_h.data_ptr(), None, -1), sim.h)
         N.check(L.lbm_step(sim.h, 1), sim.h)
         N.check(L.lbm_fields(sim.h, N.FIELD_BITS["T"], out_h.data_ptr(), out_h.numel() * 8, 0), sim.h)
         sim.heat_flux()
     e2e_s = time.perf_counter() - t
     e2e_s = max_over_ranks(e2e_s, world)
     e2e = {"value": aggregate_mlups(nodes, e2e_steps, world, e2e_s), "unit": UNIT,
-           "h2d_bytes_per_step": int(f_h.numel() * 8 + T_h.numel() * 8),
+           "h2d_bytes_per_step": int(f_h.numel() * f_h.element_size() + T_h.numel() * T_h.element_size()),
            "d2h_bytes_per_step": int(out_h.numel() * 8 + 5 * 8), "steps": e2e_steps}
 
     if rank != 0:

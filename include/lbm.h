@@ -200,6 +200,16 @@ lbm_status lbm_get_state(lbm_ctx *ctx, double *f, double *T, double *side, int64
  * returned there to keep the wall created with the context. */
 lbm_status lbm_set_state(lbm_ctx *ctx, const double *f, const double *T, const double *side, int64_t steps);
 
+/*
+ * The same checkpoint in the context's own number formats, without conversion: f* in the
+ * population storage type ([9][ny][nx]: double for LBM_STORE_F64, float for LBM_STORE_F32, IEEE
+ * half for LBM_STORE_F16S holding f_i - w_i rho_l), T and the outlet rows in the compute type
+ * (double with compute_f64, else float).  Half the bytes of the double form for an FP32
+ * context; a native checkpoint restores bit-for-bit.  Same NULL, steps and sync rules as above.
+ */
+lbm_status lbm_get_state_native(lbm_ctx *ctx, void *f, void *T, void *side, int64_t *steps);
+lbm_status lbm_set_state_native(lbm_ctx *ctx, const void *f, const void *T, const void *side, int64_t steps);
+
 /* Derived constants and counters. */
 lbm_status lbm_info(lbm_ctx *ctx, lbm_info_t *info);
 
@@ -272,8 +282,9 @@ typedef struct {
  * with lbm_step, heat-flux statistics included; T at solid nodes is first reset to T_w) and
  * return J and its gradient.  The reverse pass keeps a checkpoint every ckpt_every steps and
  * recomputes each segment from it: device memory (ckpt_every + 1 states, ckpt_every sets of
- * rho, psi, u, one state per checkpoint, 30 work planes) is allocated on first use through
- * the context's allocator and kept for later windows.  Synchronises.
+ * rho, psi, u and the stage-1 temperature, one state per checkpoint, 30 work planes) is
+ * allocated on first use through the context's allocator and kept for later windows.
+ * Synchronises.
  */
 lbm_status lbm_adjoint_window(lbm_ctx *ctx, int64_t n_steps, int32_t ckpt_every, lbm_window_grad *out);
 

@@ -21,7 +21,8 @@ FIELD_BITS = {"rho": 1, "ux": 2, "uy": 4, "T": 8, "psi": 16, "solid": 32}
 EXPORTS = ("lbm_create", "lbm_step", "lbm_sync", "lbm_wall_heat_flux", "lbm_reset_heat_flux", "lbm_fields",
            "lbm_get_state", "lbm_set_state", "lbm_info", "lbm_profile", "lbm_profile_read", "lbm_last_error",
            "lbm_destroy", "lbm_wall_heat_flux_noalloc", "lbm_batch_create", "lbm_batch_step", "lbm_batch_tune",
-           "lbm_batch_graph", "lbm_batch_domain", "lbm_batch_destroy", "lbm_adjoint_window", "lbm_adjoint_step")
+           "lbm_batch_graph", "lbm_batch_domain", "lbm_batch_destroy", "lbm_adjoint_window", "lbm_adjoint_step",
+           "lbm_get_state_native", "lbm_set_state_native")
 
 
 class Domain(C.Structure):
@@ -90,6 +91,8 @@ def lib():
     L.lbm_fields.argtypes = [vp, C.c_uint32, vp, C.c_size_t, C.c_int]
     L.lbm_get_state.argtypes = [vp, vp, vp, vp, C.POINTER(i64)]
     L.lbm_set_state.argtypes = [vp, vp, vp, vp, i64]
+    L.lbm_get_state_native.argtypes = [vp, vp, vp, vp, C.POINTER(i64)]
+    L.lbm_set_state_native.argtypes = [vp, vp, vp, vp, i64]
     L.lbm_info.argtypes = [vp, C.POINTER(Info)]
     L.lbm_profile.argtypes = [vp, C.c_int]
     L.lbm_profile_read.argtypes = [vp, C.POINTER(C.c_char_p), C.POINTER(i64), dp, C.c_int32,

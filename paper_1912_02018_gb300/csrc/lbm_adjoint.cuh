@@ -170,34 +170,32 @@ __device__ __forceinline__ Parts<C> parts_at(const C* t, int ts, const C* l, con
 
 // ---------------------------------------------------------------- energy adjoint (Heun stages)
 // One kernel per stage, on tiles of 32 x 16 nodes.  Stage 2 (seed Tb_in / 2 on L(T1) at the
-// interior fluid nodes) loads T, rho, lambda, u on the tile + 6, recomputes T1 on the tile + 4,
-// forms the sources of the transposed stencils on the tile + 2 and gathers them at the tile's
-// nodes: Tb1, the adjoint of T1.  Stage 1 (seed Tb1 on L(T), plus the heat-flux sample) does
-// the same from T on the tile + 4 and gives Tb_out, the adjoint of T.  Both add their parts
-// of the adjoints of u (ub), lambda (lamb) and rho (rhob).
+// interior fluid nodes) loads T1 (stored by the step's recomputed energy pass), rho, lambda, u
+// on the tile + 4, forms the sources of the transposed stencils on the tile + 2 and gathers
+// them at the tile's nodes: Tb1, the adjoint of T1.  Stage 1 (seed Tb1 on L(T), plus the
+// heat-flux sample) does the same from T and gives Tb_out, the adjoint of T.  Both add their
+// parts of the adjoints of u (ub), lambda (lamb) and rho (rhob).
 constexpr int kEATX = 32, kEATY = 16, kEANT = 512;
 template <typename C, int STAGE>
 struct EAdjLayout {
-  static constexpr int H = STAGE == 2 ? 6 : 4;
+  static constexpr int H = 4;
   static constexpr int AX = kEATX + 2 * H, AY = kEATY + 2 * H, A = AX * AY;  // loaded fields
-  static constexpr int BX = kEATX + 8, BY = kEATY + 8, B = STAGE == 2 ? BX * BY : 0;  // T1
   static constexpr int PX = kEATX + 4, PY = kEATY + 4, PN = PX * PY;                  // sources
   static constexpr int NN = kEATX * kEATY;
-  static constexpr size_t bytes = sizeof(C) * (5 * (size_t)A + B + 8 * (size_t)PN + 5 * (size_t)NN) + A;
+  static constexpr size_t bytes = sizeof(C) * (5 * (size_t)A + 8 * (size_t)PN + 5 * (size_t)NN) + A;
 };
 
 template <typename C, int STAGE>
 __global__ void __launch_bounds__(kEANT) k_adj_energy(Args<C> a) {
   using Lay = EAdjLayout<C, STAGE>;
-  constexpr int H = Lay::H, AX = Lay::AX, A = Lay::A, BX = Lay::BX, PX = Lay::PX, PN = Lay::PN, NN = Lay::NN;
+  constexpr int H = Lay::H, AX = Lay::AX, A = Lay::A, PX = Lay::PX, PN = Lay::PN, NN = Lay::NN;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* sT = reinterpret_cast<C*>(smem_raw);
   C* sR = sT + A;
   C* sL = sR + A;
   C* sU = sL + A;
   C* sV = sU + A;
-  C* sT1 = sV + A;
-  C* sP = sT1 + Lay::B;
+  C* sP = sV + A;
   C* sLoc = sP + 8 * PN;
   uint8_t* sM = reinterpret_cast<uint8_t*>(sLoc + 5 * NN);
   const Geo& g = a.g;
@@ -207,7 +205,7 @@ __global__ void __launch_bounds__(kEANT) k_adj_energy(Args<C> a) {
   for (int p = tid; p < A; p += kEANT) {
     const int id = map_y(g, y0 + p / AX - H) * g.pitch + map_x(g, x0 + p % AX - H);
     const C r = a.rho[id];
-    sT[p] = a.T[id];
+    sT[p] = STAGE == 2 ? a.T1[id] : a.T[id];  // the temperature field the stage read
     sR[p] = r;
     sL[p] = lam_of(a.ph, r);
     sU[p] = a.ux[id];
@@ -215,38 +213,6 @@ __global__ void __launch_bounds__(kEANT) k_adj_energy(Args<C> a) {
     sM[p] = a.mask[id];
   }
   __syncthreads();
-  if constexpr (STAGE == 2) {
-    // T1 = T + L(T) with the forward's Dirichlet values; columns past a non-periodic edge
-    // take the edge column's value (the forward's zero-gradient ghost)
-    for (int p = tid; p < Lay::B; p += kEANT) {
-      const int bx = p % BX, by = p / BX, gx = x0 + bx - 4;
-      const int ai = (by + 2) * AX + bx + 2;
-      C t1 = C(0);
-      if (g.periodic_x || (gx >= 0 && gx < g.nx)) {
-        if (sM[ai] & kSolid) {
-          t1 = sT[ai];
-        } else if (!g.periodic_x && gx == 0) {
-          t1 = k.T_sat;
-        } else {
-          const Parts<C> P = parts_at(&sT[ai], AX, &sL[ai], &sU[ai], &sV[ai], AX);
-          const C r0 = sR[ai], Ta = sT[ai];
-          const C conv = sU[ai] * P.upx + sV[ai] * P.upy;
-          const C diff = sL[ai] * P.lap + (P.lx * P.gx + P.ly * P.gy);
-          const C work = Ta * dpdT_eos(a.ph, r0, Ta) * P.divu;
-          t1 = sT[ai] + (-conv + fdiv(diff, r0 * k.c_v) - fdiv(work, r0 * k.c_v));
-        }
-      }
-      sT1[p] = t1;
-    }
-    __syncthreads();
-    if (!g.periodic_x && (x0 < 4 || x0 + kEATX + 4 > g.nx)) {
-      for (int p = tid; p < Lay::B; p += kEANT) {
-        const int bx = p % BX, by = p / BX, gx = x0 + bx - 4;
-        if (gx < 0 || gx >= g.nx) sT1[p] = sT1[by * BX + (map_x(g, gx) - x0 + 4)];
-      }
-      __syncthreads();
-    }
-  }
   // sources of the transposed stencils on the tile + 2; local parts of the tile's nodes
   for (int p = tid; p < PN; p += kEANT) {
     const int px = p % PX, py = p / PX;
@@ -266,8 +232,8 @@ __global__ void __launch_bounds__(kEANT) k_adj_energy(Args<C> a) {
       if (g.periodic_x || mx != 0) s = STAGE == 2 ? C(0.5) * a.Tb_in[gid] : a.Tb1[gid];
       const bool hf = STAGE == 1 && a.do_hf && (m & kNearWall);
       if (s != C(0) || hf) {
-        const C* t = STAGE == 2 ? &sT1[(py + 2) * BX + px + 2] : &sT[ai];
-        const int ts = STAGE == 2 ? BX : AX;
+        const C* t = &sT[ai];
+        const int ts = AX;
         const Parts<C> P = parts_at(t, ts, &sL[ai], &sU[ai], &sV[ai], AX);
         const C r0 = sR[ai], T0 = t[0], lam0 = sL[ai];
         const C rc = r0 * k.c_v;

@@ -6,8 +6,8 @@
 // copies its state (f*, T, outlet side values) at the start of each segment.  The reverse
 // pass takes the segments last to first: it recomputes the segment from its checkpoint into
 // K + 1 state slots (keeping rho, psi and u of every collision), then runs the reverse steps
-// last to first.  Memory: (K + 1) states and psi fields, K sets of rho and u, one state per
-// checkpoint and 30 adjoint work planes.
+// last to first.  Memory: (K + 1) states and psi fields, K sets of rho, u and the stage-1
+// temperature, one state per checkpoint and 30 adjoint work planes.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -27,6 +27,7 @@ struct lbm_adjoint_work {
   std::vector<void*> blocks;
   std::vector<void*> sf, sT, sside;         // K + 1 state slots
   std::vector<void*> arho, apsi, aux, auy;  // K sets of collision fields
+  std::vector<void*> aT1;                   // K stage-1 temperatures of the recomputed energy passes
   std::vector<void*> cf, cT, cside;         // nseg checkpoints
   void *fb[2] = {}, *Tb[2] = {}, *sb[2] = {};
   void *Tb1 = nullptr, *ub[2] = {}, *lamb = nullptr, *rhob = nullptr;
@@ -80,6 +81,7 @@ lbm_status prepare(lbm_ctx* c, int K, int nseg) {
     w->arho.push_back(A(plane));
     w->aux.push_back(A(plane));
     w->auy.push_back(A(plane));
+    w->aT1.push_back(A(plane));
   }
   for (int j = 0; j <= K; ++j) w->apsi.push_back(A(plane));  // psi of slot K comes from the last energy pass
   for (int s = 0; s < nseg; ++s) {
@@ -129,6 +131,7 @@ int forward_slot(lbm_ctx* c, lbm_adjoint_work* w, int j, cudaStream_t st) {
   v.uy = w->auy[j];
   v.hf = w->hf;
   v.nb = 0;  // the recompute needs no heat-flux sample
+  v.t1_out = w->aT1[j];
   int flipped = 0;
   lbm::PsiChain chain{j > 0 ? 1 : 0, 1, 0};
   const int k = c->f64 ? lbm::step_f64(c->geo, c->ph, v, 0, 0, 1, 1, c->prm.psi_mode, st, nullptr, &flipped, &chain)
@@ -150,6 +153,7 @@ lbm::AdjArgs<C> make_args(lbm_ctx* c, lbm_adjoint_work* w, int j, int ping, doub
   a.psi = static_cast<const C*>(w->apsi[j]);
   a.ux = static_cast<const C*>(w->aux[j]);
   a.uy = static_cast<const C*>(w->auy[j]);
+  a.T1 = static_cast<const C*>(w->aT1[j]);
   a.fb_in = static_cast<const C*>(w->fb[ping]);
   a.Tb_in = static_cast<const C*>(w->Tb[ping]);
   a.sb_in = static_cast<const C*>(w->sb[ping]);

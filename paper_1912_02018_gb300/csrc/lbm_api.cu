@@ -722,6 +722,41 @@ lbm_status lbm_set_state(lbm_ctx* c, const double* f, const double* T, const dou
   return check_status(c);
 }
 
+// Native checkpoints: the device layout is [plane][ny][pitch], consecutive planes back to back,
+// so a set of planes is one 2D copy of (planes * ny) rows.
+static lbm_status native_io(lbm_ctx* c, void* f, void* T, void* side, bool up) {
+  const lbm::Geo& g = c->geo;
+  const size_t es = c->f64 ? sizeof(double) : sizeof(float);
+  const size_t ps = c->prm.storage == LBM_STORE_F64 ? 8 : (c->prm.storage == LBM_STORE_F16S ? 2 : 4);
+  const cudaMemcpyKind kind = up ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToHost;
+  auto copy2d = [&](void* host, void* dev, size_t elem, size_t rows) {
+    const size_t hp = g.nx * elem, dp = g.pitch * elem;
+    return up ? cudaMemcpy2DAsync(dev, dp, host, hp, hp, rows, kind, c->stream)
+              : cudaMemcpy2DAsync(host, hp, dev, dp, hp, rows, kind, c->stream);
+  };
+  if (f) LBM_CUDA(c, copy2d(f, c->dev.f[c->cur], ps, 9 * (size_t)g.ny));
+  if (T) LBM_CUDA(c, copy2d(T, c->dev.T[c->tcur], es, g.ny));
+  if (side) {
+    const size_t b = 3 * (size_t)g.ny * es;
+    LBM_CUDA(c, up ? cudaMemcpyAsync(c->dev.side[c->cur], side, b, kind, c->stream)
+                   : cudaMemcpyAsync(side, c->dev.side[c->cur], b, kind, c->stream));
+  }
+  return check_status(c);
+}
+
+lbm_status lbm_get_state_native(lbm_ctx* c, void* f, void* T, void* side, int64_t* steps) {
+  if (!c) return LBM_EINVAL;
+  if (steps) *steps = c->steps;
+  return native_io(c, f, T, side, false);
+}
+
+lbm_status lbm_set_state_native(lbm_ctx* c, const void* f, const void* T, const void* side, int64_t steps) {
+  if (!c) return LBM_EINVAL;
+  c->psi_pending = 0;  // the state changes: psi of the next step is no longer known
+  if (steps >= 0) c->steps = steps;
+  return native_io(c, const_cast<void*>(f), const_cast<void*>(T), const_cast<void*>(side), true);
+}
+
 lbm_status lbm_info(lbm_ctx* c, lbm_info_t* info) {
   if (!c || !info) return LBM_EINVAL;
   info->Tc = c->Tc;

@@ -61,6 +61,7 @@ struct Dev {
   void* T[2];        // temperature (ping-pong)
   void* psi;         // pseudopotential of the current step
   void* psi_next;    // pseudopotential of the next step, when the energy pass computed it
+  void* t1_out;      // if set, the energy pass also stores its stage-1 temperature T1 here
   void* rho;         // density of the last collision
   void* ux;          // velocity of the last collision
   void* uy;
@@ -173,6 +174,7 @@ struct AdjArgs {
   const C* psi;
   const C* ux;
   const C* uy;
+  const C* T1;    // the step's stage-1 temperature (stored by its recompute)
   // adjoint seeds on the step's outputs, and the results on its inputs
   const C* fb_in;
   const C* Tb_in;

@@ -554,7 +554,9 @@ __device__ __forceinline__ void collide_tile(const Geo& g, const Phys& ph, const
   if (!(rho > C(0)) || !(ux == ux) || !(uy == uy)) atomicOr(status, 1);
 }
 template <typename C, typename S>
-__global__ void __launch_bounds__(kCollTX* kCollTY)
+// FP32: at most 36 registers, so 7 blocks share an SM and more pulls are in flight (the pass
+// waits on DRAM: +10% over the default register budget)
+__global__ void __launch_bounds__(kCollTX* kCollTY, sizeof(C) == 4 ? 7 : 1)
     k_collide(Geo g, Phys ph, const S* __restrict__ f, S* __restrict__ fn, const C* __restrict__ psi,
               const uint8_t* __restrict__ mask, const C* __restrict__ side_in, C* __restrict__ side_out,
               C* __restrict__ rho_o, C* __restrict__ ux_o, C* __restrict__ uy_o, int forcing, int* status) {
@@ -813,7 +815,8 @@ __device__ __forceinline__ void energy_tile(const Geo& g, const Phys& ph, const 
                                             double* partial, unsigned* counter, double* hf, int nb, int do_hf,
                                             int n_wall_tiles, int bx, int by, int bid, int nblocks,
                                             const S* __restrict__ fnew = nullptr, const C* __restrict__ side_new = nullptr,
-                                            C* __restrict__ psi_out = nullptr, int* status = nullptr) {
+                                            C* __restrict__ psi_out = nullptr, int* status = nullptr,
+                                            C* __restrict__ t1_out = nullptr) {
   constexpr int TX = EnergyTile<C, ETY>::TX, TY = EnergyTile<C, ETY>::TY, NT = EnergyTile<C, ETY>::NT;
   constexpr int H = 4, AX = TX + 2 * H, AY = TY + 2 * H;  // inputs: tile + 4
   constexpr int BX = TX + 4, BY = TY + 4;                 // stage 1: tile + 2
@@ -894,6 +897,7 @@ __device__ __forceinline__ void energy_tile(const Geo& g, const Phys& ph, const 
       else out = ((sT[a + k] + sT1[b + k]) + L[k]) * C(0.5);
       Tout[y * g.pitch + x] = out;
       tnew[k] = out;
+      if (t1_out) t1_out[y * g.pitch + x] = sT1[b + k];  // the stage-1 temperature, for the adjoint
       if (do_hf && (sM[a + k] & kNearWall)) {
         // wall heat flux -lambda grad T . n at this boundary node, from T^n (Sec. IV.B)
         C gx, gy;
@@ -954,14 +958,17 @@ __device__ __forceinline__ void energy_tile(const Geo& g, const Phys& ph, const 
   }
 }
 template <typename C, typename S, int PSI>
-__global__ void __launch_bounds__(EnergyTile<C>::NT)
+// FP32: at most 51 registers, 5 blocks per SM (+2.5%)
+__global__ void __launch_bounds__(EnergyTile<C>::NT, sizeof(C) == 4 ? 5 : 1)
     k_energy(Geo g, Phys ph, const C* __restrict__ Tin, C* __restrict__ Tout, const C* __restrict__ rho,
              const C* __restrict__ ux, const C* __restrict__ uy, const uint8_t* __restrict__ mask,
              double* partial, unsigned* counter, double* hf, int nb, int do_hf, int n_wall_tiles,
-             const S* __restrict__ fnew, const C* __restrict__ side_new, C* __restrict__ psi_out, int* status) {
+             const S* __restrict__ fnew, const C* __restrict__ side_new, C* __restrict__ psi_out, int* status,
+             C* __restrict__ t1_out) {
   energy_tile<C, EnergyTile<C>::TY, S, PSI, true>(g, ph, Tin, Tout, rho, ux, uy, mask, partial, counter, hf, nb,
-                                                   do_hf, n_wall_tiles, blockIdx.x,
-                                    blockIdx.y, blockIdx.y * gridDim.x + blockIdx.x, gridDim.x * gridDim.y, fnew, side_new, psi_out, status);
+                                                   do_hf, n_wall_tiles, blockIdx.x, blockIdx.y,
+                                                   blockIdx.y * gridDim.x + blockIdx.x, gridDim.x * gridDim.y, fnew,
+                                                   side_new, psi_out, status, t1_out);
 }
 
 // ---------------------------------------------------------------- batched passes
@@ -978,7 +985,7 @@ __global__ void __launch_bounds__(256) kb_rho_psi(const BatchDomain* __restrict_
                           local % D.psi_ntx, local / D.psi_ntx);
 }
 template <typename C, typename S, int CTY>
-__global__ void __launch_bounds__(kCollTX* CTY) kb_collide(const BatchDomain* __restrict__ doms,
+__global__ void __launch_bounds__(kCollTX* CTY, (sizeof(C) == 4 && CTY == 8) ? 7 : 1) kb_collide(const BatchDomain* __restrict__ doms,
                                                           const int* __restrict__ map, int cur, long long step) {
   const BatchDomain& D = doms[map[blockIdx.x]];
   const int local = blockIdx.x - D.coll_first;
@@ -1168,7 +1175,8 @@ int step_impl(const Geo& g, const Phys& ph, const Dev& d, int cur, int tcur, int
     const bool fuse = chain && chain->want && ph.d.G != 0.0;
     k_energy<C, S, PSI><<<grd, blk, 0, s>>>(g, ph, T, Tn, rho, ux, uy, d.mask, d.partial, d.counter, d.hf, d.nb,
                                             do_hf, d.wall_tiles[ET::TY == 16 ? 1 : 0], fuse ? fn : nullptr,
-                                            side_out, fuse ? static_cast<C*>(d.psi_next) : nullptr, d.status);
+                                            side_out, fuse ? static_cast<C*>(d.psi_next) : nullptr, d.status,
+                                            static_cast<C*>(d.t1_out));
     post(kKEnergy);
     *t_flipped = 1;
     if (chain) chain->made = fuse ? 1 : 0;

@@ -98,6 +98,7 @@ class Sim:
         L = N.lib()
         self.nx, self.ny, self.D = int(nx), int(ny), float(D)
         dom, cyl, prm, self.params = _structs(nx, ny, D, xc, yc, periodic_x, superheat_Tc, rho_s, f64, storage, params)
+        self._f64, self._storage = bool(f64), prm.storage
         n = self.nx * self.ny
         init = init or {}
         keep = {k: _dense(init.get(k), n) for k in ("rho", "drho", "ux", "uy", "T")}
@@ -134,6 +135,8 @@ class Sim:
         self._owner = owner
         self._blocks = {}
         self.n_wall = 0
+        self._f64 = owner._f64
+        self._storage = N.LBM_STORE_F64 if owner._f64 else N.LBM_STORE_F32
         self.device = torch.cuda.current_device()
         return self
 
@@ -211,6 +214,29 @@ class Sim:
         ptrs = [a.ctypes.data if a is not None else None for a in keep]
         self._chk(N.lib().lbm_set_state(self.h, *ptrs, int(steps)))
 
+    def native_dtypes(self):
+        """numpy dtypes of a native checkpoint: (populations, T and outlet rows)."""
+        pop = {N.LBM_STORE_F64: np.float64, N.LBM_STORE_F32: np.float32, N.LBM_STORE_F16S: np.float16}
+        return pop[self._storage], (np.float64 if self._f64 else np.float32)
+
+    def get_state_native(self):
+        """Checkpoint in the context's own formats (lbm_get_state_native)."""
+        fdt, tdt = self.native_dtypes()
+        f = np.empty((9, self.ny, self.nx), dtype=fdt)
+        T = np.empty((self.ny, self.nx), dtype=tdt)
+        side = np.empty((3, self.ny), dtype=tdt)
+        steps = C.c_int64()
+        self._chk(N.lib().lbm_get_state_native(self.h, f.ctypes.data, T.ctypes.data, side.ctypes.data,
+                                               C.byref(steps)))
+        return f, T, side, steps.value
+
+    def set_state_native(self, f=None, T=None, side=None, steps=-1):
+        fdt, tdt = self.native_dtypes()
+        keep = [None if a is None else np.ascontiguousarray(a, dtype=dt)
+                for a, dt in ((f, fdt), (T, tdt), (side, tdt))]
+        self._chk(N.lib().lbm_set_state_native(self.h, *[a.ctypes.data if a is not None else None for a in keep],
+                                               int(steps)))
+
     def info(self) -> dict:
         inf = N.Info()
         self._chk(N.lib().lbm_info(self.h, C.byref(inf)))
@@ -280,6 +306,7 @@ class Batch:
             doms[i], cyls[i], prms[i], _ = _structs(k["nx"], k["ny"], k["D"], k["xc"], k["yc"], k["periodic_x"],
                                                     k["superheat_Tc"], k["rho_s"], f64, "f32", k["params"])
         self.shapes = [(k["nx"], k["ny"], k["D"]) for k in kws]
+        self._f64 = bool(f64)
         self.device = torch.cuda.current_device()
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self._blocks, self._alloc_cb, self._allocator, alloc_p = _torch_allocator(torch, self.device, torch_alloc)

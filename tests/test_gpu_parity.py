@@ -221,6 +221,26 @@ def test_checkpoint_restart_is_bit_exact():
         assert np.array_equal(fa[k], fb[k]), k
 
 
+@pytest.mark.parametrize("f64,storage", [(True, "f64"), (False, "f32"), (False, "f16s"), (False, "f64")])
+def test_native_checkpoint_round_trip_is_bit_exact(f64, storage):
+    case = si.SMALL
+    a = Sim().from_case(case, f64=f64, storage=storage).step(12)
+    f, T, side, n = a.get_state_native()
+    a.step(5)
+    b = Sim().from_case(case, f64=f64, storage=storage)
+    b.set_state_native(f, T, side, n)
+    b.step(5)
+    assert b.info()["steps"] == n + 5
+    fa, fb = a.get_state_native(), b.get_state_native()
+    for x, y in zip(fa[:3], fb[:3]):
+        assert np.array_equal(x, y)
+    # the double form of the same state agrees value for value
+    fd, Td, sd, _ = a.get_state()
+    assert np.array_equal(fa[1].astype(np.float64), Td)
+    if storage != "f16s":
+        assert np.array_equal(fa[0].astype(np.float64), fd)
+
+
 def test_torch_allocator_and_cudamalloc_agree():
     case = si.SMALL
     init = {"drho": case.drho()}
