@@ -555,7 +555,8 @@ __device__ __forceinline__ void collide_tile(const Geo& g, const Phys& ph, const
 }
 template <typename C, typename S>
 // FP32: at most 36 registers, so 7 blocks share an SM and more pulls are in flight (the pass
-// waits on DRAM: +10% over the default register budget)
+// waits on DRAM: +10% over the default register budget; with FP16 storage 7 blocks and a few
+// spilled registers still beat 6 blocks without spills, 30.8 vs 32.6 us at 1536 x 768)
 __global__ void __launch_bounds__(kCollTX* kCollTY, sizeof(C) == 4 ? 7 : 1)
     k_collide(Geo g, Phys ph, const S* __restrict__ f, S* __restrict__ fn, const C* __restrict__ psi,
               const uint8_t* __restrict__ mask, const C* __restrict__ side_in, C* __restrict__ side_out,
@@ -743,9 +744,9 @@ __device__ __forceinline__ float2 lap_w2(const Win2& W) {
   }
   return __fmul2_rn(f2(2.f), acc);
 }
-// Third-order upwind derivative of the pair along x (row 2) or y (column pair 1), each node
-// biased against the sign of its own velocity v.
-__device__ __forceinline__ float2 upwind_w2(const Win2& W, bool along_x, float2 v) {
+// Six times the third-order upwind derivative of the pair along x (row 2) or y (column pair
+// 1), each node biased against the sign of its own velocity v.
+__device__ __forceinline__ float2 upwind6_w2(const Win2& W, bool along_x, float2 v) {
   float2 q[5];
 #pragma unroll
   for (int o = -2; o <= 2; ++o) q[o + 2] = along_x ? win_at(W, 2, o) : W.A[2 + o][1];
@@ -753,7 +754,7 @@ __device__ __forceinline__ float2 upwind_w2(const Win2& W, bool along_x, float2 
   const float2 m2 = sub2(q[0], c), m1 = sub2(q[1], c), p1 = sub2(q[3], c), p2 = sub2(q[4], c);
   const float2 pos = __ffma2_rn(f2(2.f), p1, __ffma2_rn(f2(-6.f), m1, m2));
   const float2 neg = sub2(__ffma2_rn(f2(6.f), p1, __fmul2_rn(f2(-2.f), m1)), p2);
-  return make_float2(__fdividef(v.x >= 0.f ? pos.x : neg.x, 6.f), __fdividef(v.y >= 0.f ? pos.y : neg.y, 6.f));
+  return make_float2(v.x >= 0.f ? pos.x : neg.x, v.y >= 0.f ? pos.y : neg.y);
 }
 template <>
 __device__ __forceinline__ void frozen_pair<float>(const float* lam, const float* u, const float* v, int as,
@@ -772,6 +773,9 @@ __device__ __forceinline__ void frozen_pair<float>(const float* lam, const float
   fz[0].lx = lx.x, fz[0].ly = ly.x, fz[0].divu = dv.x;
   fz[1].lx = lx.y, fz[1].ly = ly.y, fz[1].divu = dv.y;
 }
+__device__ __forceinline__ float2 pk_div(float2 a, float2 b) {
+  return make_float2(__fdividef(a.x, b.x), __fdividef(a.y, b.y));
+}
 template <>
 __device__ __forceinline__ void energy_rhs_pair<float>(const Phys& ph, const float* t, int ts, const float* u,
                                                        const float* v, const float* r, const Frozen<float> fz[2],
@@ -779,20 +783,120 @@ __device__ __forceinline__ void energy_rhs_pair<float>(const Phys& ph, const flo
   Win2 W;
   load_win2(t, ts, W);
   const float2 u2 = make_float2(u[0], u[1]), v2 = make_float2(v[0], v[1]);
-  const float2 conv = __ffma2_rn(u2, upwind_w2(W, true, u2), __fmul2_rn(v2, upwind_w2(W, false, v2)));
+  const float2 conv6 = __ffma2_rn(u2, upwind6_w2(W, true, u2), __fmul2_rn(v2, upwind6_w2(W, false, v2)));
   float2 gx, gy;
   grad_w2(W, gx, gy);
   const float2 lap = lap_w2(W);
   const float2 diff = __ffma2_rn(make_float2(fz[0].lam0, fz[1].lam0), lap,
                                  __ffma2_rn(make_float2(fz[0].lx, fz[1].lx), gx,
                                             __fmul2_rn(make_float2(fz[0].ly, fz[1].ly), gy)));
-  const float c_v = ph.f.c_v;
-  const float T0[2] = {W.A[2][1].x, W.A[2][1].y};
-  const float cv[2] = {conv.x, conv.y}, df[2] = {diff.x, diff.y};
+  // (dp/dT)_rho of Eq. (eos) with phi = (1 + kappa (1 - sqrt(T/Tc)))^2, dphi/dT = -kappa
+  // sqrt(phi) / sqrt(T Tc):  rep + att (kappa (1 + kappa) / sqrt(T Tc) - kappa^2 / Tc), with
+  // rep = rho R / (1 - b rho) and att = a rho^2 / (1 + 2 b rho - b^2 rho^2)
+  const PhysC<float>& k = ph.f;
+  const float2 rho = make_float2(r[0], r[1]), T0 = W.A[2][1];
+  const float2 rep = pk_div(__fmul2_rn(f2(k.R), rho), __ffma2_rn(f2(-k.b), rho, f2(1.0f)));
+  const float2 att = pk_div(__fmul2_rn(__fmul2_rn(f2(k.a), rho), rho),
+                            __ffma2_rn(rho, __ffma2_rn(f2(-k.b * k.b), rho, f2(2.0f * k.b)), f2(1.0f)));
+  const float2 rs = make_float2(rsqrtf(T0.x * k.Tc), rsqrtf(T0.y * k.Tc));
+  const float2 dpdT = __ffma2_rn(att, __ffma2_rn(f2(ph.dpdT_c1), rs, f2(-ph.dpdT_c2)), rep);
+  const float2 work = __fmul2_rn(__fmul2_rn(T0, dpdT), make_float2(fz[0].divu, fz[1].divu));
+  const float2 Lp = __ffma2_rn(sub2(diff, work), pk_div(f2(1.0f), __fmul2_rn(f2(k.c_v), rho)),
+                               __fmul2_rn(f2(-1.0f / 6.0f), conv6));
+  L[0] = Lp.x;
+  L[1] = Lp.y;
+}
+
+// Heun stage 2 at the pair whose left node is (x, y), T^{n+1} = (T + T1 + L(T1)) / 2, from
+// shared tiles: inputs sT, sL, sU, sV, sR, sM (row stride ax, pair at index a) and the stage-1
+// temperature sT1 (row stride bx, pair at index b); fz: the pair's frozen parts.  Nodes with
+// x >= nx or y >= ylim are skipped.  Writes T^{n+1}, T1 (t1_out) and, with FUSE and psi_out,
+// psi of the next step from the pull of the new populations fnew, side_new (Eq. potential);
+// adds the pair's wall heat flux -lambda grad T^n . n (Sec. IV.B) to q and sets mine when
+// the pair holds a near-wall node.
+template <typename C, typename S, int PSI, bool FUSE>
+__device__ __forceinline__ void stage2_pair(const Geo& g, const Phys& ph, const C* sT, const C* sL, const C* sU,
+                                            const C* sV, const C* sR, const uint8_t* sM, int ax, int a, const C* sT1,
+                                            int bx, int b, const Frozen<C>* fz_in, int x0, int y, int ylim,
+                                            C* __restrict__ Tout, C* __restrict__ t1_out, int do_hf,
+                                            const S* __restrict__ fnew, const uint8_t* __restrict__ mask,
+                                            const C* __restrict__ side_new, C* __restrict__ psi_out, int* status,
+                                            double& q, int& mine) {
+  const Frozen<C> fz[2] = {fz_in[0], fz_in[1]};
+  C L[2];
+  energy_rhs_pair(ph, &sT1[b], bx, &sU[a], &sV[a], &sR[a], fz, L);
+  C tnew[2];
 #pragma unroll
   for (int k = 0; k < 2; ++k) {
-    const float work = T0[k] * dpdT_eos(ph, r[k], T0[k]) * fz[k].divu;
-    L[k] = -cv[k] + __fdividef(df[k], r[k] * c_v) - __fdividef(work, r[k] * c_v);
+    const int x = x0 + k;
+    if (x < g.nx && y < ylim) {
+      C out;
+      if (sM[a + k] & kSolid) out = sT[a + k];
+      else if (!g.periodic_x && x == 0) out = pc<C>(ph).T_sat;
+      else out = ((sT[a + k] + sT1[b + k]) + L[k]) * C(0.5);
+      Tout[y * g.pitch + x] = out;
+      tnew[k] = out;
+      if (t1_out) t1_out[y * g.pitch + x] = sT1[b + k];  // the stage-1 temperature, for the adjoint
+      if (do_hf && (sM[a + k] & kNearWall)) {
+        C gx, gy;
+        grad_t(&sT[a + k], ax, gx, gy);
+        const double* nv = &g.wall_n[2 * g.wall_idx[y * g.pitch + x]];
+        q += -(double)sL[a + k] * ((double)gx * nv[0] + (double)gy * nv[1]);
+        mine = 1;
+      }
+    }
+  }
+  if constexpr (FUSE) {
+    if (psi_out) {
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        const int x = x0 + k;
+        if (x < g.nx && y < ylim) {
+          const uint8_t m = sM[a + k];
+          C fo[9];
+          pull_node<C, S>(g, ph, fnew, mask, side_new, nullptr, x, y, m, fo);
+          C r = fo[0];
+#pragma unroll
+          for (int i = 1; i < 9; ++i) r = r + fo[i];
+          if (m & kSolid) r = pc<C>(ph).rho_s;
+          psi_out[y * g.pitch + x] = psi_of<C, PSI>(ph, r, tnew[k], status);
+        }
+      }
+    }
+  }
+}
+
+// Block-level end of the wall heat flux: FP64 block sums only in the blocks that hold wall
+// nodes (the others skip the fence and the counter); the last of those n_wall blocks to
+// finish adds all nblocks partials in block order (zero elsewhere), updates the running
+// statistics hf and clears the partials for the next launch.  Every thread of the block calls it.
+template <int NT>
+__device__ __forceinline__ void heat_flux_blocks(double q, int mine, double* partial, unsigned* counter, int n_wall,
+                                                 int bid, int nblocks, double* hf, int nb, double* red,
+                                                 int* done_last) {
+  const int tid = threadIdx.x;
+  if (__syncthreads_or(mine)) {
+    const double s = block_sum<NT>(q, red);
+    if (tid == 0) {
+      partial[bid] = s;
+      __threadfence();
+      *done_last = atomicInc(counter, n_wall - 1) == (unsigned)(n_wall - 1);
+    }
+    __syncthreads();
+    if (*done_last) {
+      __threadfence();
+      double acc = 0.0;
+      for (int i = tid; i < nblocks; i += NT) acc += __ldcg(&partial[i]);
+      acc = block_sum<NT>(acc, red);  // its barrier also ends every thread's reads above
+      for (int i = tid; i < nblocks; i += NT) partial[i] = 0.0;
+      if (tid == 0) {
+        const double qv = acc / nb;
+        hf[0] = qv;
+        hf[1] += qv;
+        hf[2] += qv * qv;
+        hf[3] += 1.0;
+      }
+    }
   }
 }
 
@@ -880,86 +984,17 @@ __device__ __forceinline__ void energy_tile(const Geo& g, const Phys& ph, const 
   }
   // stage 2 on the tile: T^{n+1} = (T + T1 + L(T1)) / 2
   const int tx = (tid % (TX / 2)) * 2, ty = tid / (TX / 2);
-  const int a = (ty + H) * AX + tx + H, b = (ty + 2) * BX + tx + 2;
-  const Frozen<C> fz[2] = {sF[ty * TX + tx], sF[ty * TX + tx + 1]};
-  C L[2];
-  energy_rhs_pair(ph, &sT1[b], BX, &sU[a], &sV[a], &sR[a], fz, L);
   double q = 0.0;
-  const int y = y0 + ty;
-  C tnew[2];
-#pragma unroll
-  for (int k = 0; k < 2; ++k) {
-    const int x = x0 + tx + k;
-    if (x < g.nx && y < g.ny) {
-      C out;
-      if (sM[a + k] & kSolid) out = sT[a + k];
-      else if (!g.periodic_x && x == 0) out = pc<C>(ph).T_sat;
-      else out = ((sT[a + k] + sT1[b + k]) + L[k]) * C(0.5);
-      Tout[y * g.pitch + x] = out;
-      tnew[k] = out;
-      if (t1_out) t1_out[y * g.pitch + x] = sT1[b + k];  // the stage-1 temperature, for the adjoint
-      if (do_hf && (sM[a + k] & kNearWall)) {
-        // wall heat flux -lambda grad T . n at this boundary node, from T^n (Sec. IV.B)
-        C gx, gy;
-        grad_t(&sT[a + k], AX, gx, gy);
-        const double* nv = &g.wall_n[2 * g.wall_idx[y * g.pitch + x]];
-        q += -(double)sL[a + k] * ((double)gx * nv[0] + (double)gy * nv[1]);
-      }
-    }
-  }
-  if constexpr (FUSE) {
-    if (psi_out) {
-#pragma unroll
-      for (int k = 0; k < 2; ++k) {
-        const int x = x0 + tx + k;
-        if (x < g.nx && y < g.ny) {
-          const uint8_t m = sM[a + k];
-          C fo[9];
-          pull_node<C, S>(g, ph, fnew, mask, side_new, nullptr, x, y, m, fo);
-          C r = fo[0];
-#pragma unroll
-          for (int i = 1; i < 9; ++i) r = r + fo[i];
-          if (m & kSolid) r = pc<C>(ph).rho_s;
-          psi_out[y * g.pitch + x] = psi_of<C, PSI>(ph, r, tnew[k], status);
-        }
-      }
-    }
-  }
-  if (do_hf) {
-    // FP64 block sums only in the tiles that hold wall nodes (the others skip the fence and the
-    // counter); the last of those tiles to finish adds all partials in block order (zero
-    // elsewhere), updates the running statistics and clears the partials for the next launch
-    int mine = 0;
-#pragma unroll
-    for (int k = 0; k < 2; ++k) mine |= (x0 + tx + k < g.nx && y < g.ny && (sM[a + k] & kNearWall)) ? 1 : 0;
-    if (__syncthreads_or(mine)) {
-      const double s = block_sum<NT>(q, red);
-      if (tid == 0) {
-        partial[bid] = s;
-        __threadfence();
-        done_last = atomicInc(counter, n_wall_tiles - 1) == (unsigned)(n_wall_tiles - 1);
-      }
-      __syncthreads();
-      if (done_last) {
-        __threadfence();
-        double acc = 0.0;
-        for (int i = tid; i < nblocks; i += NT) acc += __ldcg(&partial[i]);
-        acc = block_sum<NT>(acc, red);  // its barrier also ends every thread's reads above
-        for (int i = tid; i < nblocks; i += NT) partial[i] = 0.0;
-        if (tid == 0) {
-          const double qv = acc / nb;
-          hf[0] = qv;
-          hf[1] += qv;
-          hf[2] += qv * qv;
-          hf[3] += 1.0;
-        }
-      }
-    }
-  }
+  int mine = 0;
+  stage2_pair<C, S, PSI, FUSE>(g, ph, sT, sL, sU, sV, sR, sM, AX, (ty + H) * AX + tx + H, sT1, BX,
+                               (ty + 2) * BX + tx + 2, &sF[ty * TX + tx], x0 + tx, y0 + ty, g.ny, Tout, t1_out, do_hf,
+                               fnew, mask, side_new, psi_out, status, q, mine);
+  if (do_hf) heat_flux_blocks<NT>(q, mine, partial, counter, n_wall_tiles, bid, nblocks, hf, nb, red, &done_last);
 }
 template <typename C, typename S, int PSI>
-// FP32: at most 51 registers, 5 blocks per SM (+2.5%)
-__global__ void __launch_bounds__(EnergyTile<C>::NT, sizeof(C) == 4 ? 5 : 1)
+// FP32: at most 51 registers, 5 blocks per SM (+2.5%); with FP16 storage 64 registers and
+// 4 blocks (the conversions of the fused psi pull need them: no spills)
+__global__ void __launch_bounds__(EnergyTile<C>::NT, sizeof(C) == 4 ? (sizeof(S) == 2 ? 4 : 5) : 1)
     k_energy(Geo g, Phys ph, const C* __restrict__ Tin, C* __restrict__ Tout, const C* __restrict__ rho,
              const C* __restrict__ ux, const C* __restrict__ uy, const uint8_t* __restrict__ mask,
              double* partial, unsigned* counter, double* hf, int nb, int do_hf, int n_wall_tiles,
@@ -1169,10 +1204,10 @@ int step_impl(const Geo& g, const Phys& ph, const Dev& d, int cur, int tcur, int
   *t_flipped = 0;
   if (energy && forcing) {
     const int do_hf = d.nb > 0;
+    const bool fuse = chain && chain->want && ph.d.G != 0.0;
+    pre(kKEnergy);
     using ET = EnergyTile<C>;
     const dim3 blk(ET::NT), grd((g.nx + ET::TX - 1) / ET::TX, (g.ny + ET::TY - 1) / ET::TY);
-    pre(kKEnergy);
-    const bool fuse = chain && chain->want && ph.d.G != 0.0;
     k_energy<C, S, PSI><<<grd, blk, 0, s>>>(g, ph, T, Tn, rho, ux, uy, d.mask, d.partial, d.counter, d.hf, d.nb,
                                             do_hf, d.wall_tiles[ET::TY == 16 ? 1 : 0], fuse ? fn : nullptr,
                                             side_out, fuse ? static_cast<C*>(d.psi_next) : nullptr, d.status,
