@@ -34,7 +34,8 @@
  *   - lbm_step only enqueues work on the context's stream.  A fault detected by a
  *     kernel (non-finite density, non-positive psi radicand) is latched on the device
  *     and reported as LBM_EUNSTABLE by the next call that synchronises (lbm_sync,
- *     lbm_fields, lbm_get_state, lbm_wall_heat_flux).
+ *     lbm_fields, lbm_get_state, lbm_wall_heat_flux); a bounded wait of a kernel that gave
+ *     up is reported there as LBM_ETIMEOUT.
  */
 #ifndef LBM_H
 #define LBM_H
@@ -54,7 +55,7 @@ typedef enum {
     LBM_ENOMEM = -2,    /* device allocation failed */
     LBM_ECUDA = -3,     /* a CUDA runtime call failed */
     LBM_EUNSTABLE = -4, /* a kernel saw a non-finite density or psi radicand <= 0 */
-    LBM_ETIMEOUT = -5,  /* reserved: a bounded device wait gave up */
+    LBM_ETIMEOUT = -5,  /* a bounded device wait gave up (a shared-memory tile copy that did not land) */
     LBM_ESTATE = -6     /* call not valid in the context's current state */
 } lbm_status;
 

@@ -190,6 +190,7 @@ lbm_status check_status(lbm_ctx* c) {
   LBM_CUDA(c, cudaStreamSynchronize(c->stream));
   if (st & 1) return fail(c, LBM_EUNSTABLE, "non-finite or non-positive density or velocity in the collision");
   if (st & 2) return fail(c, LBM_EUNSTABLE, "pseudopotential radicand <= 0 (Eq. potential) at some node");
+  if (st & 4) return fail(c, LBM_ETIMEOUT, "a collision tile's shared-memory copy did not complete in time");
   return LBM_OK;
 }
 

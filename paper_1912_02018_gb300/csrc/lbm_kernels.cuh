@@ -20,6 +20,7 @@
 #include <cstdint>
 
 #include "lbm_internal.h"
+#include "lbm_tma.cuh"
 
 namespace lbm {
 namespace kern {
@@ -495,29 +496,68 @@ __global__ void __launch_bounds__(256) k_rho_psi(Geo g, Phys ph, const S* __rest
 // Pull, interaction force from a psi tile with a 2-node halo, gravity, CM collision, for
 // tile (bx, by) of 32 x CTY nodes; writes f* (other buffer), rho, u and the outlet's
 // streamed values.
+// Shared-memory staging of a collision tile.  Populations: the tile's rows with a 1-row halo,
+// columns from x0 - XA (XA elements = 16 bytes, the alignment of a TMA copy's first column);
+// psi: a 2-row and PA-column halo.  Tiles whose staged boxes lie inside the lattice (no wrap,
+// no open edge) are copied by TMA; the others load psi and pull with plain loads.
+template <typename C, typename S, int CTY>
+struct CollStage {
+  static constexpr int XA = 16 / (int)sizeof(S), FW = kCollTX + 2 * XA, FH = CTY + 2;
+  static constexpr int PA = 16 / (int)sizeof(C) < 2 ? 2 : 16 / (int)sizeof(C), PW = kCollTX + 2 * PA, PH = CTY + 4;
+  static constexpr int MARGIN = XA > PA ? XA : PA;  // columns a staged tile needs left and right of it
+};
+template <typename C, typename S, int CTY>
+__device__ __forceinline__ bool coll_staged(const Geo& g, int x0, int y0) {
+  constexpr int M = CollStage<C, S, CTY>::MARGIN;
+  return x0 >= M && x0 + kCollTX + M <= g.nx && y0 >= 2 && y0 + CTY + 2 <= g.ny;
+}
+
 template <typename C, typename S, int CTY>
 __device__ __forceinline__ void collide_tile(const Geo& g, const Phys& ph, const S* __restrict__ f,
                                              S* __restrict__ fn, const C* __restrict__ psi,
                                              const uint8_t* __restrict__ mask, const C* __restrict__ side_in,
                                              C* __restrict__ side_out, C* __restrict__ rho_o, C* __restrict__ ux_o,
-                                             C* __restrict__ uy_o, int forcing, int* status, int bx, int by) {
-  constexpr int HX = kCollTX + 4, HY = CTY + 4;
-  __shared__ C s_psi[HY * HX];
+                                             C* __restrict__ uy_o, int forcing, int* status, int bx, int by,
+                                             const CUtensorMap* tm_f = nullptr, const CUtensorMap* tm_psi = nullptr) {
+  using CS = CollStage<C, S, CTY>;
+  constexpr int HX = CS::PW, HY = CS::PH;
+  __shared__ __align__(128) S s_f[9 * CS::FH * CS::FW];
+  __shared__ __align__(128) C s_psi[HY * HX];
+  __shared__ uint64_t s_bar;
   const PhysC<C>& k = pc<C>(ph);
-  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * kCollTX + tx;
   const int x0 = bx * kCollTX, y0 = by * CTY;
   const int x = x0 + tx, y = y0 + ty;
   const bool multiphase = k.G != C(0);
-  if (multiphase && forcing) {
-    for (int p = ty * kCollTX + tx; p < HX * HY; p += kCollTX * CTY) {
+  const bool need_psi = multiphase && forcing;
+  const bool staged = tm_f && (!need_psi || tm_psi) && coll_staged<C, S, CTY>(g, x0, y0);
+  if (staged) {
+    if (tid == 0) tma::bar_init(&s_bar, 1);
+    __syncthreads();
+    if (tid == 0) {
+      const uint32_t bytes = sizeof(S) * 9 * CS::FH * CS::FW + (need_psi ? sizeof(C) * HX * HY : 0);
+      tma::bar_expect_tx(&s_bar, bytes);
+      tma::load_3d(s_f, tm_f, &s_bar, x0 - CS::XA, y0 - 1, 0);
+      if (need_psi) tma::load_2d(s_psi, tm_psi, &s_bar, x0 - CS::PA, y0 - 2);
+    }
+  } else if (need_psi) {
+    for (int p = tid; p < HX * HY; p += kCollTX * CTY) {
       const int hx = p % HX, hy = p / HX;
-      s_psi[p] = psi[map_y(g, y0 + hy - 2) * g.pitch + map_x(g, x0 + hx - 2)];
+      s_psi[p] = psi[map_y(g, y0 + hy - 2) * g.pitch + map_x(g, x0 + hx - CS::PA)];
     }
     __syncthreads();
   }
-  if (x >= g.nx || y >= g.ny) return;
+  const bool inside = x < g.nx && y < g.ny;
   const int id = y * g.pitch + x;
-  const uint8_t m = mask[id];
+  const uint8_t m = inside ? mask[id] : kSolid;
+  if (staged && !tma::bar_wait(&s_bar, 0, tma::kWaitTries)) {
+    // the copies did not land in time: report it, give them a second bound to land before the
+    // block's shared memory is released, and produce nothing
+    if (tid == 0) atomicOr(status, 4);
+    tma::bar_wait(&s_bar, 0, tma::kWaitTries);
+    return;
+  }
+  if (!inside) return;
   if (m & kSolid) {
     rho_o[id] = k.rho_s;
     ux_o[id] = C(0);
@@ -525,16 +565,25 @@ __device__ __forceinline__ void collide_tile(const Geo& g, const Phys& ph, const
     return;
   }
   C fo[9];
-  pull_node<C, S>(g, ph, f, mask, side_in, side_out, x, y, m, fo);
+  if (staged) {
+    // a staged tile holds no inlet or outlet column; wall nodes redo the pull with substitutions
+#pragma unroll
+    for (int i = 0; i < 9; ++i)
+      fo[i] = PopIO<C, S>::ld(s_f[(i * CS::FH + ty + 1 - cyv(i)) * CS::FW + tx + CS::XA - cxv(i)], i, ph);
+    if (m & kNearWall) pull_slow<C, S>(g, ph, f, mask, side_in, side_out, x, y, fo);
+  } else {
+    pull_node<C, S>(g, ph, f, mask, side_in, side_out, x, y, m, fo);
+  }
   C rho = fo[0];
 #pragma unroll
   for (int i = 1; i < 9; ++i) rho = rho + fo[i];
   const C cs2 = C(1.0 / 3.0);
   C Fmx = C(0), Fmy = C(0), Fx = C(0), Fy = C(0), psi0 = C(0);
-  if (multiphase) psi0 = psi[id];
-  if (forcing && multiphase) {
+  const int pc0 = (ty + 2) * HX + tx + CS::PA;  // this node in the psi tile
+  if (multiphase) psi0 = need_psi ? s_psi[pc0] : psi[id];
+  if (need_psi) {
     C sx, sy;
-    grad_t(&s_psi[(ty + 2) * HX + tx + 2], HX, sx, sy);
+    grad_t(&s_psi[pc0], HX, sx, sy);
     Fmx = -k.G * cs2 * psi0 * sx;
     Fmy = -k.G * cs2 * psi0 * sy;
   }
@@ -543,7 +592,7 @@ __device__ __forceinline__ void collide_tile(const Geo& g, const Phys& ph, const
     Fy = Fmy;
   }
   const C omega = fdiv(C(1), fdiv(nu_of(ph, rho), cs2) + C(0.5));
-  const C sig = (forcing && multiphase) ? k.sigma : C(0);
+  const C sig = need_psi ? k.sigma : C(0);
   C fs[9], ux, uy;
   collide(fo, rho, Fx, Fy, Fmx, Fmy, psi0, omega, sig, fs, ux, uy);
 #pragma unroll
@@ -553,6 +602,7 @@ __device__ __forceinline__ void collide_tile(const Geo& g, const Phys& ph, const
   uy_o[id] = uy;
   if (!(rho > C(0)) || !(ux == ux) || !(uy == uy)) atomicOr(status, 1);
 }
+
 template <typename C, typename S>
 // FP32: at most 36 registers, so 7 blocks share an SM and more pulls are in flight (the pass
 // waits on DRAM: +10% over the default register budget; with FP16 storage 7 blocks and a few
@@ -560,9 +610,10 @@ template <typename C, typename S>
 __global__ void __launch_bounds__(kCollTX* kCollTY, sizeof(C) == 4 ? 7 : 1)
     k_collide(Geo g, Phys ph, const S* __restrict__ f, S* __restrict__ fn, const C* __restrict__ psi,
               const uint8_t* __restrict__ mask, const C* __restrict__ side_in, C* __restrict__ side_out,
-              C* __restrict__ rho_o, C* __restrict__ ux_o, C* __restrict__ uy_o, int forcing, int* status) {
+              C* __restrict__ rho_o, C* __restrict__ ux_o, C* __restrict__ uy_o, int forcing, int* status,
+              const __grid_constant__ CUtensorMap tm_f, const __grid_constant__ CUtensorMap tm_psi, int staged) {
   collide_tile<C, S, kCollTY>(g, ph, f, fn, psi, mask, side_in, side_out, rho_o, ux_o, uy_o, forcing, status,
-                              blockIdx.x, blockIdx.y);
+                              blockIdx.x, blockIdx.y, staged ? &tm_f : nullptr, staged ? &tm_psi : nullptr);
 }
 
 // ---------------------------------------------------------------- k_energy
@@ -1198,8 +1249,15 @@ int step_impl(const Geo& g, const Phys& ph, const Dev& d, int cur, int tcur, int
     k_rho_psi<C, S, PSI><<<grd, blk, 0, s>>>(g, ph, f, T, d.mask, side_in, psi, d.status);
     post(kKRhoPsi);
   }
+  // tensor maps of this step's populations and psi for the TMA-staged tiles (plain loads
+  // everywhere when a map cannot be made)
+  using CS = CollStage<C, S, kCollTY>;
+  CUtensorMap tm_f, tm_psi;
+  const bool staged = tma::encode<S>(&tm_f, f, g.nx, g.ny, g.pitch, g.plane, 9, CS::FW, CS::FH) &&
+                      tma::encode<C>(&tm_psi, psi, g.nx, g.ny, g.pitch, g.plane, 1, CS::PW, CS::PH);
   pre(kKCollide);
-  k_collide<C, S><<<grd, blk, 0, s>>>(g, ph, f, fn, psi, d.mask, side_in, side_out, rho, ux, uy, forcing, d.status);
+  k_collide<C, S><<<grd, blk, 0, s>>>(g, ph, f, fn, psi, d.mask, side_in, side_out, rho, ux, uy, forcing, d.status,
+                                      tm_f, tm_psi, staged ? 1 : 0);
   post(kKCollide);
   *t_flipped = 0;
   if (energy && forcing) {
