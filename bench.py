@@ -59,11 +59,15 @@ ALG_BYTES = {
     "k_energy": 4 * 4 + 4 + 9 * POP + 4,
 }
 STEP_ALG_BYTES = 9 * POP * 2 + 4 * 2      # the whole step: populations and T in and out
-KERNEL_SRC = os.path.join(ROOT, "paper_1912_02018_gb300", "csrc", "lbm_kernels.cuh")
+KERNEL_SRCS = [os.path.join(ROOT, "paper_1912_02018_gb300", "csrc", n) for n in ("lbm_kernels.cuh", "lbm_tma.cuh")]
 
 
 def kernel_hash() -> str:
-    return hashlib.sha256(open(KERNEL_SRC, "rb").read()).hexdigest()[:16]
+    """Hash of the step kernels' sources (the TMA staging included)."""
+    h = hashlib.sha256()
+    for p in KERNEL_SRCS:
+        h.update(open(p, "rb").read())
+    return h.hexdigest()[:16]
 
 
 def measured_peaks():

@@ -8,6 +8,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <algorithm>
 #include <cstring>
 #include <string>
@@ -492,6 +493,10 @@ lbm_status lbm_create(const lbm_domain* domain, const lbm_cylinder* cyl, const l
   uint8_t* dmask = static_cast<uint8_t*>(dalloc(c, N));
   d.mask = dmask;
   d.nb = (int)bnode.size();
+  {
+    const char* e = std::getenv("LBM_TMA");
+    d.tma = (e && e[0] == '0' && e[1] == 0) ? 0 : 1;
+  }
   int* dbn = static_cast<int*>(dalloc(c, sizeof(int) * (bnode.size() + 1)));
   double* dbv = static_cast<double*>(dalloc(c, sizeof(double) * (2 * bnode.size() + 1)));
   d.bnode = dbn;

@@ -71,6 +71,7 @@ struct Dev {
   const int* bnode;  // boundary fluid nodes (y * pitch + x)
   const double* bn;  // their outward normals, [2][nb]
   int nb;
+  int tma;           // 1: interior collision tiles are staged by TMA (environment LBM_TMA=0 turns it off)
   double* hf;        // heat-flux accumulators: last, sum, sum of squares, count
   double* partial;   // one heat-flux partial sum per energy-kernel block (zero between launches)
   int wall_tiles[2]; // energy tiles (32 wide, 8 or 16 high) that hold a near-wall node

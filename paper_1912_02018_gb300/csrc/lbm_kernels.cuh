@@ -1253,7 +1253,7 @@ int step_impl(const Geo& g, const Phys& ph, const Dev& d, int cur, int tcur, int
   // everywhere when a map cannot be made)
   using CS = CollStage<C, S, kCollTY>;
   CUtensorMap tm_f, tm_psi;
-  const bool staged = tma::encode<S>(&tm_f, f, g.nx, g.ny, g.pitch, g.plane, 9, CS::FW, CS::FH) &&
+  const bool staged = d.tma && tma::encode<S>(&tm_f, f, g.nx, g.ny, g.pitch, g.plane, 9, CS::FW, CS::FH) &&
                       tma::encode<C>(&tm_psi, psi, g.nx, g.ny, g.pitch, g.plane, 1, CS::PW, CS::PH);
   pre(kKCollide);
   k_collide<C, S><<<grd, blk, 0, s>>>(g, ph, f, fn, psi, d.mask, side_in, side_out, rho, ux, uy, forcing, d.status,

@@ -207,6 +207,24 @@ def test_psi_from_the_energy_pass_equals_the_psi_pass():
             assert np.array_equal(fa[k], fb[k]), (f64, k)
 
 
+@pytest.mark.parametrize("f64,storage,periodic_x", [(False, "f32", 0), (True, "f64", 0), (False, "f32", 1),
+                                                    (False, "f16s", 0), (False, "f64", 0)])
+def test_tma_staged_and_plain_collision_tiles_agree_bitwise(monkeypatch, f64, storage, periodic_x):
+    # interior collision tiles copy their pull window and psi tile into shared memory with TMA;
+    # LBM_TMA=0 (read at creation) makes every tile load from global memory: same bits
+    case = si.Case(nx=256, ny=96, D=24.0, xc=64.0, yc=48.0, Re=300.0, superheat_Tc=0.1, periodic_x=periodic_x,
+                   name="256x96_D24")
+    out = {}
+    for flag in ("1", "0"):
+        monkeypatch.setenv("LBM_TMA", flag)
+        s = Sim().from_case(case, f64=f64, storage=storage).step(40)
+        out[flag] = (s.fields(), s.get_state()[0], s.heat_flux()["q_mean"])
+    for k in FIELDS:
+        assert np.array_equal(out["1"][0][k], out["0"][0][k]), k
+    assert np.array_equal(out["1"][1], out["0"][1])
+    assert out["1"][2] == out["0"][2]
+
+
 def test_checkpoint_restart_is_bit_exact():
     case = si.SMALL
     drho = case.drho()
