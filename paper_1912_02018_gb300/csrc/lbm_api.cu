@@ -142,6 +142,8 @@ struct lbm_batch {
   bool use_graph = true;
   cudaGraphExec_t gexec = nullptr;
   int g_cur = -1, g_tcur = -1, g_variant = -1;
+  int g_launches[2] = {0, 0};    // launches of the two captured steps
+  std::vector<void*> psi_buf[2]; // per domain: psi of the state with population parity 0 / 1
   std::string err = "no error";
 };
 
@@ -892,23 +894,39 @@ static lbm_status batch_layout(lbm_batch* b) {
   return LBM_OK;
 }
 
-static int batch_launch(lbm_batch* b, cudaStream_t s) {
-  const int* m = b->d_maps;
-  return b->f64 ? lbm::batch_step_f64(b->variant, b->d_doms, m, b->nb_psi, m + b->max_tiles, b->nb_coll,
-                                      m + 2 * b->max_tiles, b->nb_en, b->cur, b->tcur, b->steps, s)
-                : lbm::batch_step_f32(b->variant, b->d_doms, m, b->nb_psi, m + b->max_tiles, b->nb_coll,
-                                      m + 2 * b->max_tiles, b->nb_en, b->cur, b->tcur, b->steps, s);
+// psi of the current state is unknown for some two-phase domain (creation, or a state set
+// through the API): the next step starts with the psi pass
+static bool batch_needs_psi(const lbm_batch* b) {
+  for (const lbm_ctx* c : b->ctx)
+    if (!c->psi_pending && c->ph.d.G != 0.0) return true;
+  return false;
 }
 
+static int batch_launch(lbm_batch* b, cudaStream_t s) {
+  const int* m = b->d_maps;
+  const int need_psi = batch_needs_psi(b) ? 1 : 0;
+  return b->f64 ? lbm::batch_step_f64(b->variant, b->d_doms, m, b->nb_psi, m + b->max_tiles, b->nb_coll,
+                                      m + 2 * b->max_tiles, b->nb_en, b->cur, b->tcur, b->steps, need_psi, s)
+                : lbm::batch_step_f32(b->variant, b->d_doms, m, b->nb_psi, m + b->max_tiles, b->nb_coll,
+                                      m + 2 * b->max_tiles, b->nb_en, b->cur, b->tcur, b->steps, need_psi, s);
+}
+
+// After a batched step: the energy pass has made psi of the new state in buffer b->cur; each
+// domain's context sees the buffers as a single-domain step leaves them (psi: the one the
+// step's collision used, psi_next: the pending one)
 static void batch_advance(lbm_batch* b, int launches) {
   b->cur ^= 1;
   b->tcur ^= 1;
   b->steps++;
-  for (lbm_ctx* c : b->ctx) {
+  for (size_t k = 0; k < b->ctx.size(); ++k) {
+    lbm_ctx* c = b->ctx[k];
     c->cur = b->cur;
     c->tcur = b->tcur;
     c->steps = b->steps;
     c->launches += launches;
+    c->dev.psi = b->psi_buf[b->cur ^ 1][k];
+    c->dev.psi_next = b->psi_buf[b->cur][k];
+    c->psi_pending = 1;
   }
 }
 
@@ -944,7 +962,9 @@ lbm_status lbm_batch_create(int32_t n, const lbm_domain* domains, const lbm_cyli
     lbm::BatchDomain D{};
     D.g = c->geo;
     D.ph = c->ph;
-    D.d = c->dev;
+    D.d = c->dev;  // psi, psi_next: the buffers of population parity 0 and 1
+    b->psi_buf[0].push_back(c->dev.psi);
+    b->psi_buf[1].push_back(c->dev.psi_next);
     D.warmup = params[k].warmup_steps;
     D.energy = params[k].energy;
     b->h_doms.push_back(D);
@@ -976,7 +996,8 @@ lbm_status lbm_batch_step(lbm_batch* b, int64_t n) {
   if (n < 0) return batch_fail(b, LBM_EINVAL, "negative step count");
   int64_t s = 0;
   // eager steps until every domain is past its warm-up (the graph bakes in the step counter)
-  while (s < n && (b->steps < b->max_warmup || !b->use_graph || n - s < 2)) {
+  // and psi of the current state is known (the graph holds no psi pass)
+  while (s < n && (b->steps < b->max_warmup || !b->use_graph || n - s < 2 || batch_needs_psi(b))) {
     const int k = batch_launch(b, b->stream);
     if (k < 0) return batch_fail(b, LBM_ECUDA, cudaGetErrorString(cudaGetLastError()));
     batch_advance(b, k);
@@ -1017,13 +1038,15 @@ lbm_status lbm_batch_step(lbm_batch* b, int64_t n) {
     b->g_cur = b->cur;
     b->g_tcur = b->tcur;
     b->g_variant = b->variant;
+    b->g_launches[0] = k1;
+    b->g_launches[1] = k2;
   }
   if (cudaEventRecord(b->ev_in, b->stream) != cudaSuccess || cudaStreamWaitEvent(b->gstream, b->ev_in, 0) != cudaSuccess)
     return batch_fail(b, LBM_ECUDA, "event ordering failed");
   for (; s + 2 <= n; s += 2) {
     if (cudaGraphLaunch(b->gexec, b->gstream) != cudaSuccess) return batch_fail(b, LBM_ECUDA, "graph launch failed");
-    batch_advance(b, 3);
-    batch_advance(b, 3);
+    batch_advance(b, b->g_launches[0]);
+    batch_advance(b, b->g_launches[1]);
   }
   if (cudaEventRecord(b->ev_out, b->gstream) != cudaSuccess || cudaStreamWaitEvent(b->stream, b->ev_out, 0) != cudaSuccess)
     return batch_fail(b, LBM_ECUDA, "event ordering failed");

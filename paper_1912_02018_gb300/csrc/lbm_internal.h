@@ -101,11 +101,14 @@ inline void batch_variant(int v, bool f64, int& cty, int& ety) {
 }
 
 // Batched step over all domains (one launch per pass).  maps: block -> domain index for
-// the psi, collision and energy passes.  Returns the number of launches or -1.
+// the psi, collision and energy passes; need_psi: run the psi pass first (psi of the current
+// state is not known from the last energy pass).  Returns the number of launches or -1.
 int batch_step_f32(int variant, const BatchDomain* doms, const int* map_psi, int nb_psi, const int* map_coll,
-                   int nb_coll, const int* map_en, int nb_en, int cur, int tcur, long long step, cudaStream_t s);
+                   int nb_coll, const int* map_en, int nb_en, int cur, int tcur, long long step, int need_psi,
+                   cudaStream_t s);
 int batch_step_f64(int variant, const BatchDomain* doms, const int* map_psi, int nb_psi, const int* map_coll,
-                   int nb_coll, const int* map_en, int nb_en, int cur, int tcur, long long step, cudaStream_t s);
+                   int nb_coll, const int* map_en, int nb_en, int cur, int tcur, long long step, int need_psi,
+                   cudaStream_t s);
 
 // Kernel identifiers for per-launch timing.
 enum KernelId { kKRhoPsi = 0, kKCollide, kKEnergy, kKExport, kKImport, kNumKernels };

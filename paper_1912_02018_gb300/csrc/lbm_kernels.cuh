@@ -493,9 +493,6 @@ __global__ void __launch_bounds__(256) k_rho_psi(Geo g, Phys ph, const S* __rest
   rho_psi_tile<C, S, PSI>(g, ph, f, T, mask, side_in, psi_o, status, blockIdx.x, blockIdx.y);
 }
 
-// Pull, interaction force from a psi tile with a 2-node halo, gravity, CM collision, for
-// tile (bx, by) of 32 x CTY nodes; writes f* (other buffer), rho, u and the outlet's
-// streamed values.
 // Shared-memory staging of a collision tile.  Populations: the tile's rows with a 1-row halo,
 // columns from x0 - XA (XA elements = 16 bytes, the alignment of a TMA copy's first column);
 // psi: a 2-row and PA-column halo.  Tiles whose staged boxes lie inside the lattice (no wrap,
@@ -512,6 +509,9 @@ __device__ __forceinline__ bool coll_staged(const Geo& g, int x0, int y0) {
   return x0 >= M && x0 + kCollTX + M <= g.nx && y0 >= 2 && y0 + CTY + 2 <= g.ny;
 }
 
+// Pull, interaction force from a psi tile with a 2-node halo, gravity, CM collision, for
+// tile (bx, by) of 32 x CTY nodes; writes f* (other buffer), rho, u and the outlet's
+// streamed values.  tm_f, tm_psi: tensor maps of f and psi for TMA staging, or null.
 template <typename C, typename S, int CTY>
 __device__ __forceinline__ void collide_tile(const Geo& g, const Phys& ph, const S* __restrict__ f,
                                              S* __restrict__ fn, const C* __restrict__ psi,
@@ -1060,6 +1060,13 @@ __global__ void __launch_bounds__(EnergyTile<C>::NT, sizeof(C) == 4 ? (sizeof(S)
 // ---------------------------------------------------------------- batched passes
 // Every block of a batched pass finds its domain through the block -> domain map and its
 // tile from its index within that domain; the tile bodies are the single-domain ones.
+// psi of the state with population parity p sits in domain buffer p (psi, psi_next): the
+// energy pass of a step with parity cur writes psi of the next state into buffer cur ^ 1,
+// so the psi pass runs only when the host no longer knows psi (creation, a state change).
+template <typename C>
+__device__ __forceinline__ C* psi_buf(const BatchDomain& D, int p) {
+  return static_cast<C*>(p ? D.d.psi_next : D.d.psi);
+}
 template <typename C, typename S, int PSI>
 __global__ void __launch_bounds__(256) kb_rho_psi(const BatchDomain* __restrict__ doms, const int* __restrict__ map,
                                                  int cur, int tcur) {
@@ -1067,7 +1074,7 @@ __global__ void __launch_bounds__(256) kb_rho_psi(const BatchDomain* __restrict_
   if (pc<C>(D.ph).G == C(0)) return;
   const int local = blockIdx.x - D.psi_first;
   rho_psi_tile<C, S, PSI>(D.g, D.ph, static_cast<const S*>(D.d.f[cur]), static_cast<const C*>(D.d.T[tcur]),
-                          D.d.mask, static_cast<const C*>(D.d.side[cur]), static_cast<C*>(D.d.psi), D.d.status,
+                          D.d.mask, static_cast<const C*>(D.d.side[cur]), psi_buf<C>(D, cur), D.d.status,
                           local % D.psi_ntx, local / D.psi_ntx);
 }
 template <typename C, typename S, int CTY>
@@ -1076,40 +1083,51 @@ __global__ void __launch_bounds__(kCollTX* CTY, (sizeof(C) == 4 && CTY == 8) ? 7
   const BatchDomain& D = doms[map[blockIdx.x]];
   const int local = blockIdx.x - D.coll_first;
   collide_tile<C, S, CTY>(D.g, D.ph, static_cast<const S*>(D.d.f[cur]), static_cast<S*>(D.d.f[cur ^ 1]),
-                          static_cast<const C*>(D.d.psi), D.d.mask, static_cast<const C*>(D.d.side[cur]),
+                          psi_buf<C>(D, cur), D.d.mask, static_cast<const C*>(D.d.side[cur]),
                           static_cast<C*>(D.d.side[cur ^ 1]), static_cast<C*>(D.d.rho), static_cast<C*>(D.d.ux),
                           static_cast<C*>(D.d.uy), step >= D.warmup, D.d.status, local % D.coll_ntx,
                           local / D.coll_ntx);
 }
-template <typename C, int ETY>
+template <typename C, int ETY, int PSI>
 __global__ void __launch_bounds__(EnergyTile<C, ETY>::NT) kb_energy(const BatchDomain* __restrict__ doms,
-                                                                   const int* __restrict__ map, int tcur,
+                                                                   const int* __restrict__ map, int cur, int tcur,
                                                                    long long step) {
   const BatchDomain& D = doms[map[blockIdx.x]];
   const int local = blockIdx.x - D.en_first, bx = local % D.en_ntx, by = local / D.en_ntx;
   const C* Tin = static_cast<const C*>(D.d.T[tcur]);
   C* Tout = static_cast<C*>(D.d.T[tcur ^ 1]);
+  const C* fnew = static_cast<const C*>(D.d.f[cur ^ 1]);
+  const C* side_new = static_cast<const C*>(D.d.side[cur ^ 1]);
+  C* psi_next = pc<C>(D.ph).G != C(0) ? psi_buf<C>(D, cur ^ 1) : nullptr;
   if (!D.energy || step < D.warmup) {
-    // no energy update for this domain this step: carry T over so all domains flip together
+    // no energy update for this domain this step: carry T over so all domains flip together,
+    // and make psi of the next state from the new populations and the unchanged T
     constexpr int TX = EnergyTile<C, ETY>::TX, TY = EnergyTile<C, ETY>::TY;
     for (int p = threadIdx.x; p < TX * TY; p += EnergyTile<C, ETY>::NT) {
       const int x = bx * TX + p % TX, y = by * TY + p / TX;
-      if (x < D.g.nx && y < D.g.ny) Tout[y * D.g.pitch + x] = Tin[y * D.g.pitch + x];
+      if (x < D.g.nx && y < D.g.ny) {
+        Tout[y * D.g.pitch + x] = Tin[y * D.g.pitch + x];
+        if (psi_next)
+          psi_next[y * D.g.pitch + x] =
+              psi_node<C, C, PSI>(D.g, D.ph, fnew, Tin, D.d.mask, side_new, x, y, D.d.status);
+      }
     }
     return;
   }
-  energy_tile<C, ETY>(D.g, D.ph, Tin, Tout, static_cast<const C*>(D.d.rho), static_cast<const C*>(D.d.ux),
-                      static_cast<const C*>(D.d.uy), D.d.mask, D.d.partial, D.d.counter, D.d.hf, D.d.nb, D.d.nb > 0,
-                      D.d.wall_tiles[ETY == 16 ? 1 : 0], bx, by, local, D.en_nblocks);
+  energy_tile<C, ETY, C, PSI, true>(D.g, D.ph, Tin, Tout, static_cast<const C*>(D.d.rho),
+                                    static_cast<const C*>(D.d.ux), static_cast<const C*>(D.d.uy), D.d.mask,
+                                    D.d.partial, D.d.counter, D.d.hf, D.d.nb, D.d.nb > 0,
+                                    D.d.wall_tiles[ETY == 16 ? 1 : 0], bx, by, local, D.en_nblocks, fnew, side_new,
+                                    psi_next, D.d.status);
 }
 
 template <typename C, typename S, int PSI, int CTY, int ETY>
 int batch_step_impl(const BatchDomain* doms, const int* map_psi, int nb_psi, const int* map_coll, int nb_coll,
-                    const int* map_en, int nb_en, int cur, int tcur, long long step, cudaStream_t s) {
-  kb_rho_psi<C, S, PSI><<<nb_psi, dim3(kCollTX, 8), 0, s>>>(doms, map_psi, cur, tcur);
+                    const int* map_en, int nb_en, int cur, int tcur, long long step, int need_psi, cudaStream_t s) {
+  if (need_psi) kb_rho_psi<C, S, PSI><<<nb_psi, dim3(kCollTX, 8), 0, s>>>(doms, map_psi, cur, tcur);
   kb_collide<C, S, CTY><<<nb_coll, dim3(kCollTX, CTY), 0, s>>>(doms, map_coll, cur, step);
-  kb_energy<C, ETY><<<nb_en, EnergyTile<C, ETY>::NT, 0, s>>>(doms, map_en, tcur, step);
-  return cudaPeekAtLastError() == cudaSuccess ? 3 : -1;
+  kb_energy<C, ETY, PSI><<<nb_en, EnergyTile<C, ETY>::NT, 0, s>>>(doms, map_en, cur, tcur, step);
+  return cudaPeekAtLastError() == cudaSuccess ? (need_psi ? 3 : 2) : -1;
 }
 
 // ---------------------------------------------------------------- init / export / import
