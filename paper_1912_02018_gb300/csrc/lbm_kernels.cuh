@@ -72,6 +72,26 @@ __device__ __forceinline__ float fdiv<float>(float a, float b) {
   return __fdividef(a, b);
 }
 
+// Sums and products whose rounding the source fixes, whatever kernel they are inlined into:
+// FP32 fuses a b + c into one fma; FP64 rounds the product and the sum separately, as the
+// FP64 build (compiled without contraction) does for every expression.
+template <typename C>
+__device__ __forceinline__ C mad(C a, C b, C c);
+template <>
+__device__ __forceinline__ float mad<float>(float a, float b, float c) {
+  return __fmaf_rn(a, b, c);
+}
+template <>
+__device__ __forceinline__ double mad<double>(double a, double b, double c) {
+  return __dadd_rn(__dmul_rn(a, b), c);
+}
+__device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
+
 // ---------------------------------------------------------------- addressing
 // Node coordinate of an arbitrary lattice position for stencil reads: periodic in y; in x
 // periodic, or the nearest boundary column (zero-gradient ghost) at the inlet and outlet.
@@ -266,18 +286,18 @@ __device__ __forceinline__ C dpdT_eos(const Phys& ph, C rho, C T) {
 template <typename C>
 __device__ __forceinline__ C phase_frac(const Phys& ph, C rho) {
   if (!(pc<C>(ph).rho_l > pc<C>(ph).rho_v)) return C(1);
-  C f = fdiv(rho - pc<C>(ph).rho_v, pc<C>(ph).rho_l - pc<C>(ph).rho_v);
+  C f = fdiv(sub(rho, pc<C>(ph).rho_v), sub(pc<C>(ph).rho_l, pc<C>(ph).rho_v));
   f = f < C(0) ? C(0) : f;
   return f > C(1) ? C(1) : f;
 }
 template <typename C>
 __device__ __forceinline__ C nu_of(const Phys& ph, C rho) {
-  return pc<C>(ph).nu_v + phase_frac(ph, rho) * (pc<C>(ph).nu_l - pc<C>(ph).nu_v);
+  return mad(phase_frac(ph, rho), sub(pc<C>(ph).nu_l, pc<C>(ph).nu_v), pc<C>(ph).nu_v);
 }
 template <typename C>
 __device__ __forceinline__ C lam_of(const Phys& ph, C rho) {
-  C alpha = pc<C>(ph).alpha_v + phase_frac(ph, rho) * (pc<C>(ph).alpha_l - pc<C>(ph).alpha_v);
-  return rho * pc<C>(ph).c_v * alpha;
+  C alpha = mad(phase_frac(ph, rho), sub(pc<C>(ph).alpha_l, pc<C>(ph).alpha_v), pc<C>(ph).alpha_v);
+  return mul(mul(rho, pc<C>(ph).c_v), alpha);
 }
 
 // ---------------------------------------------------------------- stencils on tiles (Sec. II.C)
@@ -291,9 +311,9 @@ __device__ __forceinline__ void grad_t(const C* p, int s, C& gx, C& gy) {
     const int ex = exv(k), ey = eyv(k);
     if ((kX && ex != 0) || (kY && ey != 0)) {
       // w e is w scaled by a power of two: (w e) d rounds exactly like (w d) e
-      C d = p[ey * s + ex] - p[-ey * s - ex];
-      if (kX && ex != 0) sx = sx + C(wiso(k) * ex) * d;
-      if (kY && ey != 0) sy = sy + C(wiso(k) * ey) * d;
+      C d = sub(p[ey * s + ex], p[-ey * s - ex]);
+      if (kX && ex != 0) sx = mad(C(wiso(k) * ex), d, sx);
+      if (kY && ey != 0) sy = mad(C(wiso(k) * ey), d, sy);
     }
   }
   gx = sx;
@@ -333,9 +353,11 @@ __device__ __forceinline__ void pull_slow(const Geo& g, const Phys& ph, const S*
         const int nyp = wrap_y(g, y + cy);
         if (g.periodic_x) nxp = nxp < 0 ? nxp + g.nx : (nxp >= g.nx ? nxp - g.nx : nxp);
         const bool ok = nxp >= 0 && nxp < g.nx && !(mask[nyp * g.pitch + nxp] & kSolid);
-        v = ok ? C(2) * q * a + (C(1) - C(2) * q) * ldf<C>(g, ph, f, io, nyp, nxp) : a;
+        const C q2 = mul(C(2), q);
+        v = ok ? add(mul(q2, a), mul(sub(C(1), q2), ldf<C>(g, ph, f, io, nyp, nxp))) : a;
       } else {
-        v = fdiv(a, C(2) * q) + fdiv(C(2) * q - C(1), C(2) * q) * ldf<C>(g, ph, f, i, y, x);
+        const C q2 = mul(C(2), q);
+        v = add(fdiv(a, q2), mul(fdiv(sub(q2, C(1)), q2), ldf<C>(g, ph, f, i, y, x)));
       }
     } else {
       v = ldf<C>(g, ph, f, i, sy, sx);
@@ -346,10 +368,10 @@ __device__ __forceinline__ void pull_slow(const Geo& g, const Phys& ph, const S*
   if (x == 0) {
     // Zou-He velocity inlet, u = (u_in, 0): unknowns f1, f5, f7
     const C u = pc<C>(ph).u_in;
-    const C rho = fdiv(fo[0] + fo[3] + fo[4] + C(2) * (fo[2] + fo[6] + fo[8]), C(1) - u);
-    fo[1] = fo[2] + C(2.0 / 3.0) * rho * u;
-    fo[5] = fo[6] - C(0.5) * (fo[3] - fo[4]) + fdiv(rho * u, C(6));
-    fo[7] = fo[8] + C(0.5) * (fo[3] - fo[4]) + fdiv(rho * u, C(6));
+    const C rho = fdiv(add(add(add(fo[0], fo[3]), fo[4]), mul(C(2), add(add(fo[2], fo[6]), fo[8]))), sub(C(1), u));
+    fo[1] = add(fo[2], mul(mul(C(2.0 / 3.0), rho), u));
+    fo[5] = add(sub(fo[6], mul(C(0.5), sub(fo[3], fo[4]))), fdiv(mul(rho, u), C(6)));
+    fo[7] = add(add(fo[8], mul(C(0.5), sub(fo[3], fo[4]))), fdiv(mul(rho, u), C(6)));
   }
   if (x == g.nx - 1) {
     // convective outlet: f(t+1) = (f(t) + U f_{nx-2}(t+1)) / (1 + U) for f2, f6, f8
@@ -358,7 +380,7 @@ __device__ __forceinline__ void pull_slow(const Geo& g, const Phys& ph, const S*
     for (int j = 0; j < 3; ++j) {
       const int i = j == 0 ? 2 : (j == 1 ? 6 : 8);
       const C inner = ldf<C>(g, ph, f, i, wrap_y(g, y - cyv(i)), g.nx - 1);
-      const C v = fdiv(side_in[j * g.ny + y] + U * inner, C(1) + U);
+      const C v = fdiv(add(side_in[j * g.ny + y], mul(U, inner)), add(C(1), U));
       fo[i] = v;
       if (side_out) side_out[j * g.ny + y] = v;
     }
@@ -471,6 +493,69 @@ __device__ __forceinline__ void collide(const C f[9], C rho, C Fx, C Fy, C Fmx, 
   fs[7] = ((-q * ms5 - q * ms6) + q * ms7) + q * ms8;
   fs[8] = ((-q * ms5 + q * ms6) - q * ms7) + q * ms8;
 }
+// The same for FP32 with every rounding written out (explicit fma, mul, add), so that the
+// result does not depend on which kernel inlines it.  Forward substitution of N(u) m* = k*
+// in closed form; m*_1 = k*_1 + u rho = m1 + Fx and m*_2 = m2 + Fy hold exactly since
+// u rho = m1 + Fx / 2.
+template <>
+__device__ __forceinline__ void collide<float>(const float f[9], float rho, float Fx, float Fy, float Fmx, float Fmy,
+                                               float psi, float omega, float sigma, float fs[9], float& ux,
+                                               float& uy) {
+  const float a56 = __fsub_rn(f[5], f[6]), a78 = __fsub_rn(f[7], f[8]);
+  const float m1 = __fadd_rn(__fadd_rn(__fsub_rn(f[1], f[2]), a56), a78);
+  const float m2 = __fsub_rn(__fadd_rn(__fsub_rn(f[3], f[4]), a56), a78);
+  const float m4 = __fsub_rn(__fadd_rn(f[1], f[2]), __fadd_rn(f[3], f[4]));
+  const float m5 = __fsub_rn(__fadd_rn(f[5], f[6]), __fadd_rn(f[7], f[8]));
+  const float u = __fdividef(__fmaf_rn(0.5f, Fx, m1), rho), v = __fdividef(__fmaf_rn(0.5f, Fy, m2), rho);
+  ux = u;
+  uy = v;
+  const float uu = __fmul_rn(u, u), vv = __fmul_rn(v, v), uv = __fmul_rn(u, v);
+  const float s2 = __fadd_rn(uu, vv), d2 = __fsub_rn(uu, vv), u2 = __fmul_rn(2.0f, u), v2 = __fmul_rn(2.0f, v);
+  // central moments k4, k5 of the pre-collision populations (Eq. (postColl2) shift)
+  const float k4 = __fmaf_rn(d2, rho, __fmaf_rn(v2, m2, __fmaf_rn(-u2, m1, m4)));
+  const float k5 = __fmaf_rn(uv, rho, __fmaf_rn(-v, m1, __fmaf_rn(-u, m2, m5)));
+  // post-collision central moments with the consistency terms alpha |Fm|^2
+  const float alpha = sigma != 0.0f ? __fdividef(sigma, __fmul_rn(psi, psi)) : 0.0f;
+  const float aF = __fmul_rn(alpha, __fmaf_rn(Fmx, Fmx, __fmul_rn(Fmy, Fmy)));
+  const float om = __fsub_rn(1.0f, omega);
+  const float ks3 = __fmaf_rn(2.0f, aF, __fmul_rn(2.0f / 3.0f, rho));
+  const float ks4 = __fmul_rn(om, k4), ks5 = __fmul_rn(om, k5);
+  const float ks6 = __fmul_rn(1.0f / 6.0f, Fy), ks7 = __fmul_rn(1.0f / 6.0f, Fx);
+  const float ks8 = __fmaf_rn(2.0f / 3.0f, aF, __fmul_rn(1.0f / 9.0f, rho));
+  // raw moments m* = N(u)^{-1} k*
+  const float ms1 = __fadd_rn(m1, Fx), ms2 = __fadd_rn(m2, Fy);
+  const float ms3 = __fmaf_rn(u2, ms1, __fmaf_rn(v2, ms2, __fmaf_rn(-s2, rho, ks3)));
+  const float ms4 = __fmaf_rn(u2, ms1, __fmaf_rn(-v2, ms2, __fmaf_rn(-d2, rho, ks4)));
+  const float ms5 = __fmaf_rn(v, ms1, __fmaf_rn(u, ms2, __fmaf_rn(-uv, rho, ks5)));
+  const float uv2 = __fmul_rn(2.0f, uv);
+  const float ms6 = __fmaf_rn(u2, ms5, __fmaf_rn(__fmul_rn(0.5f, v), __fadd_rn(ms3, ms4),
+                              __fmaf_rn(-uu, ms2, __fmaf_rn(-uv2, ms1, __fmaf_rn(__fmul_rn(uu, v), rho, ks6)))));
+  const float ms7 = __fmaf_rn(v2, ms5, __fmaf_rn(__fmul_rn(0.5f, u), __fsub_rn(ms3, ms4),
+                              __fmaf_rn(-uv2, ms2, __fmaf_rn(-vv, ms1, __fmaf_rn(__fmul_rn(u, vv), rho, ks7)))));
+  const float ms8 = __fmaf_rn(
+      u2, ms7,
+      __fmaf_rn(v2, ms6,
+                __fmaf_rn(__fmul_rn(-2.0f, uv2), ms5,
+                          __fmaf_rn(__fmul_rn(0.5f, d2), ms4,
+                                    __fmaf_rn(__fmul_rn(-0.5f, s2), ms3,
+                                              __fmaf_rn(__fmul_rn(uv2, u), ms2,
+                                                        __fmaf_rn(__fmul_rn(uv2, v), ms1,
+                                                                  __fmaf_rn(-__fmul_rn(uu, vv), rho, ks8))))))));
+  // f* = M^{-1} m*
+  const float A = __fmul_rn(0.25f, __fadd_rn(ms3, ms4)), B = __fmul_rn(0.25f, __fsub_rn(ms3, ms4));
+  const float c = __fmaf_rn(-0.5f, ms8, A), e = __fmaf_rn(-0.5f, ms8, B);
+  const float d = __fmul_rn(0.5f, __fsub_rn(ms1, ms7)), gy = __fmul_rn(0.5f, __fsub_rn(ms2, ms6));
+  fs[0] = __fadd_rn(__fsub_rn(rho, ms3), ms8);
+  fs[1] = __fadd_rn(c, d);
+  fs[2] = __fsub_rn(c, d);
+  fs[3] = __fadd_rn(e, gy);
+  fs[4] = __fsub_rn(e, gy);
+  const float sp = __fadd_rn(ms5, ms8), tp = __fadd_rn(ms6, ms7), wm = __fsub_rn(ms8, ms5), zm = __fsub_rn(ms6, ms7);
+  fs[5] = __fmul_rn(0.25f, __fadd_rn(sp, tp));
+  fs[6] = __fmul_rn(0.25f, __fsub_rn(sp, tp));
+  fs[7] = __fmul_rn(0.25f, __fsub_rn(wm, zm));
+  fs[8] = __fmul_rn(0.25f, __fadd_rn(wm, zm));
+}
 
 // ---------------------------------------------------------------- k_rho_psi, k_collide
 constexpr int kCollTX = 32, kCollTY = 8;
@@ -509,61 +594,29 @@ __device__ __forceinline__ bool coll_staged(const Geo& g, int x0, int y0) {
   return x0 >= M && x0 + kCollTX + M <= g.nx && y0 >= 2 && y0 + CTY + 2 <= g.ny;
 }
 
-// Pull, interaction force from a psi tile with a 2-node halo, gravity, CM collision, for
-// tile (bx, by) of 32 x CTY nodes; writes f* (other buffer), rho, u and the outlet's
-// streamed values.  tm_f, tm_psi: tensor maps of f and psi for TMA staging, or null.
+// One fluid-or-solid node (x, y) = (x0 + tx, y0 + ty) of a collision tile, mask m: pull (from
+// the staged populations s_f of a staged tile, else from global memory with the boundary
+// substitutions), interaction force from the psi tile s_psi with its 2-node halo, gravity,
+// CM collision; writes f* (other buffer), rho, u and the outlet's streamed values.
 template <typename C, typename S, int CTY>
-__device__ __forceinline__ void collide_tile(const Geo& g, const Phys& ph, const S* __restrict__ f,
+__device__ __forceinline__ void collide_node(const Geo& g, const Phys& ph, const S* __restrict__ f,
                                              S* __restrict__ fn, const C* __restrict__ psi,
                                              const uint8_t* __restrict__ mask, const C* __restrict__ side_in,
                                              C* __restrict__ side_out, C* __restrict__ rho_o, C* __restrict__ ux_o,
-                                             C* __restrict__ uy_o, int forcing, int* status, int bx, int by,
-                                             const CUtensorMap* tm_f = nullptr, const CUtensorMap* tm_psi = nullptr) {
+                                             C* __restrict__ uy_o, int forcing, int* status, int tx, int ty, int x,
+                                             int y, uint8_t m, bool staged, const S* s_f, const C* s_psi) {
   using CS = CollStage<C, S, CTY>;
-  constexpr int HX = CS::PW, HY = CS::PH;
-  __shared__ __align__(128) S s_f[9 * CS::FH * CS::FW];
-  __shared__ __align__(128) C s_psi[HY * HX];
-  __shared__ uint64_t s_bar;
+  constexpr int HX = CS::PW;
   const PhysC<C>& k = pc<C>(ph);
-  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * kCollTX + tx;
-  const int x0 = bx * kCollTX, y0 = by * CTY;
-  const int x = x0 + tx, y = y0 + ty;
-  const bool multiphase = k.G != C(0);
-  const bool need_psi = multiphase && forcing;
-  const bool staged = tm_f && (!need_psi || tm_psi) && coll_staged<C, S, CTY>(g, x0, y0);
-  if (staged) {
-    if (tid == 0) tma::bar_init(&s_bar, 1);
-    __syncthreads();
-    if (tid == 0) {
-      const uint32_t bytes = sizeof(S) * 9 * CS::FH * CS::FW + (need_psi ? sizeof(C) * HX * HY : 0);
-      tma::bar_expect_tx(&s_bar, bytes);
-      tma::load_3d(s_f, tm_f, &s_bar, x0 - CS::XA, y0 - 1, 0);
-      if (need_psi) tma::load_2d(s_psi, tm_psi, &s_bar, x0 - CS::PA, y0 - 2);
-    }
-  } else if (need_psi) {
-    for (int p = tid; p < HX * HY; p += kCollTX * CTY) {
-      const int hx = p % HX, hy = p / HX;
-      s_psi[p] = psi[map_y(g, y0 + hy - 2) * g.pitch + map_x(g, x0 + hx - CS::PA)];
-    }
-    __syncthreads();
-  }
-  const bool inside = x < g.nx && y < g.ny;
   const int id = y * g.pitch + x;
-  const uint8_t m = inside ? mask[id] : kSolid;
-  if (staged && !tma::bar_wait(&s_bar, 0, tma::kWaitTries)) {
-    // the copies did not land in time: report it, give them a second bound to land before the
-    // block's shared memory is released, and produce nothing
-    if (tid == 0) atomicOr(status, 4);
-    tma::bar_wait(&s_bar, 0, tma::kWaitTries);
-    return;
-  }
-  if (!inside) return;
   if (m & kSolid) {
     rho_o[id] = k.rho_s;
     ux_o[id] = C(0);
     uy_o[id] = C(0);
     return;
   }
+  const bool multiphase = k.G != C(0);
+  const bool need_psi = multiphase && forcing;
   C fo[9];
   if (staged) {
     // a staged tile holds no inlet or outlet column; wall nodes redo the pull with substitutions
@@ -588,10 +641,10 @@ __device__ __forceinline__ void collide_tile(const Geo& g, const Phys& ph, const
     Fmy = -k.G * cs2 * psi0 * sy;
   }
   if (forcing) {
-    Fx = Fmx - (rho - k.rho_l) * k.g;
+    Fx = sub(Fmx, mul(sub(rho, k.rho_l), k.g));
     Fy = Fmy;
   }
-  const C omega = fdiv(C(1), fdiv(nu_of(ph, rho), cs2) + C(0.5));
+  const C omega = fdiv(C(1), add(fdiv(nu_of(ph, rho), cs2), C(0.5)));
   const C sig = need_psi ? k.sigma : C(0);
   C fs[9], ux, uy;
   collide(fo, rho, Fx, Fy, Fmx, Fmy, psi0, omega, sig, fs, ux, uy);
@@ -601,6 +654,62 @@ __device__ __forceinline__ void collide_tile(const Geo& g, const Phys& ph, const
   ux_o[id] = ux;
   uy_o[id] = uy;
   if (!(rho > C(0)) || !(ux == ux) || !(uy == uy)) atomicOr(status, 1);
+}
+
+// The psi tile of tile (x0, y0) with plain loads (periodic in y, clamped or periodic in x).
+template <typename C, typename S, int CTY>
+__device__ __forceinline__ void psi_tile_plain(const Geo& g, const C* __restrict__ psi, int x0, int y0, C* s_psi) {
+  using CS = CollStage<C, S, CTY>;
+  for (int p = threadIdx.y * kCollTX + threadIdx.x; p < CS::PW * CS::PH; p += kCollTX * CTY) {
+    const int hx = p % CS::PW, hy = p / CS::PW;
+    s_psi[p] = psi[map_y(g, y0 + hy - 2) * g.pitch + map_x(g, x0 + hx - CS::PA)];
+  }
+}
+
+// Collision tile (bx, by) of 32 x CTY nodes.  tm_f, tm_psi: tensor maps of f and psi for TMA
+// staging, or null.
+template <typename C, typename S, int CTY>
+__device__ __forceinline__ void collide_tile(const Geo& g, const Phys& ph, const S* __restrict__ f,
+                                             S* __restrict__ fn, const C* __restrict__ psi,
+                                             const uint8_t* __restrict__ mask, const C* __restrict__ side_in,
+                                             C* __restrict__ side_out, C* __restrict__ rho_o, C* __restrict__ ux_o,
+                                             C* __restrict__ uy_o, int forcing, int* status, int bx, int by,
+                                             const CUtensorMap* tm_f = nullptr, const CUtensorMap* tm_psi = nullptr) {
+  using CS = CollStage<C, S, CTY>;
+  constexpr int HX = CS::PW, HY = CS::PH;
+  __shared__ __align__(128) S s_f[9 * CS::FH * CS::FW];
+  __shared__ __align__(128) C s_psi[HY * HX];
+  __shared__ uint64_t s_bar;
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * kCollTX + tx;
+  const int x0 = bx * kCollTX, y0 = by * CTY;
+  const int x = x0 + tx, y = y0 + ty;
+  const bool need_psi = pc<C>(ph).G != C(0) && forcing;
+  const bool staged = tm_f && (!need_psi || tm_psi) && coll_staged<C, S, CTY>(g, x0, y0);
+  if (staged) {
+    if (tid == 0) tma::bar_init(&s_bar, 1);
+    __syncthreads();
+    if (tid == 0) {
+      const uint32_t bytes = sizeof(S) * 9 * CS::FH * CS::FW + (need_psi ? sizeof(C) * HX * HY : 0);
+      tma::bar_expect_tx(&s_bar, bytes);
+      tma::load_3d(s_f, tm_f, &s_bar, x0 - CS::XA, y0 - 1, 0);
+      if (need_psi) tma::load_2d(s_psi, tm_psi, &s_bar, x0 - CS::PA, y0 - 2);
+    }
+  } else if (need_psi) {
+    psi_tile_plain<C, S, CTY>(g, psi, x0, y0, s_psi);
+    __syncthreads();
+  }
+  const bool inside = x < g.nx && y < g.ny;
+  const uint8_t m = inside ? mask[y * g.pitch + x] : kSolid;
+  if (staged && !tma::bar_wait(&s_bar, 0, tma::kWaitTries)) {
+    // the copies did not land in time: report it, give them a second bound to land before the
+    // block's shared memory is released, and produce nothing
+    if (tid == 0) atomicOr(status, 4);
+    tma::bar_wait(&s_bar, 0, tma::kWaitTries);
+    return;
+  }
+  if (!inside) return;
+  collide_node<C, S, CTY>(g, ph, f, fn, psi, mask, side_in, side_out, rho_o, ux_o, uy_o, forcing, status, tx, ty, x,
+                          y, m, staged, s_f, s_psi);
 }
 
 template <typename C, typename S>
