@@ -1060,6 +1060,12 @@ __device__ __forceinline__ void heat_flux_blocks(double q, int mine, double* par
   }
 }
 
+// Tensor maps of the energy pass's inputs (T, rho, u_x, u_y), each with the box of a tile and
+// its 4-node halo; interior tiles copy them into shared memory with TMA.
+struct EnergyMaps {
+  CUtensorMap T, r, u, v;
+};
+
 template <typename C, int TY_ = (sizeof(C) == 8 ? 8 : kEnergyTY)>
 struct EnergyTile {
   static constexpr int TX = kEnergyTX;
@@ -1080,15 +1086,17 @@ __device__ __forceinline__ void energy_tile(const Geo& g, const Phys& ph, const 
                                             int n_wall_tiles, int bx, int by, int bid, int nblocks,
                                             const S* __restrict__ fnew = nullptr, const C* __restrict__ side_new = nullptr,
                                             C* __restrict__ psi_out = nullptr, int* status = nullptr,
-                                            C* __restrict__ t1_out = nullptr) {
+                                            C* __restrict__ t1_out = nullptr, const EnergyMaps* maps = nullptr) {
   constexpr int TX = EnergyTile<C, ETY>::TX, TY = EnergyTile<C, ETY>::TY, NT = EnergyTile<C, ETY>::NT;
   constexpr int H = 4, AX = TX + 2 * H, AY = TY + 2 * H;  // inputs: tile + 4
   constexpr int BX = TX + 4, BY = TY + 4;                 // stage 1: tile + 2
-  __shared__ __align__(16) C sT[AY * AX];
-  __shared__ __align__(16) C sL[AY * AX];
-  __shared__ __align__(16) C sU[AY * AX];
-  __shared__ __align__(16) C sV[AY * AX];
-  __shared__ __align__(16) C sR[AY * AX];
+  static_assert(AX * AY * sizeof(C) % 128 == 0 && AX * sizeof(C) % 16 == 0, "TMA boxes of the input tile");
+  __shared__ __align__(128) C sT[AY * AX];
+  __shared__ __align__(128) C sL[AY * AX];
+  __shared__ __align__(128) C sU[AY * AX];
+  __shared__ __align__(128) C sV[AY * AX];
+  __shared__ __align__(128) C sR[AY * AX];
+  __shared__ uint64_t s_bar;
   __shared__ __align__(16) C sT1[BY * BX];
   __shared__ Frozen<C> sF[TX * TY];
   __shared__ uint8_t sM[AY * AX];
@@ -1097,16 +1105,39 @@ __device__ __forceinline__ void energy_tile(const Geo& g, const Phys& ph, const 
   const int tid = threadIdx.x;
   const int x0 = bx * TX, y0 = by * TY;
   const bool interior = x0 >= H && y0 >= H && x0 + TX + H <= g.nx && y0 + TY + H <= g.ny;
-  for (int p = tid; p < AX * AY; p += NT) {
-    const int gx = x0 + p % AX - H, gy = y0 + p / AX - H;
-    const int nid = interior ? gy * g.pitch + gx : map_y(g, gy) * g.pitch + map_x(g, gx);
-    const C r = rho[nid];
-    sT[p] = Tin[nid];
-    sR[p] = r;
-    sL[p] = lam_of(ph, r);
-    sU[p] = ux[nid];
-    sV[p] = uy[nid];
-    sM[p] = mask[nid];
+  if (maps && interior) {
+    // the four input boxes by TMA (first column x0 - 4: 16-byte aligned); the mask with plain
+    // loads while they fly; lambda(rho) once rho has landed
+    if (tid == 0) tma::bar_init(&s_bar, 1);
+    __syncthreads();
+    if (tid == 0) {
+      tma::bar_expect_tx(&s_bar, 4 * AX * AY * sizeof(C));
+      tma::load_2d(sT, &maps->T, &s_bar, x0 - H, y0 - H);
+      tma::load_2d(sR, &maps->r, &s_bar, x0 - H, y0 - H);
+      tma::load_2d(sU, &maps->u, &s_bar, x0 - H, y0 - H);
+      tma::load_2d(sV, &maps->v, &s_bar, x0 - H, y0 - H);
+    }
+    for (int p = tid; p < AX * AY; p += NT) sM[p] = mask[(y0 + p / AX - H) * g.pitch + x0 + p % AX - H];
+    const bool landed = tma::bar_wait(&s_bar, 0, tma::kWaitTries);
+    if (__syncthreads_or(!landed)) {
+      // a copy did not land in time: report it, let the copies land (bounded) and stop the tile
+      if (tid == 0) atomicOr(status, 4);
+      tma::bar_wait(&s_bar, 0, tma::kWaitTries);
+      return;
+    }
+    for (int p = tid; p < AX * AY; p += NT) sL[p] = lam_of(ph, sR[p]);
+  } else {
+    for (int p = tid; p < AX * AY; p += NT) {
+      const int gx = x0 + p % AX - H, gy = y0 + p / AX - H;
+      const int nid = interior ? gy * g.pitch + gx : map_y(g, gy) * g.pitch + map_x(g, gx);
+      const C r = rho[nid];
+      sT[p] = Tin[nid];
+      sR[p] = r;
+      sL[p] = lam_of(ph, r);
+      sU[p] = ux[nid];
+      sV[p] = uy[nid];
+      sM[p] = mask[nid];
+    }
   }
   __syncthreads();
   // stage 1: T1 = T + L(T) on the tile and a 2-node halo, two nodes per thread; the frozen
@@ -1159,11 +1190,11 @@ __global__ void __launch_bounds__(EnergyTile<C>::NT, sizeof(C) == 4 ? (sizeof(S)
              const C* __restrict__ ux, const C* __restrict__ uy, const uint8_t* __restrict__ mask,
              double* partial, unsigned* counter, double* hf, int nb, int do_hf, int n_wall_tiles,
              const S* __restrict__ fnew, const C* __restrict__ side_new, C* __restrict__ psi_out, int* status,
-             C* __restrict__ t1_out) {
+             C* __restrict__ t1_out, const __grid_constant__ EnergyMaps maps, int staged) {
   energy_tile<C, EnergyTile<C>::TY, S, PSI, true>(g, ph, Tin, Tout, rho, ux, uy, mask, partial, counter, hf, nb,
                                                    do_hf, n_wall_tiles, blockIdx.x, blockIdx.y,
                                                    blockIdx.y * gridDim.x + blockIdx.x, gridDim.x * gridDim.y, fnew,
-                                                   side_new, psi_out, status, t1_out);
+                                                   side_new, psi_out, status, t1_out, staged ? &maps : nullptr);
 }
 
 // ---------------------------------------------------------------- batched passes
@@ -1393,10 +1424,16 @@ int step_impl(const Geo& g, const Phys& ph, const Dev& d, int cur, int tcur, int
     pre(kKEnergy);
     using ET = EnergyTile<C>;
     const dim3 blk(ET::NT), grd((g.nx + ET::TX - 1) / ET::TX, (g.ny + ET::TY - 1) / ET::TY);
+    constexpr int AX = ET::TX + 8, AY = ET::TY + 8;
+    EnergyMaps em;
+    const bool e_staged = d.tma && tma::encode<C>(&em.T, T, g.nx, g.ny, g.pitch, g.plane, 1, AX, AY) &&
+                          tma::encode<C>(&em.r, rho, g.nx, g.ny, g.pitch, g.plane, 1, AX, AY) &&
+                          tma::encode<C>(&em.u, ux, g.nx, g.ny, g.pitch, g.plane, 1, AX, AY) &&
+                          tma::encode<C>(&em.v, uy, g.nx, g.ny, g.pitch, g.plane, 1, AX, AY);
     k_energy<C, S, PSI><<<grd, blk, 0, s>>>(g, ph, T, Tn, rho, ux, uy, d.mask, d.partial, d.counter, d.hf, d.nb,
                                             do_hf, d.wall_tiles[ET::TY == 16 ? 1 : 0], fuse ? fn : nullptr,
                                             side_out, fuse ? static_cast<C*>(d.psi_next) : nullptr, d.status,
-                                            static_cast<C*>(d.t1_out));
+                                            static_cast<C*>(d.t1_out), em, e_staged ? 1 : 0);
     post(kKEnergy);
     *t_flipped = 1;
     if (chain) chain->made = fuse ? 1 : 0;
