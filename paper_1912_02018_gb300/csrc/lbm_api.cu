@@ -144,6 +144,7 @@ struct lbm_batch {
   int g_cur = -1, g_tcur = -1, g_variant = -1;
   int g_launches[2] = {0, 0};    // launches of the two captured steps
   std::vector<void*> psi_buf[2]; // per domain: psi of the state with population parity 0 / 1
+  std::vector<lbm::DomainMaps> hmaps;  // per domain: tensor maps for the current tile variant
   std::string err = "no error";
 };
 
@@ -873,6 +874,9 @@ static lbm_status batch_layout(lbm_batch* b) {
     D.en_ntx = ntx;
     D.en_nblocks = ntx * ((g.ny + ety - 1) / ety);
     me.insert(me.end(), (size_t)D.en_nblocks, (int)k);
+    // TMA maps for this variant's tiles (plain loads for the domain when one cannot be made)
+    if (b->f64) lbm::batch_maps_f64(D, b->hmaps[k], cty, ety);
+    else lbm::batch_maps_f32(D, b->hmaps[k], cty, ety);
   }
   b->nb_psi = (int)mp.size();
   b->nb_coll = (int)mc.size();
@@ -905,10 +909,13 @@ static bool batch_needs_psi(const lbm_batch* b) {
 static int batch_launch(lbm_batch* b, cudaStream_t s) {
   const int* m = b->d_maps;
   const int need_psi = batch_needs_psi(b) ? 1 : 0;
+  const int nd = (int)b->h_doms.size();
   return b->f64 ? lbm::batch_step_f64(b->variant, b->d_doms, m, b->nb_psi, m + b->max_tiles, b->nb_coll,
-                                      m + 2 * b->max_tiles, b->nb_en, b->cur, b->tcur, b->steps, need_psi, s)
+                                      m + 2 * b->max_tiles, b->nb_en, b->cur, b->tcur, b->steps, need_psi,
+                                      b->h_doms.data(), b->hmaps.data(), nd, s)
                 : lbm::batch_step_f32(b->variant, b->d_doms, m, b->nb_psi, m + b->max_tiles, b->nb_coll,
-                                      m + 2 * b->max_tiles, b->nb_en, b->cur, b->tcur, b->steps, need_psi, s);
+                                      m + 2 * b->max_tiles, b->nb_en, b->cur, b->tcur, b->steps, need_psi,
+                                      b->h_doms.data(), b->hmaps.data(), nd, s);
 }
 
 // After a batched step: the energy pass has made psi of the new state in buffer b->cur; each
@@ -971,6 +978,7 @@ lbm_status lbm_batch_create(int32_t n, const lbm_domain* domains, const lbm_cyli
     b->max_warmup = std::max<long long>(b->max_warmup, params[k].warmup_steps);
     b->max_tiles += ((domains[k].nx + 31) / 32) * ((domains[k].ny + 7) / 8);
   }
+  b->hmaps.resize(b->h_doms.size());
   cudaError_t e = cudaMalloc(&b->d_doms, sizeof(lbm::BatchDomain) * n);
   if (e == cudaSuccess) e = cudaMalloc(&b->d_maps, sizeof(int) * 3 * (size_t)b->max_tiles);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->gstream, cudaStreamNonBlocking);

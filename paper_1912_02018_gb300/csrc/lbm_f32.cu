@@ -52,13 +52,18 @@ int init_f32(const Geo& g, const Phys& ph, const Dev& d, const double* rho0, con
   }
 }
 
+bool batch_maps_f32(BatchDomain& D, DomainMaps& m, int cty, int ety) {
+  return kern::batch_maps_impl<float, float>(D, m, cty, ety);
+}
+
 int batch_step_f32(int variant, const BatchDomain* doms, const int* mp, int np, const int* mc, int nc,
-                   const int* me, int ne, int cur, int tcur, long long step, int need_psi, cudaStream_t s) {
+                   const int* me, int ne, int cur, int tcur, long long step, int need_psi,
+                   const BatchDomain* hd, const DomainMaps* hm, int nd, cudaStream_t s) {
   switch (variant) {
-    case 1: return kern::batch_step_impl<float, float, kPsiDF, 16, 16>(doms, mp, np, mc, nc, me, ne, cur, tcur, step, need_psi, s);
-    case 2: return kern::batch_step_impl<float, float, kPsiDF, 8, 8>(doms, mp, np, mc, nc, me, ne, cur, tcur, step, need_psi, s);
-    case 3: return kern::batch_step_impl<float, float, kPsiDF, 16, 8>(doms, mp, np, mc, nc, me, ne, cur, tcur, step, need_psi, s);
-    default: return kern::batch_step_impl<float, float, kPsiDF, 8, 16>(doms, mp, np, mc, nc, me, ne, cur, tcur, step, need_psi, s);
+    case 1: return kern::batch_step_impl<float, float, kPsiDF, 16, 16>(doms, mp, np, mc, nc, me, ne, cur, tcur, step, need_psi, hd, hm, nd, s);
+    case 2: return kern::batch_step_impl<float, float, kPsiDF, 8, 8>(doms, mp, np, mc, nc, me, ne, cur, tcur, step, need_psi, hd, hm, nd, s);
+    case 3: return kern::batch_step_impl<float, float, kPsiDF, 16, 8>(doms, mp, np, mc, nc, me, ne, cur, tcur, step, need_psi, hd, hm, nd, s);
+    default: return kern::batch_step_impl<float, float, kPsiDF, 8, 16>(doms, mp, np, mc, nc, me, ne, cur, tcur, step, need_psi, hd, hm, nd, s);
   }
 }
 

@@ -23,11 +23,16 @@ int init_f64(const Geo& g, const Phys& ph, const Dev& d, const double* rho0, con
   return init_impl<double, double>(g, ph, d, rho0, drho, ux0, uy0, T0, Tw, seed, amp, s);
 }
 
+bool batch_maps_f64(BatchDomain& D, DomainMaps& m, int cty, int ety) {
+  return kern::batch_maps_impl<double, double>(D, m, cty, ety);
+}
+
 int batch_step_f64(int variant, const BatchDomain* doms, const int* mp, int np, const int* mc, int nc,
-                   const int* me, int ne, int cur, int tcur, long long step, int need_psi, cudaStream_t s) {
+                   const int* me, int ne, int cur, int tcur, long long step, int need_psi,
+                   const BatchDomain* hd, const DomainMaps* hm, int nd, cudaStream_t s) {
   switch (variant & 1) {
-    case 1: return kern::batch_step_impl<double, double, kPsiF64, 16, 8>(doms, mp, np, mc, nc, me, ne, cur, tcur, step, need_psi, s);
-    default: return kern::batch_step_impl<double, double, kPsiF64, 8, 8>(doms, mp, np, mc, nc, me, ne, cur, tcur, step, need_psi, s);
+    case 1: return kern::batch_step_impl<double, double, kPsiF64, 16, 8>(doms, mp, np, mc, nc, me, ne, cur, tcur, step, need_psi, hd, hm, nd, s);
+    default: return kern::batch_step_impl<double, double, kPsiF64, 8, 8>(doms, mp, np, mc, nc, me, ne, cur, tcur, step, need_psi, hd, hm, nd, s);
   }
 }
 

@@ -2,8 +2,10 @@
 // (lbm_kernels.cuh, instantiated in lbm_f64.cu and lbm_f32.cu).
 #pragma once
 
-#include <cstdint>
+#include <cuda.h>
 #include <cuda_runtime.h>
+
+#include <cstdint>
 
 namespace lbm {
 
@@ -82,6 +84,12 @@ struct Dev {
 
 // One domain of a batch, as the batched kernels see it.  Tiles of every pass are numbered
 // consecutively over the domains; *_first is this domain's first tile of that pass.
+// Tensor maps of the energy pass's inputs (T, rho, u_x, u_y), each with the box of a tile and
+// its 4-node halo; interior tiles copy them into shared memory with TMA.
+struct EnergyMaps {
+  CUtensorMap T, r, u, v;
+};
+
 struct BatchDomain {
   Geo g;
   Phys ph;
@@ -91,7 +99,29 @@ struct BatchDomain {
   int psi_first, psi_ntx;                 // psi pass: 32 x 8 tiles
   int coll_first, coll_ntx;               // collision pass: 32 x CTY tiles
   int en_first, en_ntx, en_nblocks;       // energy pass: 32 x ETY tiles
+  int tma;                                // 1: the launch passes this domain's tensor maps
 };
+
+// Tensor maps of one batched domain for the current tile variant (kept on the host): the
+// populations and psi of population parity 0 / 1 for the collision pass, and the energy
+// inputs with T of parity 0 / 1.  A batched launch passes the current parity's maps of a
+// range of domains as kernel parameters (at most about 32 KB of them), hence the ranges below.
+struct DomainMaps {
+  CUtensorMap f[2], psi[2];
+  EnergyMaps em[2];
+};
+constexpr int kBatchCollDomains = 126, kBatchEnDomains = 63;
+struct CollLaunchMaps {
+  CUtensorMap f[kBatchCollDomains], psi[kBatchCollDomains];
+};
+struct EnLaunchMaps {
+  EnergyMaps e[kBatchEnDomains];
+};
+
+// Encode the tensor maps of one batched domain for tile heights (cty, ety); sets D.tma to
+// whether all of them could be made.
+bool batch_maps_f32(BatchDomain& D, DomainMaps& m, int cty, int ety);
+bool batch_maps_f64(BatchDomain& D, DomainMaps& m, int cty, int ety);
 
 // Tile-height variants of the batched step the autotuner chooses from: (CTY, ETY).
 constexpr int kBatchVariants = 4;
@@ -103,12 +133,13 @@ inline void batch_variant(int v, bool f64, int& cty, int& ety) {
 // Batched step over all domains (one launch per pass).  maps: block -> domain index for
 // the psi, collision and energy passes; need_psi: run the psi pass first (psi of the current
 // state is not known from the last energy pass).  Returns the number of launches or -1.
+// hdoms, hmaps, ndom: the host copies of the domains (their first tiles) and their tensor maps.
 int batch_step_f32(int variant, const BatchDomain* doms, const int* map_psi, int nb_psi, const int* map_coll,
                    int nb_coll, const int* map_en, int nb_en, int cur, int tcur, long long step, int need_psi,
-                   cudaStream_t s);
+                   const BatchDomain* hdoms, const DomainMaps* hmaps, int ndom, cudaStream_t s);
 int batch_step_f64(int variant, const BatchDomain* doms, const int* map_psi, int nb_psi, const int* map_coll,
                    int nb_coll, const int* map_en, int nb_en, int cur, int tcur, long long step, int need_psi,
-                   cudaStream_t s);
+                   const BatchDomain* hdoms, const DomainMaps* hmaps, int ndom, cudaStream_t s);
 
 // Kernel identifiers for per-launch timing.
 enum KernelId { kKRhoPsi = 0, kKCollide, kKEnergy, kKExport, kKImport, kNumKernels };

@@ -1060,12 +1060,6 @@ __device__ __forceinline__ void heat_flux_blocks(double q, int mine, double* par
   }
 }
 
-// Tensor maps of the energy pass's inputs (T, rho, u_x, u_y), each with the box of a tile and
-// its 4-node halo; interior tiles copy them into shared memory with TMA.
-struct EnergyMaps {
-  CUtensorMap T, r, u, v;
-};
-
 template <typename C, int TY_ = (sizeof(C) == 8 ? 8 : kEnergyTY)>
 struct EnergyTile {
   static constexpr int TX = kEnergyTX;
@@ -1217,23 +1211,31 @@ __global__ void __launch_bounds__(256) kb_rho_psi(const BatchDomain* __restrict_
                           D.d.mask, static_cast<const C*>(D.d.side[cur]), psi_buf<C>(D, cur), D.d.status,
                           local % D.psi_ntx, local / D.psi_ntx);
 }
+// A batched launch covers the blocks [block0, block0 + gridDim.x) of a pass, which belong to
+// the domains dom0 ..; their tensor maps come as kernel parameters (index k - dom0).
 template <typename C, typename S, int CTY>
-__global__ void __launch_bounds__(kCollTX* CTY, (sizeof(C) == 4 && CTY == 8) ? 7 : 1) kb_collide(const BatchDomain* __restrict__ doms,
-                                                          const int* __restrict__ map, int cur, long long step) {
-  const BatchDomain& D = doms[map[blockIdx.x]];
-  const int local = blockIdx.x - D.coll_first;
+__global__ void __launch_bounds__(kCollTX* CTY, (sizeof(C) == 4 && CTY == 8) ? 7 : 1)
+    kb_collide(const BatchDomain* __restrict__ doms, const int* __restrict__ map, int cur, long long step,
+               int block0, int dom0, const __grid_constant__ CollLaunchMaps maps) {
+  const int blk = block0 + blockIdx.x, k = map[blk];
+  const BatchDomain& D = doms[k];
+  const int local = blk - D.coll_first;
   collide_tile<C, S, CTY>(D.g, D.ph, static_cast<const S*>(D.d.f[cur]), static_cast<S*>(D.d.f[cur ^ 1]),
                           psi_buf<C>(D, cur), D.d.mask, static_cast<const C*>(D.d.side[cur]),
                           static_cast<C*>(D.d.side[cur ^ 1]), static_cast<C*>(D.d.rho), static_cast<C*>(D.d.ux),
                           static_cast<C*>(D.d.uy), step >= D.warmup, D.d.status, local % D.coll_ntx,
-                          local / D.coll_ntx);
+                          local / D.coll_ntx, D.tma ? &maps.f[k - dom0] : nullptr,
+                          D.tma ? &maps.psi[k - dom0] : nullptr);
 }
 template <typename C, int ETY, int PSI>
-__global__ void __launch_bounds__(EnergyTile<C, ETY>::NT) kb_energy(const BatchDomain* __restrict__ doms,
+// FP32: a register budget for 1280 threads per SM, as the single-domain energy pass
+__global__ void __launch_bounds__(EnergyTile<C, ETY>::NT, sizeof(C) == 4 ? 1280 / EnergyTile<C, ETY>::NT : 1) kb_energy(const BatchDomain* __restrict__ doms,
                                                                    const int* __restrict__ map, int cur, int tcur,
-                                                                   long long step) {
-  const BatchDomain& D = doms[map[blockIdx.x]];
-  const int local = blockIdx.x - D.en_first, bx = local % D.en_ntx, by = local / D.en_ntx;
+                                                                   long long step, int block0, int dom0,
+                                                                   const __grid_constant__ EnLaunchMaps maps) {
+  const int blk = block0 + blockIdx.x, k = map[blk];
+  const BatchDomain& D = doms[k];
+  const int local = blk - D.en_first, bx = local % D.en_ntx, by = local / D.en_ntx;
   const C* Tin = static_cast<const C*>(D.d.T[tcur]);
   C* Tout = static_cast<C*>(D.d.T[tcur ^ 1]);
   const C* fnew = static_cast<const C*>(D.d.f[cur ^ 1]);
@@ -1254,20 +1256,63 @@ __global__ void __launch_bounds__(EnergyTile<C, ETY>::NT) kb_energy(const BatchD
     }
     return;
   }
+  const EnergyMaps* em = D.tma ? &maps.e[k - dom0] : nullptr;
   energy_tile<C, ETY, C, PSI, true>(D.g, D.ph, Tin, Tout, static_cast<const C*>(D.d.rho),
                                     static_cast<const C*>(D.d.ux), static_cast<const C*>(D.d.uy), D.d.mask,
                                     D.d.partial, D.d.counter, D.d.hf, D.d.nb, D.d.nb > 0,
                                     D.d.wall_tiles[ETY == 16 ? 1 : 0], bx, by, local, D.en_nblocks, fnew, side_new,
-                                    psi_next, D.d.status);
+                                    psi_next, D.d.status, nullptr, em);
 }
 
 template <typename C, typename S, int PSI, int CTY, int ETY>
 int batch_step_impl(const BatchDomain* doms, const int* map_psi, int nb_psi, const int* map_coll, int nb_coll,
-                    const int* map_en, int nb_en, int cur, int tcur, long long step, int need_psi, cudaStream_t s) {
-  if (need_psi) kb_rho_psi<C, S, PSI><<<nb_psi, dim3(kCollTX, 8), 0, s>>>(doms, map_psi, cur, tcur);
-  kb_collide<C, S, CTY><<<nb_coll, dim3(kCollTX, CTY), 0, s>>>(doms, map_coll, cur, step);
-  kb_energy<C, ETY, PSI><<<nb_en, EnergyTile<C, ETY>::NT, 0, s>>>(doms, map_en, cur, tcur, step);
-  return cudaPeekAtLastError() == cudaSuccess ? (need_psi ? 3 : 2) : -1;
+                    const int* map_en, int nb_en, int cur, int tcur, long long step, int need_psi,
+                    const BatchDomain* hdoms, const DomainMaps* hmaps, int ndom, cudaStream_t s) {
+  int n = 0;
+  if (need_psi) {
+    kb_rho_psi<C, S, PSI><<<nb_psi, dim3(kCollTX, 8), 0, s>>>(doms, map_psi, cur, tcur);
+    ++n;
+  }
+  for (int d0 = 0; d0 < ndom; d0 += kBatchCollDomains) {
+    const int d1 = d0 + kBatchCollDomains < ndom ? d0 + kBatchCollDomains : ndom;
+    CollLaunchMaps m;
+    for (int k = d0; k < d1; ++k) {
+      m.f[k - d0] = hmaps[k].f[cur];
+      m.psi[k - d0] = hmaps[k].psi[cur];
+    }
+    const int b0 = hdoms[d0].coll_first, b1 = d1 < ndom ? hdoms[d1].coll_first : nb_coll;
+    kb_collide<C, S, CTY><<<b1 - b0, dim3(kCollTX, CTY), 0, s>>>(doms, map_coll, cur, step, b0, d0, m);
+    ++n;
+  }
+  for (int d0 = 0; d0 < ndom; d0 += kBatchEnDomains) {
+    const int d1 = d0 + kBatchEnDomains < ndom ? d0 + kBatchEnDomains : ndom;
+    EnLaunchMaps m;
+    for (int k = d0; k < d1; ++k) m.e[k - d0] = hmaps[k].em[tcur];
+    const int b0 = hdoms[d0].en_first, b1 = d1 < ndom ? hdoms[d1].en_first : nb_en;
+    kb_energy<C, ETY, PSI><<<b1 - b0, EnergyTile<C, ETY>::NT, 0, s>>>(doms, map_en, cur, tcur, step, b0, d0, m);
+    ++n;
+  }
+  return cudaPeekAtLastError() == cudaSuccess ? n : -1;
+}
+
+// Tensor maps of one batched domain for tile heights (cty, ety), as the single-domain step
+// encodes them per launch (here once per layout: the buffers of a domain do not move).
+template <typename C, typename S>
+bool batch_maps_impl(BatchDomain& D, DomainMaps& m, int cty, int ety) {
+  const Geo& g = D.g;
+  const int XA = 16 / (int)sizeof(S), PA = 16 / (int)sizeof(C) < 2 ? 2 : 16 / (int)sizeof(C);
+  bool ok = D.d.tma != 0;
+  for (int p = 0; p < 2 && ok; ++p) {
+    ok = tma::encode<S>(&m.f[p], D.d.f[p], g.nx, g.ny, g.pitch, g.plane, 9, kCollTX + 2 * XA, cty + 2) &&
+         tma::encode<C>(&m.psi[p], p ? D.d.psi_next : D.d.psi, g.nx, g.ny, g.pitch, g.plane, 1,
+                        kCollTX + 2 * PA, cty + 4) &&
+         tma::encode<C>(&m.em[p].T, D.d.T[p], g.nx, g.ny, g.pitch, g.plane, 1, kEnergyTX + 8, ety + 8) &&
+         tma::encode<C>(&m.em[p].r, D.d.rho, g.nx, g.ny, g.pitch, g.plane, 1, kEnergyTX + 8, ety + 8) &&
+         tma::encode<C>(&m.em[p].u, D.d.ux, g.nx, g.ny, g.pitch, g.plane, 1, kEnergyTX + 8, ety + 8) &&
+         tma::encode<C>(&m.em[p].v, D.d.uy, g.nx, g.ny, g.pitch, g.plane, 1, kEnergyTX + 8, ety + 8);
+  }
+  D.tma = ok ? 1 : 0;
+  return ok;
 }
 
 // ---------------------------------------------------------------- init / export / import
