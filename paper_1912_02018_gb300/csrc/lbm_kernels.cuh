@@ -2,17 +2,22 @@
 // templated on the compute type C (double or float) and population storage type S.
 //
 // Layout: structure of arrays, every field [ny][pitch] with x fastest; populations are
-// 9 such planes, ping-ponged between two buffers.  A step is three kernels:
-//   k_rho_psi pull f with boundary substitutions, rho, psi(rho, T); writes psi.
-//   k_collide pull f again, interaction force from a psi tile with a 2-node halo in
-//             shared memory, gravity, CM collision; writes f*, rho, u.
-//   k_energy  per 32x16 tile: T, rho, u, lambda(rho) on a 4-node halo in shared memory,
+// 9 such planes, ping-ponged between two buffers.  The kernels:
+//   k_rho_psi pull f with boundary substitutions, rho, psi(rho, T); writes psi.  Runs only
+//             when no energy pass made psi (first step, after a restore, warm-up).
+//   k_collide per 32x8 tile: the pull window of the 9 planes (1-node halo) and the psi tile
+//             (2-node halo) staged in shared memory by TMA (edge tiles: plain loads);
+//             interaction force, gravity, CM collision; writes f*, rho, u.
+//   k_energy  per 32x16 tile: T, rho, u staged by TMA with a 4-node halo, lambda(rho);
 //             Heun stage 1 on a 2-node halo, stage 2 on the tile, two nodes per thread;
-//             writes T^{n+1}; blocks
-//             holding wall nodes sum the wall heat flux in FP64 and the last block to
-//             finish adds the per-block partials in block order.
+//             writes T^{n+1} and, from the pull of the new populations, psi of the next
+//             step; blocks holding wall nodes sum the wall heat flux in FP64 and the last
+//             block to finish adds the per-block partials in block order.
+//   kb_*      the same passes over the tiles of many domains in one launch per pass.
 // The operation order inside each node follows the paper's equations term by term so
-// that the FP64 build (compiled without FMA contraction) rounds like a plain reference.
+// that the FP64 build (compiled without FMA contraction) rounds like a plain reference;
+// the FP32 build writes its roundings out (packed FP32x2 stencils, explicit fma) so that
+// every kernel that inlines the same code gives the same bits.
 #pragma once
 
 #include <cuda_fp16.h>
