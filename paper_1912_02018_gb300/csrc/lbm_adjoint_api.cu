@@ -78,9 +78,10 @@ lbm_status prepare(lbm_ctx* c, int K, int nseg) {
     w->sside.push_back(A(ss));
   }
   for (int j = 0; j < K; ++j) {
-    w->arho.push_back(A(plane));
-    w->aux.push_back(A(plane));
-    w->auy.push_back(A(plane));
+    char* ruv = static_cast<char*>(A(3 * plane));  // rho, u_x, u_y as consecutive planes (one TMA map)
+    w->arho.push_back(ruv);
+    w->aux.push_back(ruv ? ruv + plane : nullptr);
+    w->auy.push_back(ruv ? ruv + 2 * plane : nullptr);
     w->aT1.push_back(A(plane));
   }
   for (int j = 0; j <= K; ++j) w->apsi.push_back(A(plane));  // psi of slot K comes from the last energy pass

@@ -484,9 +484,10 @@ lbm_status lbm_create(const lbm_domain* domain, const lbm_cylinder* cyl, const l
   d.T[1] = dalloc(c, N * es);
   d.psi = dalloc(c, N * es);
   d.psi_next = dalloc(c, N * es);
-  d.rho = dalloc(c, N * es);
-  d.ux = dalloc(c, N * es);
-  d.uy = dalloc(c, N * es);
+  // rho, u_x, u_y as three consecutive planes: one 3D tensor map stages all three
+  d.rho = dalloc(c, 3 * N * es);
+  d.ux = d.rho ? static_cast<char*>(d.rho) + N * es : nullptr;
+  d.uy = d.rho ? static_cast<char*>(d.rho) + 2 * N * es : nullptr;
   d.side[0] = dalloc(c, 3 * (size_t)g.ny * es);
   d.side[1] = dalloc(c, 3 * (size_t)g.ny * es);
   d.partial = static_cast<double*>(dalloc(c, sizeof(double) * lbm::energy_blocks(g.nx, g.ny)));

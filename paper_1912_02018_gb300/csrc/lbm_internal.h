@@ -84,10 +84,11 @@ struct Dev {
 
 // One domain of a batch, as the batched kernels see it.  Tiles of every pass are numbered
 // consecutively over the domains; *_first is this domain's first tile of that pass.
-// Tensor maps of the energy pass's inputs (T, rho, u_x, u_y), each with the box of a tile and
-// its 4-node halo; interior tiles copy them into shared memory with TMA.
+// Tensor maps of the energy pass's inputs with the box of a tile and its 4-node halo: T, and
+// rho, u_x, u_y as three consecutive planes (one 3D box); interior tiles copy them into shared
+// memory with TMA.
 struct EnergyMaps {
-  CUtensorMap T, r, u, v;
+  CUtensorMap T, ruv;
 };
 
 struct BatchDomain {
@@ -110,7 +111,7 @@ struct DomainMaps {
   CUtensorMap f[2], psi[2];
   EnergyMaps em[2];
 };
-constexpr int kBatchCollDomains = 126, kBatchEnDomains = 63;
+constexpr int kBatchCollDomains = 126, kBatchEnDomains = 126;
 struct CollLaunchMaps {
   CUtensorMap f[kBatchCollDomains], psi[kBatchCollDomains];
 };

@@ -1092,9 +1092,10 @@ __device__ __forceinline__ void energy_tile(const Geo& g, const Phys& ph, const 
   static_assert(AX * AY * sizeof(C) % 128 == 0 && AX * sizeof(C) % 16 == 0, "TMA boxes of the input tile");
   __shared__ __align__(128) C sT[AY * AX];
   __shared__ __align__(128) C sL[AY * AX];
-  __shared__ __align__(128) C sU[AY * AX];
-  __shared__ __align__(128) C sV[AY * AX];
-  __shared__ __align__(128) C sR[AY * AX];
+  __shared__ __align__(128) C sRUV[3 * AY * AX];  // rho, u_x, u_y: the planes of one TMA box
+  C* const sR = sRUV;
+  C* const sU = sRUV + AY * AX;
+  C* const sV = sRUV + 2 * AY * AX;
   __shared__ uint64_t s_bar;
   __shared__ __align__(16) C sT1[BY * BX];
   __shared__ Frozen<C> sF[TX * TY];
@@ -1105,16 +1106,15 @@ __device__ __forceinline__ void energy_tile(const Geo& g, const Phys& ph, const 
   const int x0 = bx * TX, y0 = by * TY;
   const bool interior = x0 >= H && y0 >= H && x0 + TX + H <= g.nx && y0 + TY + H <= g.ny;
   if (maps && interior) {
-    // the four input boxes by TMA (first column x0 - 4: 16-byte aligned); the mask with plain
+    // the input boxes by TMA (T; rho, u_x, u_y in one 3-plane box; first column x0 - 4:
+    // 16-byte aligned); the mask with plain
     // loads while they fly; lambda(rho) once rho has landed
     if (tid == 0) tma::bar_init(&s_bar, 1);
     __syncthreads();
     if (tid == 0) {
       tma::bar_expect_tx(&s_bar, 4 * AX * AY * sizeof(C));
       tma::load_2d(sT, &maps->T, &s_bar, x0 - H, y0 - H);
-      tma::load_2d(sR, &maps->r, &s_bar, x0 - H, y0 - H);
-      tma::load_2d(sU, &maps->u, &s_bar, x0 - H, y0 - H);
-      tma::load_2d(sV, &maps->v, &s_bar, x0 - H, y0 - H);
+      tma::load_3d(sRUV, &maps->ruv, &s_bar, x0 - H, y0 - H, 0);
     }
     for (int p = tid; p < AX * AY; p += NT) sM[p] = mask[(y0 + p / AX - H) * g.pitch + x0 + p % AX - H];
     const bool landed = tma::bar_wait(&s_bar, 0, tma::kWaitTries);
@@ -1312,9 +1312,9 @@ bool batch_maps_impl(BatchDomain& D, DomainMaps& m, int cty, int ety) {
          tma::encode<C>(&m.psi[p], p ? D.d.psi_next : D.d.psi, g.nx, g.ny, g.pitch, g.plane, 1,
                         kCollTX + 2 * PA, cty + 4) &&
          tma::encode<C>(&m.em[p].T, D.d.T[p], g.nx, g.ny, g.pitch, g.plane, 1, kEnergyTX + 8, ety + 8) &&
-         tma::encode<C>(&m.em[p].r, D.d.rho, g.nx, g.ny, g.pitch, g.plane, 1, kEnergyTX + 8, ety + 8) &&
-         tma::encode<C>(&m.em[p].u, D.d.ux, g.nx, g.ny, g.pitch, g.plane, 1, kEnergyTX + 8, ety + 8) &&
-         tma::encode<C>(&m.em[p].v, D.d.uy, g.nx, g.ny, g.pitch, g.plane, 1, kEnergyTX + 8, ety + 8);
+         static_cast<const C*>(D.d.ux) == static_cast<const C*>(D.d.rho) + g.plane &&
+         static_cast<const C*>(D.d.uy) == static_cast<const C*>(D.d.rho) + 2 * (size_t)g.plane &&
+         tma::encode<C>(&m.em[p].ruv, D.d.rho, g.nx, g.ny, g.pitch, g.plane, 3, kEnergyTX + 8, ety + 8);
   }
   D.tma = ok ? 1 : 0;
   return ok;
@@ -1476,10 +1476,9 @@ int step_impl(const Geo& g, const Phys& ph, const Dev& d, int cur, int tcur, int
     const dim3 blk(ET::NT), grd((g.nx + ET::TX - 1) / ET::TX, (g.ny + ET::TY - 1) / ET::TY);
     constexpr int AX = ET::TX + 8, AY = ET::TY + 8;
     EnergyMaps em;
-    const bool e_staged = d.tma && tma::encode<C>(&em.T, T, g.nx, g.ny, g.pitch, g.plane, 1, AX, AY) &&
-                          tma::encode<C>(&em.r, rho, g.nx, g.ny, g.pitch, g.plane, 1, AX, AY) &&
-                          tma::encode<C>(&em.u, ux, g.nx, g.ny, g.pitch, g.plane, 1, AX, AY) &&
-                          tma::encode<C>(&em.v, uy, g.nx, g.ny, g.pitch, g.plane, 1, AX, AY);
+    const bool ruv = ux == rho + g.plane && uy == rho + 2 * (size_t)g.plane;  // consecutive planes
+    const bool e_staged = d.tma && ruv && tma::encode<C>(&em.T, T, g.nx, g.ny, g.pitch, g.plane, 1, AX, AY) &&
+                          tma::encode<C>(&em.ruv, rho, g.nx, g.ny, g.pitch, g.plane, 3, AX, AY);
     k_energy<C, S, PSI><<<grd, blk, 0, s>>>(g, ph, T, Tn, rho, ux, uy, d.mask, d.partial, d.counter, d.hf, d.nb,
                                             do_hf, d.wall_tiles[ET::TY == 16 ? 1 : 0], fuse ? fn : nullptr,
                                             side_out, fuse ? static_cast<C*>(d.psi_next) : nullptr, d.status,
