@@ -70,7 +70,10 @@ typedef enum { LBM_STORE_F64 = 0, LBM_STORE_F32 = 1, LBM_STORE_F16S = 2 } lbm_st
 typedef struct {
     int32_t nx, ny;     /* lattice size; nx, ny >= 5 */
     int32_t periodic_x; /* 0: Zou-He inlet at x=0, convective outlet at x=nx-1; 1: periodic in x */
-    int32_t reserved;
+    int32_t walls;      /* flat solid walls with halfway bounce-back (link fraction 1/2), their solid nodes at
+                           T_w: bit 0 the column x = 0 (replaces the inlet; needs periodic_x = 0), as the
+                           heated wall of the Stefan problem (Sec. III.E) turned to face +x; bit 1 the rows
+                           y = 0 and y = ny-1, the no-slip planes of the Poiseuille flow (Sec. III.C) */
 } lbm_domain;
 
 typedef struct {
@@ -107,6 +110,8 @@ typedef struct {
                              0 double-float (FP32 pairs, ~2^-44 relative), 1 IEEE FP64, 2 FP32 */
     uint64_t seed;        /* SplitMix64 stream for the default density perturbation */
     double noise_amp;     /* amplitude of that perturbation (uniform in +/- noise_amp) */
+    double body_fx;       /* uniform body force density along +x added to the force of Eq. (force), as the
+                             driving force F_x = 8 nu U_0 / L_y^2 of the Poiseuille flow (Sec. III.C); 0: none */
 } lbm_params;
 
 /* Optional initial fields (host, [ny][nx]); any pointer may be NULL.

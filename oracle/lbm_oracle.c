@@ -75,8 +75,11 @@ typedef struct {
     double rho_l, rho_v, rho_s; /* coexistence densities; virtual solid density */
     double nu_l, nu_v, alpha_l, alpha_v, c_v;
     double g, u_in, U_out;      /* gravity; inlet speed; convective-outlet speed */
-    int32_t n_wall, pad;        /* optional angular wall-superheat profile (knots, fractions of Tc) */
+    int32_t n_wall;             /* optional angular wall-superheat profile (knots, fractions of Tc) */
+    int32_t walls;              /* flat solid walls: bit 0 the column x = 0 (at T_wall, instead of the
+                                   inlet), bit 1 the rows y = 0 and y = ny - 1 */
     const double *wall_dT;
+    double body_fx;             /* uniform body force along +x (0: none) */
 } orc_params;
 
 typedef struct {
@@ -385,11 +388,19 @@ static double energy_rhs(const orc_t *o, const double *T, int x, int y)
 
 /* ---------- geometry ---------- */
 
-static int is_solid_xy(const orc_params *p, int x, int y)
+static int is_cylinder_xy(const orc_params *p, int x, int y)
 {
     if (!(p->D > 0.0)) return 0;
     double dx = x - p->xc, dy = y - p->yc, r = 0.5 * p->D;
     return dx * dx + dy * dy <= r * r;
+}
+
+/* Solid nodes: the cylinder, and the flat walls: the column x = 0 (the heated wall of the
+ * Stefan problem, Sec. III.E, turned so that its normal is +x) and the rows y = 0, ny - 1
+ * (the no-slip planes of the Poiseuille flow, Sec. III.C). */
+static int is_solid_xy(const orc_params *p, int x, int y)
+{
+    return ((p->walls & 1) && x == 0) || ((p->walls & 2) && (y == 0 || y == p->ny - 1)) || is_cylinder_xy(p, x, y);
 }
 
 /* Fraction q of the link from fluid node (x, y) along (cx, cy) that lies in the fluid:
@@ -434,7 +445,7 @@ orc_t *orc_create(const orc_params *p, const double *rho0, const double *ux0, co
     o->nb = 0;
     for (int y = 0; y < ny; ++y)
         for (int x = 0; x < nx; ++x) {
-            int id = y * nx + x, touches = 0;
+            int id = y * nx + x, touches = 0, touches_cyl = 0;
             for (int i = 0; i < Q; ++i) o->qlink[id * Q + i] = -1.0;
             if (o->solid[id]) continue;
             for (int i = 1; i < Q; ++i) {
@@ -442,15 +453,26 @@ orc_t *orc_create(const orc_params *p, const double *rho0, const double *ux0, co
                 if (p->periodic_x) sx = wrap(sx, nx);
                 if (sx < 0 || sx >= nx) continue;
                 if (o->solid[sy * nx + sx]) {
-                    o->qlink[id * Q + i] = link_fraction(p, x, y, -CX[i], -CY[i]);
+                    /* the flat wall's surface lies halfway between its column and the next */
+                    int cyl = is_cylinder_xy(p, sx, sy);
+                    o->qlink[id * Q + i] = cyl ? link_fraction(p, x, y, -CX[i], -CY[i]) : 0.5;
                     touches = 1;
+                    touches_cyl |= cyl;
                 }
             }
             if (touches) {
-                double dx = x - p->xc, dy = y - p->yc, r = sqrt(dx * dx + dy * dy);
+                /* outward normal: from the cylinder centre, else that of the flat wall */
+                double nxv = 1.0, nyv = 0.0;
+                if ((p->walls & 2) && y == 1) { nxv = 0.0; nyv = 1.0; }
+                if ((p->walls & 2) && y == ny - 2) { nxv = 0.0; nyv = -1.0; }
+                if (touches_cyl) {
+                    double dx = x - p->xc, dy = y - p->yc, r = sqrt(dx * dx + dy * dy);
+                    nxv = dx / r;
+                    nyv = dy / r;
+                }
                 o->bnode[o->nb] = id;
-                o->bnx[o->nb] = dx / r;
-                o->bny[o->nb] = dy / r;
+                o->bnx[o->nb] = nxv;
+                o->bny[o->nb] = nyv;
                 o->nb++;
             }
         }
@@ -462,7 +484,7 @@ orc_t *orc_create(const orc_params *p, const double *rho0, const double *ux0, co
             int id = y * nx + x;
             if (!o->solid[id]) continue;
             double tw = p->T_wall;
-            if (p->n_wall > 0 && p->wall_dT) {
+            if (p->n_wall > 0 && p->wall_dT && is_cylinder_xy(p, x, y)) {
                 double th = atan2(y - p->yc, x - p->xc);
                 double s = th / (2.0 * M_PI);
                 if (s < 0.0) s += 1.0;
@@ -630,6 +652,7 @@ void orc_step(orc_t *o, int64_t nsteps)
                 }
                 if (forcing) {
                     Fx = Fmx - (o->rho[id] - p->rho_l) * p->g;
+                    if (p->body_fx != 0.0) Fx = Fx + p->body_fx;
                     Fy = Fmy;
                 }
                 double f[Q], fst[Q], r, u, v;

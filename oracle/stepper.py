@@ -27,7 +27,8 @@ class OrcParams(C.Structure):
         ("nu_l", C.c_double), ("nu_v", C.c_double), ("alpha_l", C.c_double), ("alpha_v", C.c_double),
         ("c_v", C.c_double),
         ("g", C.c_double), ("u_in", C.c_double), ("U_out", C.c_double),
-        ("n_wall", C.c_int32), ("pad", C.c_int32), ("wall_dT", C.POINTER(C.c_double)),
+        ("n_wall", C.c_int32), ("walls", C.c_int32), ("wall_dT", C.POINTER(C.c_double)),
+        ("body_fx", C.c_double),
     ]
 
 
@@ -141,7 +142,8 @@ def derive(case) -> tuple[OrcParams, Derived]:
         G=case.G, sigma=case.sigma, T_sat=T_sat, T_wall=T_wall, rho_l=rho_l, rho_v=rho_v,
         rho_s=case.rho_s if case.rho_s > 0 else rho_l,
         nu_l=nu_l, nu_v=nu_v, alpha_l=alpha_l, alpha_v=alpha_v, c_v=case.c_v,
-        g=g, u_in=case.u_in, U_out=U_out)
+        g=g, u_in=case.u_in, U_out=U_out, walls=int(getattr(case, "walls", 0)),
+        body_fx=float(getattr(case, "body_fx", 0.0)))
     knots = np.ascontiguousarray(getattr(case, "wall_dT", ()) or (), dtype=np.float64)
     if knots.size:
         p.n_wall = knots.size

@@ -26,7 +26,7 @@ EXPORTS = ("lbm_create", "lbm_step", "lbm_sync", "lbm_wall_heat_flux", "lbm_rese
 
 
 class Domain(C.Structure):
-    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("periodic_x", C.c_int32), ("reserved", C.c_int32)]
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("periodic_x", C.c_int32), ("walls", C.c_int32)]
 
 
 class Cylinder(C.Structure):
@@ -42,7 +42,7 @@ class Params(C.Structure):
                 ("Pr_v", C.c_double), ("c_v", C.c_double), ("g", C.c_double), ("outlet_U", C.c_double),
                 ("warmup_steps", C.c_int64), ("energy", C.c_int32), ("storage", C.c_int32),
                 ("compute_f64", C.c_int32), ("psi_mode", C.c_int32), ("seed", C.c_uint64),
-                ("noise_amp", C.c_double)]
+                ("noise_amp", C.c_double), ("body_fx", C.c_double)]
 
 
 class Init(C.Structure):

@@ -262,6 +262,9 @@ lbm_status lbm_create(const lbm_domain* domain, const lbm_cylinder* cyl, const l
   if (!P.compute_f64 && P.storage != LBM_STORE_F32 && P.storage != LBM_STORE_F64 && P.storage != LBM_STORE_F16S)
     return fail(nullptr, LBM_EINVAL, "storage must be LBM_STORE_F64, LBM_STORE_F32 or LBM_STORE_F16S");
   if (P.psi_mode < 0 || P.psi_mode > 2) return fail(nullptr, LBM_EINVAL, "psi_mode must be 0, 1 or 2");
+  if (D.walls & ~3) return fail(nullptr, LBM_EINVAL, "walls takes bit 0 (x = 0) and bit 1 (y = 0, ny-1) only");
+  if ((D.walls & 1) && D.periodic_x) return fail(nullptr, LBM_EINVAL, "a wall at x = 0 needs periodic_x = 0");
+  if (!std::isfinite(P.body_fx)) return fail(nullptr, LBM_EINVAL, "body_fx must be finite");
   if (!(P.a > 0 && P.b > 0 && P.R > 0)) return fail(nullptr, LBM_EINVAL, "EOS constants a, b, R must be > 0");
   if (P.G > 0) return fail(nullptr, LBM_EINVAL, "G must be <= 0 (Eq. potential needs G < 0; 0 = single phase)");
   if (!(P.Tr_sat > 0 && P.Tr_sat < 1)) return fail(nullptr, LBM_EINVAL, "Tr_sat must lie in (0, 1)");
@@ -324,6 +327,7 @@ lbm_status lbm_create(const lbm_domain* domain, const lbm_cylinder* cyl, const l
   ph.alpha_v = ph.nu_v / P.Pr_v;
   ph.c_v = P.c_v;
   ph.g = P.g >= 0 ? P.g : (has_cyl ? P.u_in * P.u_in / (16.0 * cyl->D) : 0.0);
+  ph.body_fx = P.body_fx;
   ph.u_in = P.u_in;
   ph.U_out = P.outlet_U >= 0 ? P.outlet_U : P.u_in;
   c->lambda_v = rho_v * P.c_v * ph.alpha_v;
@@ -334,6 +338,7 @@ lbm_status lbm_create(const lbm_domain* domain, const lbm_cylinder* cyl, const l
     pf.rho_l = (float)ph.rho_l, pf.rho_v = (float)ph.rho_v, pf.rho_s = (float)ph.rho_s;
     pf.nu_l = (float)ph.nu_l, pf.nu_v = (float)ph.nu_v, pf.alpha_l = (float)ph.alpha_l, pf.alpha_v = (float)ph.alpha_v;
     pf.c_v = (float)ph.c_v, pf.g = (float)ph.g, pf.u_in = (float)ph.u_in, pf.U_out = (float)ph.U_out;
+    pf.body_fx = (float)ph.body_fx;
   }
   auto split = [](double v) {
     lbm::F2 r;
@@ -386,10 +391,14 @@ lbm_status lbm_create(const lbm_domain* domain, const lbm_cylinder* cyl, const l
   g.r = has_cyl ? 0.5 * cyl->D : -1.0;
   const long long plane = g.plane;
   std::vector<uint8_t> mask(plane, 0);
-  auto solid_at = [&](int x, int y) {
+  auto cyl_at = [&](int x, int y) {
     if (!has_cyl) return false;
     double dx = x - g.xc, dy = y - g.yc;
     return dx * dx + dy * dy <= g.r * g.r;
+  };
+  // the flat walls: the column x = 0 (bit 0) and the rows y = 0, ny - 1 (bit 1)
+  auto solid_at = [&](int x, int y) {
+    return ((D.walls & 1) && x == 0) || ((D.walls & 2) && (y == 0 || y == g.ny - 1)) || cyl_at(x, y);
   };
   for (int y = 0; y < g.ny; ++y)
     for (int x = 0; x < g.nx; ++x)
@@ -402,19 +411,30 @@ lbm_status lbm_create(const lbm_domain* domain, const lbm_cylinder* cyl, const l
     for (int x = 0; x < g.nx; ++x) {
       const long long id = (long long)y * g.pitch + x;
       if (mask[id] & lbm::kSolid) continue;
-      bool near = false;
-      for (int i = 1; i < 9 && !near; ++i) {
+      bool near = false, near_cyl = false;
+      for (int i = 1; i < 9; ++i) {
         int sx = x - CX[i], sy = (y - CY[i] + g.ny) % g.ny;
         if (g.periodic_x) sx = (sx + g.nx) % g.nx;
         if (sx < 0 || sx >= g.nx) continue;
-        near = (mask[(long long)sy * g.pitch + sx] & lbm::kSolid) != 0;
+        if (mask[(long long)sy * g.pitch + sx] & lbm::kSolid) {
+          near = true;
+          near_cyl = near_cyl || cyl_at(sx, sy);
+        }
       }
       if (near) {
+        // outward normal: from the cylinder centre, else that of the flat wall
         mask[id] |= lbm::kNearWall;
-        double dx = x - g.xc, dy = y - g.yc, rr = std::sqrt(dx * dx + dy * dy);
+        double nxv = 1.0, nyv = 0.0;
+        if ((D.walls & 2) && y == 1) nxv = 0.0, nyv = 1.0;
+        if ((D.walls & 2) && y == g.ny - 2) nxv = 0.0, nyv = -1.0;
+        if (near_cyl) {
+          double dx = x - g.xc, dy = y - g.yc, rr = std::sqrt(dx * dx + dy * dy);
+          nxv = dx / rr;
+          nyv = dy / rr;
+        }
         bnode.push_back((int)id);
-        bnx.push_back(dx / rr);
-        bny.push_back(dy / rr);
+        bnx.push_back(nxv);
+        bny.push_back(nyv);
       }
     }
 
@@ -430,7 +450,9 @@ lbm_status lbm_create(const lbm_domain* domain, const lbm_cylinder* cyl, const l
         int sx = x - CX[i], sy = (y - CY[i] + g.ny) % g.ny;
         if (g.periodic_x) sx = (sx + g.nx) % g.nx;
         double q = -1.0;
-        if (sx >= 0 && sx < g.nx && (mask[(long long)sy * g.pitch + sx] & lbm::kSolid)) {
+        if (sx >= 0 && sx < g.nx && (mask[(long long)sy * g.pitch + sx] & lbm::kSolid) && !cyl_at(sx, sy)) {
+          q = 0.5;  // a flat wall's surface lies halfway between its nodes and the fluid's
+        } else if (sx >= 0 && sx < g.nx && (mask[(long long)sy * g.pitch + sx] & lbm::kSolid)) {
           const int cx = -CX[i], cy = -CY[i];
           const double dx = x - g.xc, dy = y - g.yc, r = g.r;
           const double A = (double)(cx * cx + cy * cy);
@@ -562,7 +584,7 @@ lbm_status lbm_create(const lbm_domain* domain, const lbm_cylinder* cyl, const l
     const double two_pi = 2.0 * std::acos(-1.0);
     for (int y = 0; y < g.ny; ++y)
       for (int x = 0; x < g.nx; ++x) {
-        if (!solid_at(x, y)) continue;
+        if (!cyl_at(x, y)) continue;  // the profile is the cylinder's; flat walls stay at T_w
         double s = std::atan2(y - g.yc, x - g.xc) / two_pi;
         if (s < 0.0) s += 1.0;
         const double pos = s * cyl->n_wall, fl = std::floor(pos), t = pos - fl;

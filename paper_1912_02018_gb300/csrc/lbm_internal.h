@@ -41,6 +41,7 @@ struct PhysC {
   C rho_l, rho_v, rho_s;
   C nu_l, nu_v, alpha_l, alpha_v, c_v;
   C g, u_in, U_out;
+  C body_fx;  // uniform body force along +x (0: none)
 };
 
 // Physical constants, derived on the host in double and rounded once to float there, so

@@ -647,6 +647,7 @@ __device__ __forceinline__ void collide_node(const Geo& g, const Phys& ph, const
   }
   if (forcing) {
     Fx = sub(Fmx, mul(sub(rho, k.rho_l), k.g));
+    if (k.body_fx != C(0)) Fx = add(Fx, k.body_fx);
     Fy = Fmy;
   }
   const C omega = fdiv(C(1), add(fdiv(nu_of(ph, rho), cs2), C(0.5)));

@@ -204,7 +204,7 @@ extern "C" lbm_status lbm_wall_heat_flux_noalloc(const lbm_domain* dom, const lb
                                                  const lbm_params* P, const double* T, const double* rho,
                                                  double* q_out, void* cuda_stream) {
   if (!dom || !cyl || !P || !T || !rho || !q_out) return LBM_EINVAL;
-  if (dom->nx < 5 || dom->ny < 5 || !(cyl->D > 0)) return LBM_EINVAL;
+  if (dom->nx < 5 || dom->ny < 5 || !(cyl->D > 0) || dom->walls != 0) return LBM_EINVAL;  // the cylinder alone
   const int bx = (dom->nx + kTX - 1) / kTX, by = (dom->ny + kTY - 1) / kTY;
   if ((long long)bx * by > kMaxBlocks) return LBM_EINVAL;  // more than 8,388,608 nodes: beyond the scratch
   int dev = 0;

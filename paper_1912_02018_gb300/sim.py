@@ -14,16 +14,17 @@ from . import _native as N
 
 _PARAM_DEFAULTS = dict(a=2.0 / 49.0, b=2.0 / 21.0, R=1.0, acentric=0.344, G=-1.0, sigma=0.38, Tr_sat=0.86,
                        Re=30.0, u_in=0.05, nu_l=0.0, nu_ratio=1.0, Pr_l=0.862, Pr_v=1.5, c_v=11.0, g=-1.0,
-                       outlet_U=-1.0, warmup=0, energy=1, seed=0, noise_amp=1e-4, psi_mode=0, wall_dT=())
+                       outlet_U=-1.0, warmup=0, energy=1, seed=0, noise_amp=1e-4, psi_mode=0, wall_dT=(),
+                       body_fx=0.0)
 
 
-def _structs(nx, ny, D, xc, yc, periodic_x, superheat_Tc, rho_s, f64, storage, params):
+def _structs(nx, ny, D, xc, yc, periodic_x, superheat_Tc, rho_s, f64, storage, params, walls=0):
     kw = dict(_PARAM_DEFAULTS)
     unknown = set(params) - set(kw)
     if unknown:
         raise TypeError(f"unknown parameters {sorted(unknown)}")
     kw.update(params)
-    dom = N.Domain(int(nx), int(ny), int(periodic_x), 0)
+    dom = N.Domain(int(nx), int(ny), int(periodic_x), int(walls))
     cyl = N.Cylinder(float(xc), float(yc), float(D), float(superheat_Tc), float(rho_s))
     knots = np.ascontiguousarray(kw.pop("wall_dT", ()) or (), dtype=np.float64)
     if knots.size:
@@ -35,7 +36,8 @@ def _structs(nx, ny, D, xc, yc, periodic_x, superheat_Tc, rho_s, f64, storage, p
                    nu_ratio=kw["nu_ratio"], Pr_l=kw["Pr_l"], Pr_v=kw["Pr_v"], c_v=kw["c_v"], g=kw["g"],
                    outlet_U=kw["outlet_U"], warmup_steps=int(kw["warmup"]), energy=int(kw["energy"]),
                    storage=N.LBM_STORE_F64 if f64 else N.STORAGE[storage], compute_f64=1 if f64 else 0,
-                   psi_mode=int(kw["psi_mode"]), seed=int(kw["seed"]), noise_amp=kw["noise_amp"])
+                   psi_mode=int(kw["psi_mode"]), seed=int(kw["seed"]), noise_amp=kw["noise_amp"],
+                   body_fx=float(kw["body_fx"]))
     return dom, cyl, prm, kw
 
 
@@ -65,7 +67,8 @@ def _case_kwargs(case):
     if hasattr(case, "U_out"):
         params["outlet_U"] = case.U_out
     return dict(nx=case.nx, ny=case.ny, D=case.D, xc=case.xc, yc=case.yc, periodic_x=case.periodic_x,
-                superheat_Tc=case.superheat_Tc, rho_s=getattr(case, "rho_s", 0.0), params=params)
+                superheat_Tc=case.superheat_Tc, rho_s=getattr(case, "rho_s", 0.0), walls=getattr(case, "walls", 0),
+                params=params)
 
 
 def _dense(a, n):
@@ -91,13 +94,14 @@ class Sim:
     """
 
     def __init__(self, nx, ny, D=0.0, xc=0.0, yc=0.0, periodic_x=0, superheat_Tc=0.05, rho_s=0.0, f64=False,
-                 storage="f32", init=None, stream=None, torch_alloc=True, **params):
+                 storage="f32", init=None, stream=None, torch_alloc=True, walls=0, **params):
         import torch
 
         self._torch = torch
         L = N.lib()
         self.nx, self.ny, self.D = int(nx), int(ny), float(D)
-        dom, cyl, prm, self.params = _structs(nx, ny, D, xc, yc, periodic_x, superheat_Tc, rho_s, f64, storage, params)
+        dom, cyl, prm, self.params = _structs(nx, ny, D, xc, yc, periodic_x, superheat_Tc, rho_s, f64, storage, params,
+                                              walls)
         self._f64, self._storage = bool(f64), prm.storage
         n = self.nx * self.ny
         init = init or {}
@@ -120,7 +124,7 @@ class Sim:
         k = _case_kwargs(case)
         params = {p: v for p, v in k.pop("params").items() if p not in kw}
         return cls(k["nx"], k["ny"], D=k["D"], xc=k["xc"], yc=k["yc"], periodic_x=k["periodic_x"],
-                   superheat_Tc=k["superheat_Tc"], rho_s=k["rho_s"], f64=f64, **params, **kw)
+                   superheat_Tc=k["superheat_Tc"], rho_s=k["rho_s"], f64=f64, walls=k["walls"], **params, **kw)
 
     # ------------------------------------------------------------------ lifecycle
     @classmethod
@@ -304,7 +308,7 @@ class Batch:
         doms, cyls, prms = (N.Domain * n)(), (N.Cylinder * n)(), (N.Params * n)()
         for i, k in enumerate(kws):
             doms[i], cyls[i], prms[i], _ = _structs(k["nx"], k["ny"], k["D"], k["xc"], k["yc"], k["periodic_x"],
-                                                    k["superheat_Tc"], k["rho_s"], f64, "f32", k["params"])
+                                                    k["superheat_Tc"], k["rho_s"], f64, "f32", k["params"], k["walls"])
         self.shapes = [(k["nx"], k["ny"], k["D"]) for k in kws]
         self._f64 = bool(f64)
         self.device = torch.cuda.current_device()

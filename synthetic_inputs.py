@@ -57,6 +57,8 @@ class Case:
     xc: float
     yc: float
     periodic_x: int = 0
+    walls: int = 0  # flat walls: bit 0 the column x = 0 (heated, instead of the inlet), bit 1 the rows y = 0, ny-1
+    body_fx: float = 0.0  # uniform body force along +x
     a: float = 2.0 / 49.0
     b: float = 2.0 / 21.0
     R: float = 1.0
@@ -123,3 +125,19 @@ def batch_sweep(n: int = 64, seed: int = 1) -> list[Case]:
         out.append(Case(nx=12 * D, ny=6 * D, D=float(D), xc=3.0 * D, yc=3.0 * D, Re=300.0,
                         superheat_Tc=float(sh[k]), seed=seed + k, name=f"sweep{k}_D{D}"))
     return out
+
+
+def poiseuille_case(L: int, U0: float = 0.01, nu: float = 1.0 / 6.0, nx: int = 8) -> Case:
+    """Poiseuille flow (Sec. III.C): a single-phase channel of width L between the no-slip planes
+    (flat walls on the rows y = 0 and y = L + 1, halfway bounce-back: surfaces at y = 1/2 and
+    L + 1/2), periodic in x, driven by the uniform force F_x = 8 nu U0 / L^2 (rho_0 = 1), whose
+    steady profile is u_x = 4 U0 y' (L - y') / L^2 with y' the distance from the lower surface."""
+    return Case(nx=nx, ny=L + 2, D=0.0, xc=0.0, yc=0.0, periodic_x=1, walls=2, G=0.0, energy=0, u_in=0.0,
+                nu_l=nu, nu_ratio=1.0, g=0.0, body_fx=8.0 * nu * U0 / (L * L), noise_amp=0.0,
+                name=f"poiseuille_L{L}")
+
+
+def poiseuille_profile(L: int, U0: float = 0.01) -> np.ndarray:
+    """The closed-form steady u_x at the fluid rows y = 1 .. L of poiseuille_case(L)."""
+    yp = np.arange(1, L + 1) - 0.5
+    return 4.0 * U0 * yp * (L - yp) / (L * L)

@@ -39,7 +39,7 @@ def test_library_exports_every_declared_symbol(lib):
 def test_struct_sizes_match_header_layout():
     assert C.sizeof(N.Domain) == 16
     assert C.sizeof(N.Cylinder) == 56
-    assert C.sizeof(N.Params) == 16 * 8 + 8 + 16 + 16
+    assert C.sizeof(N.Params) == 16 * 8 + 8 + 16 + 16 + 8
     assert C.sizeof(N.Init) == 40
     assert C.sizeof(N.Info) == 14 * 8 + 4 * 8
     assert C.sizeof(N.WindowGrad) == 3 * 8 + 2 * 8
@@ -67,7 +67,8 @@ def _good():
     return dom, cyl, prm
 
 
-@pytest.mark.parametrize("what", ["small", "storage", "G", "Tr", "cyl_inlet", "cyl_wide", "nu", "psi_mode"])
+@pytest.mark.parametrize("what", ["small", "storage", "G", "Tr", "cyl_inlet", "cyl_wide", "nu", "psi_mode",
+                                  "walls_bits", "wall_periodic"])
 def test_invalid_parameters_are_rejected_on_the_host(lib, what):
     dom, cyl, prm = _good()
     if what == "small":
@@ -84,6 +85,10 @@ def test_invalid_parameters_are_rejected_on_the_host(lib, what):
         cyl.D = 62.0
     elif what == "psi_mode":
         prm.psi_mode = 3
+    elif what == "walls_bits":
+        dom.walls = 4
+    elif what == "wall_periodic":
+        dom.walls, dom.periodic_x = 1, 1  # a wall at x = 0 replaces the inlet of a non-periodic domain
     elif what == "nu":
         prm.Re = 0.0  # nu_l = 0 and no Reynolds number: no valid relaxation rate
     st, h = _create(lib, dom, cyl, prm)

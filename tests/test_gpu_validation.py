@@ -1,0 +1,114 @@
+"""Flat walls and the body force on the CUDA path: against the oracle, and the Poiseuille flow
+against its closed form (Sec. III.C).
+
+The channel (walls on the rows y = 0, ny - 1, periodic in x, uniform force) and the heated
+flat wall at x = 0 with a vapour film in front of it (the Stefan geometry of Sec. III.E) run
+on the GPU and on the oracle from the same state; the FP64 build must agree to 1e-12, the
+FP32 build to its parity bar, and the GPU's steady channel profile must converge to the
+closed form at second order.
+"""
+import numpy as np
+import pytest
+
+import synthetic_inputs as si
+from oracle import Oracle
+from oracle.thermo import PR
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+
+    from oracle import build as ob
+    from paper_1912_02018_gb300 import build
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    build()
+    ob.build()
+    torch.cuda.set_device(0)
+
+
+def _pair(case, init, steps, f64):
+    from paper_1912_02018_gb300 import Sim
+
+    sim = Sim.from_case(case, f64=f64, init={k: v.reshape(-1) for k, v in init.items()}).step(steps)
+    ref = Oracle(case, **init).step(steps)
+    return sim.fields(("rho", "ux", "uy", "T", "psi")), ref
+
+
+def _rel(got, ref, fluid, speed=None):
+    den = speed if speed is not None else np.abs(ref[fluid]).max()
+    return np.abs(got[fluid] - ref[fluid]).max() / (den if den > 0 else 1.0)
+
+
+def _channel_init(case):
+    rho = np.ones((case.ny, case.nx))
+    return {"rho": rho, "ux": np.zeros_like(rho), "uy": np.zeros_like(rho)}
+
+
+def _stefan_case_and_init():
+    # a vapour film on the heated wall at x = 0 (wall density rho_v: vapour-wetting), liquid
+    # beyond a tanh interface at x = 5, u = 0, T = T_sat in the fluid
+    eos = PR(3.0 / 49.0, 2.0 / 21.0, 1.0, 0.344)
+    rv, rl, _ = eos.maxwell(0.86 * eos.Tc)
+    case = si.Case(nx=64, ny=5, D=0.0, xc=0.0, yc=0.0, walls=1, a=3.0 / 49.0, Tr_sat=0.86,
+                   superheat_Tc=0.010 / eos.Tc, u_in=0.0, nu_l=0.15, nu_ratio=1.0, Pr_v=1.5, U_out=0.05,
+                   rho_s=rv, g=0.0, noise_amp=0.0, name="stefan_geometry_64x5")
+    x = np.arange(case.nx)
+    rho = np.tile(rv + (rl - rv) * 0.5 * (1.0 + np.tanh((x - 5.0) / 2.0)), (case.ny, 1))
+    return case, {"rho": rho, "ux": np.zeros_like(rho), "uy": np.zeros_like(rho)}
+
+
+# FP32 velocity of this low-Mach channel (peak 0.01) is a difference of populations ~0.1, so its
+# rounding relative to the peak speed is ~100x that of rho: the FP32 bar for u is 5e-4
+@pytest.mark.parametrize("f64,steps,tol,utol", [(True, 2000, 1e-12, 1e-12), (False, 2000, 1e-5, 5e-4)])
+def test_channel_matches_oracle(f64, steps, tol, utol):
+    case = si.poiseuille_case(16)
+    got, ref = _pair(case, _channel_init(case), steps, f64)
+    fluid = ref.field("solid") == 0
+    speed = np.hypot(ref.field("ux"), ref.field("uy"))[fluid].max()
+    assert _rel(got["ux"], ref.field("ux"), fluid, speed) < utol
+    assert _rel(got["uy"], ref.field("uy"), fluid, speed) < utol
+    assert _rel(got["rho"], ref.field("rho"), fluid) < tol
+
+
+# The film's interface (density ratio 17 over ~4 nodes) sits next to the wall, where FP32
+# rounding of the pull and of psi weighs more than around the cylinder: FP32 bar 5e-5.  Its
+# velocities (parasitic currents, ~4e-4 at most) are compared in absolute lattice units
+# (c_s = 0.577): FP32 rounding of liquid populations ~1 accumulates to ~2e-6 in 200 steps.
+@pytest.mark.parametrize("f64,steps,tol,uabs", [(True, 300, 1e-12, 1e-13), (False, 200, 5e-5, 5e-6)])
+def test_heated_flat_wall_with_vapour_film_matches_oracle(f64, steps, tol, uabs):
+    case, init = _stefan_case_and_init()
+    got, ref = _pair(case, init, steps, f64)
+    fluid = ref.field("solid") == 0
+    for k in ("rho", "T", "psi"):
+        assert _rel(got[k], ref.field(k), fluid) < tol, k
+    for k in ("ux", "uy"):
+        assert np.abs(got[k][fluid] - ref.field(k)[fluid]).max() < uabs, k
+
+
+def _channel_error(L, f64):
+    from paper_1912_02018_gb300 import Sim
+
+    case = si.poiseuille_case(L)
+    init = {k: v.reshape(-1) for k, v in _channel_init(case).items()}
+    sim = Sim.from_case(case, f64=f64, init=init).step(int(8 * L * L * 6))  # eight diffusion times
+    u = sim.fields(("ux",))["ux"][1:case.ny - 1].mean(axis=1)
+    ref = si.poiseuille_profile(L)
+    return np.linalg.norm(u - ref) / np.linalg.norm(ref)
+
+
+def test_gpu_channel_converges_to_the_closed_form_at_second_order():
+    # the FP64 build: a convergence study needs the discretisation error above the rounding
+    errs = [_channel_error(L, True) for L in (16, 32)]
+    order = np.log2(errs[0] / errs[1])
+    assert errs[1] < 6e-4 and 1.95 < order < 2.05, (errs, order)
+
+
+def test_gpu_fp32_channel_within_the_discretisation_error():
+    # FP32 rounding shifts the steady profile by a few 1e-4 of the peak (the force is ~1e-5 per
+    # step), below the L = 16 discretisation error the oracle pins (1.8e-3)
+    assert _channel_error(16, False) < 2.5e-3
