@@ -10,7 +10,7 @@ stages of the temperature equation).  Default workload: the paper-shaped single 
              write) before every timed step; CUDA events on the library's stream.
   e2e        the same metric through the C ABI with host buffers: each step restores the
              state from pinned host memory (lbm_set_state_native, the context's own formats),
-             steps once and reads T back (lbm_fields, doubles) plus the heat flux.
+             steps once and reads T back in its own format (lbm_get_state_native) plus the heat flux.
   roofline   the dominant kernel's algorithmic bytes per launch / its mean event-timed
              duration, against the measured HBM copy bandwidth.
   adjoint    cost of the checkpointed adjoint window (512 x 256, D = 32, 500 steps,
@@ -327,11 +327,11 @@ def run_ours(args):
     value = aggregate_mlups(nodes, args.steps, world, ms / 1e3)
 
     # end to end through the C ABI with pinned host buffers: the state in the context's own
-    # formats (lbm_set_state_native), T read back as doubles (lbm_fields)
+    # formats (lbm_set_state_native), the new T read back in its own format too
     f0, T0, side0, n0 = sim.get_state_native()
     f_h = torch.from_numpy(f0).pin_memory()
     T_h = torch.from_numpy(T0).pin_memory()
-    out_h = torch.empty((case.ny, case.nx), dtype=torch.float64).pin_memory()
+    out_h = torch.empty_like(T_h).pin_memory()
     import ctypes as C
 
     from paper_1912_02018_gb300 import _native as N
@@ -345,13 +345,13 @@ def run_ours(args):
     for _ in range(e2e_steps):
         N.check(L.lbm_set_state_native(sim.h, f_h.data_ptr(), T_h.data_ptr(), None, -1), sim.h)
         N.check(L.lbm_step(sim.h, 1), sim.h)
-        N.check(L.lbm_fields(sim.h, N.FIELD_BITS["T"], out_h.data_ptr(), out_h.numel() * 8, 0), sim.h)
+        N.check(L.lbm_get_state_native(sim.h, None, out_h.data_ptr(), None, None), sim.h)
         sim.heat_flux()
     e2e_s = time.perf_counter() - t
     e2e_s = max_over_ranks(e2e_s, world)
     e2e = {"value": aggregate_mlups(nodes, e2e_steps, world, e2e_s), "unit": UNIT,
            "h2d_bytes_per_step": int(f_h.numel() * f_h.element_size() + T_h.numel() * T_h.element_size()),
-           "d2h_bytes_per_step": int(out_h.numel() * 8 + 5 * 8), "steps": e2e_steps}
+           "d2h_bytes_per_step": int(out_h.numel() * out_h.element_size() + 5 * 8), "steps": e2e_steps}
 
     if rank != 0:
         if world > 1:
