@@ -1078,6 +1078,8 @@ struct EnergyTile {
 // With FUSE, and psi_out set, the tile also evaluates psi of the next step at its nodes: the
 // pull of the populations this step's collision wrote (fnew, side_new), rho their sum (rho_s
 // in the solid), T the new temperature (Eq. potential) -- the next step then needs no psi pass.
+// maps: tensor maps of the inputs, with which an interior tile stages them by TMA (else null:
+// plain loads); t1_out: where to store the stage-1 temperature (the adjoint's recompute).
 template <typename C, int ETY, typename S = C, int PSI = kPsiF64, bool FUSE = false>
 __device__ __forceinline__ void energy_tile(const Geo& g, const Phys& ph, const C* __restrict__ Tin,
                                             C* __restrict__ Tout, const C* __restrict__ rho, const C* __restrict__ ux,
