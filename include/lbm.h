@@ -135,6 +135,7 @@ typedef struct {
 typedef struct {
     double Tc, pc, T_sat, T_wall;
     double rho_l, rho_v, p_sat;  /* Maxwell equal-area coexistence at T_sat */
+    double h_fg;                 /* latent heat T_sat (1/rho_v - 1/rho_l) dp_sat/dT (Clausius-Clapeyron; Sec. IV.A) */
     double nu_l, nu_v, alpha_l, alpha_v, lambda_v, g, outlet_U;
     int64_t steps;               /* steps taken so far */
     int64_t n_boundary;          /* fluid nodes with a D2Q9 link into the cylinder */

@@ -64,7 +64,7 @@ class Allocator(C.Structure):
 
 
 class Info(C.Structure):
-    _fields_ = [(n, C.c_double) for n in ("Tc", "pc", "T_sat", "T_wall", "rho_l", "rho_v", "p_sat", "nu_l",
+    _fields_ = [(n, C.c_double) for n in ("Tc", "pc", "T_sat", "T_wall", "rho_l", "rho_v", "p_sat", "h_fg", "nu_l",
                                           "nu_v", "alpha_l", "alpha_v", "lambda_v", "g", "outlet_U")] + [
         ("steps", C.c_int64), ("n_boundary", C.c_int64), ("kernel_launches", C.c_int64),
         ("device_bytes", C.c_int64)]

@@ -307,6 +307,15 @@ lbm_status lbm_create(const lbm_domain* domain, const lbm_cylinder* cyl, const l
     return fail(nullptr, LBM_EINVAL, "no liquid-vapour coexistence at T_sat = %g", T_sat);
   }
   c->p_sat = p_s;
+  {
+    // latent heat from the EOS (Sec. IV.A), read as Clausius-Clapeyron: h_fg = T (1/rho_v - 1/rho_l)
+    // dp_sat/dT, the slope of the coexistence pressure by a central difference (steps of 1e-5 T)
+    double rv, rl, pp, pm;
+    const double dT = 1e-5 * T_sat;
+    c->h_fg = (eos.maxwell(T_sat + dT, rv, rl, pp) && eos.maxwell(T_sat - dT, rv, rl, pm))
+                  ? T_sat * (1.0 / rho_v - 1.0 / rho_l) * (pp - pm) / (2.0 * dT)
+                  : 0.0;
+  }
   lbm::Phys& phys = c->ph;
   lbm::PhysC<double>& ph = phys.d;
   ph.a = P.a;
@@ -800,6 +809,7 @@ lbm_status lbm_info(lbm_ctx* c, lbm_info_t* info) {
   info->rho_l = c->ph.d.rho_l;
   info->rho_v = c->ph.d.rho_v;
   info->p_sat = c->p_sat;
+  info->h_fg = c->h_fg;
   info->nu_l = c->ph.d.nu_l;
   info->nu_v = c->ph.d.nu_v;
   info->alpha_l = c->ph.d.alpha_l;

@@ -29,7 +29,7 @@ struct lbm_ctx {
   int64_t steps = 0;
   int64_t launches = 0;
   bool f64 = false;
-  double Tc = 0, pc = 0, p_sat = 0, lambda_v = 0;
+  double Tc = 0, pc = 0, p_sat = 0, h_fg = 0, lambda_v = 0;
   std::vector<void*> blocks;
   size_t bytes = 0;
   std::string err = "no error";

@@ -41,7 +41,7 @@ def test_struct_sizes_match_header_layout():
     assert C.sizeof(N.Cylinder) == 56
     assert C.sizeof(N.Params) == 16 * 8 + 8 + 16 + 16 + 8
     assert C.sizeof(N.Init) == 40
-    assert C.sizeof(N.Info) == 14 * 8 + 4 * 8
+    assert C.sizeof(N.Info) == 15 * 8 + 4 * 8
     assert C.sizeof(N.WindowGrad) == 3 * 8 + 2 * 8
 
 

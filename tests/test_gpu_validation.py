@@ -112,3 +112,27 @@ def test_gpu_fp32_channel_within_the_discretisation_error():
     # FP32 rounding shifts the steady profile by a few 1e-4 of the peak (the force is ~1e-5 per
     # step), below the L = 16 discretisation error the oracle pins (1.8e-3)
     assert _channel_error(16, False) < 2.5e-3
+
+
+def test_latent_heat_of_the_paper_eos():
+    # Sec. IV.A: a = 3/49, b = 2/21 give h_fg = 0.572 (Clausius-Clapeyron); the library's value
+    # equals the oracle's thermodynamics
+    from oracle.thermo import PR
+    from paper_1912_02018_gb300 import Sim
+
+    sim = Sim.from_case(si.SMALL.replace(a=3.0 / 49.0), f64=True)
+    h = sim.info()["h_fg"]
+    eos = PR(3.0 / 49.0, 2.0 / 21.0, 1.0, 0.344)
+    assert abs(h - 0.572) < 5e-4
+    assert abs(h - eos.h_fg(0.86 * eos.Tc)) < 1e-7 * h
+
+
+def test_boiling_curve_driver_runs_the_paper_domain():
+    from paper_1912_02018_gb300 import boiling_curve as bc
+
+    out = bc.run(30.0, [0.010, 0.020], steps=4000, warmup=3000)
+    assert out["domain"] == [1350, 600] and len(out["points"]) == 2
+    for p in out["points"]:
+        assert p["status"] == "ok", p["status"]
+        assert p["samples"] == 500 and np.isfinite(p["q_mean"]) and p["q_mean"] > 0 and p["Nu"] > 0
+        assert all(np.isfinite(v) and v > 0 for v in p["correlations"].values())
