@@ -107,3 +107,12 @@ def collide_direct(f, Fx, Fy, Fmx, Fmy, psi, omega, sigma):
         extra[8] = 4.0 / 3.0 * alpha * Fm2
         out = out + Ti @ ((I - K / 2) @ extra)
     return out, rho, ux, uy
+
+
+def collide_bgk_direct(f, Fx, Fy, omega):
+    """The comparison operator of Sec. III.B: single-rate BGK on the same fourth-order Hermite
+    equilibrium and forcing, in population space, f* = f + omega (f^eq - f) + (1 - omega/2) F_i."""
+    f = np.asarray(f, dtype=np.float64)
+    rho, ux, uy = velocity(f, Fx, Fy)
+    out = f + omega * (feq(rho, ux, uy) - f) + (1.0 - omega / 2.0) * huang_force(Fx, Fy, ux, uy)
+    return out, rho, ux, uy

@@ -80,6 +80,9 @@ typedef struct {
                                    inlet), bit 1 the rows y = 0 and y = ny - 1 */
     const double *wall_dT;
     double body_fx;             /* uniform body force along +x (0: none) */
+    int32_t collision;          /* 0: CM collision (Sec. II.A); 1: single-rate BGK on the same equilibrium
+                                   and forcing, the comparison operator of Sec. III.B */
+    int32_t reserved;
 } orc_params;
 
 typedef struct {
@@ -269,10 +272,14 @@ int orc_invert9(const double A[Q * Q], double Ainv[Q * Q])
  *   Fmx,Fmy: interaction force F_m alone (enters the consistency terms)
  *   psi    : pseudopotential at the node (used only when sigma != 0)
  *   omega  : relaxation rate of k_4, k_5
+ *   bgk    : 0 for the CM collision, K = diag(1, 1, 1, 1, omega, omega, 1, 1, 1); 1 for the
+ *            single-rate BGK operator of the Sec. III.B comparison, K = omega I on the same
+ *            equilibrium and forcing central moments (in population space f* = f + omega (f^eq - f)
+ *            + (1 - omega/2) F_i, as T(u) is linear); the consistency terms are CM-only
  * Outputs f* (post-collision), rho and u (rho u = sum f c + F/2).
  */
 void orc_collide_node(const double f[Q], double Fx, double Fy, double Fmx, double Fmy, double psi,
-                      double omega, double sigma, const double Minv[Q * Q], double fstar[Q],
+                      double omega, double sigma, int bgk, const double Minv[Q * Q], double fstar[Q],
                       double *rho_out, double *ux_out, double *uy_out)
 {
     double M[Q * Q], N[Q * Q];
@@ -295,10 +302,12 @@ void orc_collide_node(const double f[Q], double Fx, double Fy, double Fmx, doubl
     }
     /* equilibrium CMs (Sec. II.A) and forcing CMs with the consistency terms, Eq. (force2) */
     double keq[Q] = {rho, 0.0, 0.0, 2.0 * rho / 3.0, 0.0, 0.0, 0.0, 0.0, rho / 9.0};
-    double alpha = sigma != 0.0 ? sigma / (psi * psi) : 0.0;
+    double alpha = (sigma != 0.0 && !bgk) ? sigma / (psi * psi) : 0.0;
     double Fm2 = Fmx * Fmx + Fmy * Fmy;
     double Rp[Q] = {0.0, Fx, Fy, 4.0 * alpha * Fm2, 0.0, 0.0, Fy / 3.0, Fx / 3.0, 4.0 / 3.0 * alpha * Fm2};
     double K[Q] = {1.0, 1.0, 1.0, 1.0, omega, omega, 1.0, 1.0, 1.0};
+    if (bgk)
+        for (int j = 0; j < Q; ++j) K[j] = omega;
     double ks[Q];
     for (int j = 0; j < Q; ++j)
         ks[j] = (1.0 - K[j]) * k[j] + K[j] * keq[j] + (1.0 - K[j] / 2.0) * Rp[j];
@@ -659,7 +668,7 @@ void orc_step(orc_t *o, int64_t nsteps)
                 for (int i = 0; i < Q; ++i) f[i] = o->fp[i * N + id];
                 double omega = 1.0 / (orc_nu(p, o->rho[id]) / cs2 + 0.5);
                 double sig = (forcing && p->G != 0.0) ? p->sigma : 0.0;
-                orc_collide_node(f, Fx, Fy, Fmx, Fmy, o->psi[id], omega, sig, o->Minv, fst, &r, &u, &v);
+                orc_collide_node(f, Fx, Fy, Fmx, Fmy, o->psi[id], omega, sig, p->collision, o->Minv, fst, &r, &u, &v);
                 for (int i = 0; i < Q; ++i) o->fs[i * N + id] = fst[i];
                 o->ux[id] = u;
                 o->uy[id] = v;

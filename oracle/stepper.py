@@ -29,6 +29,7 @@ class OrcParams(C.Structure):
         ("g", C.c_double), ("u_in", C.c_double), ("U_out", C.c_double),
         ("n_wall", C.c_int32), ("walls", C.c_int32), ("wall_dT", C.POINTER(C.c_double)),
         ("body_fx", C.c_double),
+        ("collision", C.c_int32), ("reserved", C.c_int32),
     ]
 
 
@@ -72,7 +73,7 @@ def load():
         lib.orc_invert9.restype = C.c_int
         lib.orc_invert9.argtypes = [dp, dp]
         lib.orc_collide_node.argtypes = [dp, C.c_double, C.c_double, C.c_double, C.c_double, C.c_double,
-                                         C.c_double, C.c_double, dp, dp, dp, dp, dp]
+                                         C.c_double, C.c_double, C.c_int, dp, dp, dp, dp, dp]
         lib.orc_energy_rhs_fields.argtypes = [P, dp, dp, dp, dp, dp]
         lib.orc_interaction_force.argtypes = [P, dp, dp, dp]
         _LIB = lib
@@ -143,7 +144,7 @@ def derive(case) -> tuple[OrcParams, Derived]:
         rho_s=case.rho_s if case.rho_s > 0 else rho_l,
         nu_l=nu_l, nu_v=nu_v, alpha_l=alpha_l, alpha_v=alpha_v, c_v=case.c_v,
         g=g, u_in=case.u_in, U_out=U_out, walls=int(getattr(case, "walls", 0)),
-        body_fx=float(getattr(case, "body_fx", 0.0)))
+        body_fx=float(getattr(case, "body_fx", 0.0)), collision=int(getattr(case, "collision", 0)))
     knots = np.ascontiguousarray(getattr(case, "wall_dT", ()) or (), dtype=np.float64)
     if knots.size:
         p.n_wall = knots.size
@@ -239,8 +240,8 @@ class Oracle:
                 "q_sum": out[1], "q_sumsq": out[2]}
 
 
-def collide_node(f, Fx, Fy, Fmx, Fmy, psi, omega, sigma):
-    """The C oracle's one-node CM collision (for definition-level tests)."""
+def collide_node(f, Fx, Fy, Fmx, Fmy, psi, omega, sigma, bgk=0):
+    """The C oracle's one-node collision, CM or (bgk=1) BGK (for definition-level tests)."""
     lib = load()
     M = np.empty(81)
     lib.orc_matrix_M(_ptr(M))
@@ -251,7 +252,7 @@ def collide_node(f, Fx, Fy, Fmx, Fmy, psi, omega, sigma):
     r = C.c_double()
     u = C.c_double()
     v = C.c_double()
-    lib.orc_collide_node(_ptr(f), Fx, Fy, Fmx, Fmy, psi, omega, sigma, _ptr(Minv), _ptr(out),
+    lib.orc_collide_node(_ptr(f), Fx, Fy, Fmx, Fmy, psi, omega, sigma, int(bgk), _ptr(Minv), _ptr(out),
                          C.byref(r), C.byref(u), C.byref(v))
     return out, r.value, u.value, v.value
 

@@ -59,6 +59,7 @@ class Case:
     periodic_x: int = 0
     walls: int = 0  # flat walls: bit 0 the column x = 0 (heated, instead of the inlet), bit 1 the rows y = 0, ny-1
     body_fx: float = 0.0  # uniform body force along +x
+    collision: int = 0  # 0: the central-moment collision; 1: single-rate BGK (the comparison operator)
     a: float = 2.0 / 49.0
     b: float = 2.0 / 21.0
     R: float = 1.0
@@ -141,3 +142,25 @@ def poiseuille_profile(L: int, U0: float = 0.01) -> np.ndarray:
     """The closed-form steady u_x at the fluid rows y = 1 .. L of poiseuille_case(L)."""
     yp = np.arange(1, L + 1) - 0.5
     return 4.0 * U0 * yp * (L - yp) / (L * L)
+
+
+def shear_layer_case(L: int = 512, Ma: float = 0.1, Re: float = 3.0e4, collision: int = 0) -> Case:
+    """Double shear layer (Sec. III.B): a periodic L x L single-phase fluid (G = 0, T fixed), with
+    u0 = Ma c_s (c_s^2 = 1/3) and nu = u0 L / Re; the initial velocity is shear_layer_velocity and
+    the initial density 1."""
+    u0 = Ma / np.sqrt(3.0)
+    return Case(nx=L, ny=L, D=0.0, xc=0.0, yc=0.0, periodic_x=1, G=0.0, sigma=0.0, energy=0, u_in=0.0,
+                nu_l=u0 * L / Re, nu_ratio=1.0, g=0.0, noise_amp=0.0, collision=collision,
+                name=f"shear_layer_L{L}_Ma{Ma:g}_{'bgk' if collision else 'cm'}")
+
+
+def shear_layer_velocity(L: int, Ma: float, kappa: float = 80.0, delta: float = 0.05):
+    """Initial (u_x, u_y) of the double shear layer (Sec. III.B) at the nodes (x, y), 0 <= x, y < L,
+    shape (L, L): two tanh shear layers of width 1/kappa at y/L = 1/4 and 3/4 and a transverse
+    sine perturbation of relative amplitude delta."""
+    u0 = Ma / np.sqrt(3.0)
+    y, x = np.mgrid[0:L, 0:L].astype(np.float64) / L
+    ux = np.where(y <= 0.5, u0 * np.tanh(kappa * (y - 0.25)), u0 * np.tanh(kappa * (0.75 - y)))
+    uy = u0 * delta * np.sin(2.0 * np.pi * (x + 0.25))
+    return ux, uy
+
