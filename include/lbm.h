@@ -112,7 +112,14 @@ typedef struct {
     double noise_amp;     /* amplitude of that perturbation (uniform in +/- noise_amp) */
     double body_fx;       /* uniform body force density along +x added to the force of Eq. (force), as the
                              driving force F_x = 8 nu U_0 / L_y^2 of the Poiseuille flow (Sec. III.C); 0: none */
+    int32_t collision;    /* lbm_collision: LBM_COLL_CM, the central-moment collision of Sec. II.A (the method), or
+                             LBM_COLL_BGK, the single-rate BGK operator the paper compares it with in Sec. III.B
+                             (same equilibrium, Eq. (equi), and forcing, Eq. (forcingTerm); every central moment
+                             relaxed at omega; no consistency term).  Batches and the adjoint take LBM_COLL_CM only */
+    int32_t reserved;     /* must be 0 */
 } lbm_params;
+
+typedef enum { LBM_COLL_CM = 0, LBM_COLL_BGK = 1 } lbm_collision;
 
 /* Optional initial fields (host, [ny][nx]); any pointer may be NULL.
  * rho0 = (rho ? rho : rho_l) + (drho ? drho : SplitMix64(seed) noise of amplitude noise_amp),

@@ -35,6 +35,9 @@ class Cylinder(C.Structure):
                 ("reserved", C.c_int32)]
 
 
+LBM_COLL_CM, LBM_COLL_BGK = 0, 1
+
+
 class Params(C.Structure):
     _fields_ = [("a", C.c_double), ("b", C.c_double), ("R", C.c_double), ("acentric", C.c_double),
                 ("G", C.c_double), ("sigma", C.c_double), ("Tr_sat", C.c_double), ("Re", C.c_double),
@@ -42,7 +45,8 @@ class Params(C.Structure):
                 ("Pr_v", C.c_double), ("c_v", C.c_double), ("g", C.c_double), ("outlet_U", C.c_double),
                 ("warmup_steps", C.c_int64), ("energy", C.c_int32), ("storage", C.c_int32),
                 ("compute_f64", C.c_int32), ("psi_mode", C.c_int32), ("seed", C.c_uint64),
-                ("noise_amp", C.c_double), ("body_fx", C.c_double)]
+                ("noise_amp", C.c_double), ("body_fx", C.c_double), ("collision", C.c_int32),
+                ("reserved", C.c_int32)]
 
 
 class Init(C.Structure):

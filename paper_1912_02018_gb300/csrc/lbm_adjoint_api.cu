@@ -333,6 +333,7 @@ lbm_status check_adjoint_ctx(lbm_ctx* c) {
   if (!c->prm.energy) return fail(c, LBM_EINVAL, "the adjoint needs the energy equation (energy = 1)");
   if (c->dom.walls != 0 || c->prm.body_fx != 0.0)
     return fail(c, LBM_EINVAL, "the adjoint differentiates the cylinder flow: no flat walls, no body force");
+  if (c->prm.collision != LBM_COLL_CM) return fail(c, LBM_EINVAL, "the adjoint differentiates the CM collision");
   if (!c->f64 && c->prm.storage != LBM_STORE_F32)
     return fail(c, LBM_EINVAL, "the FP32 adjoint needs storage = LBM_STORE_F32");
   if (c->steps < c->prm.warmup_steps)

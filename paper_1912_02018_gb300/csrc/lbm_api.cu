@@ -265,6 +265,9 @@ lbm_status lbm_create(const lbm_domain* domain, const lbm_cylinder* cyl, const l
   if (D.walls & ~3) return fail(nullptr, LBM_EINVAL, "walls takes bit 0 (x = 0) and bit 1 (y = 0, ny-1) only");
   if ((D.walls & 1) && D.periodic_x) return fail(nullptr, LBM_EINVAL, "a wall at x = 0 needs periodic_x = 0");
   if (!std::isfinite(P.body_fx)) return fail(nullptr, LBM_EINVAL, "body_fx must be finite");
+  if (P.collision != LBM_COLL_CM && P.collision != LBM_COLL_BGK)
+    return fail(nullptr, LBM_EINVAL, "collision must be LBM_COLL_CM (0) or LBM_COLL_BGK (1)");
+  if (P.reserved != 0) return fail(nullptr, LBM_EINVAL, "lbm_params.reserved must be 0");
   if (!(P.a > 0 && P.b > 0 && P.R > 0)) return fail(nullptr, LBM_EINVAL, "EOS constants a, b, R must be > 0");
   if (P.G > 0) return fail(nullptr, LBM_EINVAL, "G must be <= 0 (Eq. potential needs G < 0; 0 = single phase)");
   if (!(P.Tr_sat > 0 && P.Tr_sat < 1)) return fail(nullptr, LBM_EINVAL, "Tr_sat must lie in (0, 1)");
@@ -532,6 +535,8 @@ lbm_status lbm_create(const lbm_domain* domain, const lbm_cylinder* cyl, const l
     const char* e = std::getenv("LBM_TMA");
     d.tma = (e && e[0] == '0' && e[1] == 0) ? 0 : 1;
   }
+  static_assert(lbm::kCollCM == LBM_COLL_CM && lbm::kCollBGK == LBM_COLL_BGK, "collision operator codes");
+  d.collision = P.collision;
   int* dbn = static_cast<int*>(dalloc(c, sizeof(int) * (bnode.size() + 1)));
   double* dbv = static_cast<double*>(dalloc(c, sizeof(double) * (2 * bnode.size() + 1)));
   d.bnode = dbn;
@@ -981,6 +986,7 @@ lbm_status lbm_batch_create(int32_t n, const lbm_domain* domains, const lbm_cyli
     const int want = params[k].compute_f64 ? LBM_STORE_F64 : LBM_STORE_F32;
     if (params[k].storage != want || params[k].psi_mode != 0)
       return batch_fail(nullptr, LBM_EINVAL, "batches need storage F32 (FP32) or F64 (FP64 build) and psi_mode 0");
+    if (params[k].collision != LBM_COLL_CM) return batch_fail(nullptr, LBM_EINVAL, "batches use the CM collision");
   }
   lbm_batch* b = new lbm_batch();
   b->stream = static_cast<cudaStream_t>(cuda_stream);

@@ -58,6 +58,9 @@ struct Phys {
 
 // psi evaluation of the FP32 build (Eq. potential with Eq. eos); values of lbm_params.psi_mode.
 enum PsiMode { kPsiDF = 0, kPsiF64 = 1, kPsiF32 = 2 };
+// Collision operator (the values of lbm_collision): the CM collision of Sec. II.A, or the
+// single-rate BGK operator of the Sec. III.B comparison.
+enum CollisionOp { kCollCM = 0, kCollBGK = 1 };
 
 // Device buffers of one context (type-erased; element type is the storage / compute type).
 struct Dev {
@@ -75,6 +78,7 @@ struct Dev {
   const double* bn;  // their outward normals, [2][nb]
   int nb;
   int tma;           // 1: interior collision tiles are staged by TMA (environment LBM_TMA=0 turns it off)
+  int collision;     // LBM_COLL_CM or LBM_COLL_BGK
   double* hf;        // heat-flux accumulators: last, sum, sum of squares, count
   double* partial;   // one heat-flux partial sum per energy-kernel block (zero between launches)
   int wall_tiles[2]; // energy tiles (32 wide, 8 or 16 high) that hold a near-wall node

@@ -562,6 +562,60 @@ __device__ __forceinline__ void collide<float>(const float f[9], float rho, floa
   fs[8] = __fmul_rn(0.25f, __fadd_rn(wm, zm));
 }
 
+// Single-rate BGK on the same equilibrium and forcing, the operator the paper compares the CM
+// collision with (Sec. III.B): f* = f + omega (f^eq - f) + (1 - omega/2) F_i, u as above.  T(u) =
+// N(u) M is linear and maps f^eq and F_i to k^eq = (rho, 0, 0, 2 rho/3, 0, 0, 0, 0, rho/9) and
+// R = (0, F_x, F_y, 0, 0, 0, F_y/3, F_x/3, 0), so f* = (1 - omega) f + M^{-1} N(u)^{-1} k' with
+// k' = omega k^eq + (1 - omega/2) R: the forward substitution and reconstruction of the CM
+// collision on k'.  No consistency term (it belongs to the CM forcing of Eq. (force2)).
+template <typename C>
+__device__ __forceinline__ void collide_bgk(const C f[9], C rho, C Fx, C Fy, C omega, C fs[9], C& ux, C& uy) {
+  const C m1 = ((((f[1] - f[2]) + f[5]) - f[6]) + f[7]) - f[8];
+  const C m2 = ((((f[3] - f[4]) + f[5]) - f[6]) - f[7]) + f[8];
+  ux = fdiv(m1 + C(0.5) * Fx, rho);
+  uy = fdiv(m2 + C(0.5) * Fy, rho);
+  const C u = ux, v = uy;
+  // shift matrix N(u), App. A
+  const C N10 = -u, N20 = -v;
+  const C N30 = u * u + v * v, N31 = C(-2) * u, N32 = C(-2) * v;
+  const C N40 = u * u - v * v, N41 = C(-2) * u, N42 = C(2) * v;
+  const C N50 = u * v, N51 = -v, N52 = -u;
+  const C N60 = -u * u * v, N61 = C(2) * u * v, N62 = u * u, N63 = -v / C(2), N64 = -v / C(2), N65 = C(-2) * u;
+  const C N70 = -u * v * v, N71 = v * v, N72 = C(2) * u * v, N73 = -u / C(2), N74 = u / C(2), N75 = C(-2) * v;
+  const C N80 = u * u * v * v, N81 = C(-2) * u * v * v, N82 = C(-2) * u * u * v, N83 = (u * u + v * v) / C(2),
+          N84 = -(u * u - v * v) / C(2), N85 = C(4) * u * v, N86 = C(-2) * v, N87 = C(-2) * u;
+  const C cf = C(1) - C(0.5) * omega;
+  const C ks0 = omega * rho;
+  const C ks1 = cf * Fx;
+  const C ks2 = cf * Fy;
+  const C ks3 = omega * fdiv(C(2) * rho, C(3));
+  const C ks6 = cf * fdiv(Fy, C(3));
+  const C ks7 = cf * fdiv(Fx, C(3));
+  const C ks8 = omega * fdiv(rho, C(9));
+  // forward substitution N m' = k' (k'_4 = k'_5 = 0)
+  const C ms0 = ks0;
+  const C ms1 = ks1 - N10 * ms0;
+  const C ms2 = ks2 - N20 * ms0;
+  const C ms3 = ((ks3 - N30 * ms0) - N31 * ms1) - N32 * ms2;
+  const C ms4 = ((-N40 * ms0) - N41 * ms1) - N42 * ms2;
+  const C ms5 = ((-N50 * ms0) - N51 * ms1) - N52 * ms2;
+  const C ms6 = (((((ks6 - N60 * ms0) - N61 * ms1) - N62 * ms2) - N63 * ms3) - N64 * ms4) - N65 * ms5;
+  const C ms7 = (((((ks7 - N70 * ms0) - N71 * ms1) - N72 * ms2) - N73 * ms3) - N74 * ms4) - N75 * ms5;
+  const C ms8 =
+      (((((((ks8 - N80 * ms0) - N81 * ms1) - N82 * ms2) - N83 * ms3) - N84 * ms4) - N85 * ms5) - N86 * ms6) - N87 * ms7;
+  // f* = (1 - omega) f + M^{-1} m'
+  const C h = C(0.5), q = C(0.25), r = C(1) - omega;
+  fs[0] = r * f[0] + ((ms0 - ms3) + ms8);
+  fs[1] = r * f[1] + ((((h * ms1 + q * ms3) + q * ms4) - h * ms7) - h * ms8);
+  fs[2] = r * f[2] + ((((-h * ms1 + q * ms3) + q * ms4) + h * ms7) - h * ms8);
+  fs[3] = r * f[3] + ((((h * ms2 + q * ms3) - q * ms4) - h * ms6) - h * ms8);
+  fs[4] = r * f[4] + ((((-h * ms2 + q * ms3) - q * ms4) + h * ms6) - h * ms8);
+  fs[5] = r * f[5] + (((q * ms5 + q * ms6) + q * ms7) + q * ms8);
+  fs[6] = r * f[6] + (((q * ms5 - q * ms6) - q * ms7) + q * ms8);
+  fs[7] = r * f[7] + (((-q * ms5 - q * ms6) + q * ms7) + q * ms8);
+  fs[8] = r * f[8] + (((-q * ms5 + q * ms6) - q * ms7) + q * ms8);
+}
+
 // ---------------------------------------------------------------- k_rho_psi, k_collide
 constexpr int kCollTX = 32, kCollTY = 8;
 
@@ -602,8 +656,9 @@ __device__ __forceinline__ bool coll_staged(const Geo& g, int x0, int y0) {
 // One fluid-or-solid node (x, y) = (x0 + tx, y0 + ty) of a collision tile, mask m: pull (from
 // the staged populations s_f of a staged tile, else from global memory with the boundary
 // substitutions), interaction force from the psi tile s_psi with its 2-node halo, gravity,
-// CM collision; writes f* (other buffer), rho, u and the outlet's streamed values.
-template <typename C, typename S, int CTY>
+// CM collision (or, with OP = kCollBGK, the BGK comparison operator); writes f* (other
+// buffer), rho, u and the outlet's streamed values.
+template <typename C, typename S, int CTY, int OP = kCollCM>
 __device__ __forceinline__ void collide_node(const Geo& g, const Phys& ph, const S* __restrict__ f,
                                              S* __restrict__ fn, const C* __restrict__ psi,
                                              const uint8_t* __restrict__ mask, const C* __restrict__ side_in,
@@ -653,7 +708,8 @@ __device__ __forceinline__ void collide_node(const Geo& g, const Phys& ph, const
   const C omega = fdiv(C(1), add(fdiv(nu_of(ph, rho), cs2), C(0.5)));
   const C sig = need_psi ? k.sigma : C(0);
   C fs[9], ux, uy;
-  collide(fo, rho, Fx, Fy, Fmx, Fmy, psi0, omega, sig, fs, ux, uy);
+  if constexpr (OP == kCollBGK) collide_bgk(fo, rho, Fx, Fy, omega, fs, ux, uy);
+  else collide(fo, rho, Fx, Fy, Fmx, Fmy, psi0, omega, sig, fs, ux, uy);
 #pragma unroll
   for (int i = 0; i < 9; ++i) fn[i * g.plane + id] = PopIO<C, S>::st(fs[i], i, ph);
   rho_o[id] = rho;
@@ -674,7 +730,7 @@ __device__ __forceinline__ void psi_tile_plain(const Geo& g, const C* __restrict
 
 // Collision tile (bx, by) of 32 x CTY nodes.  tm_f, tm_psi: tensor maps of f and psi for TMA
 // staging, or null.
-template <typename C, typename S, int CTY>
+template <typename C, typename S, int CTY, int OP = kCollCM>
 __device__ __forceinline__ void collide_tile(const Geo& g, const Phys& ph, const S* __restrict__ f,
                                              S* __restrict__ fn, const C* __restrict__ psi,
                                              const uint8_t* __restrict__ mask, const C* __restrict__ side_in,
@@ -714,11 +770,11 @@ __device__ __forceinline__ void collide_tile(const Geo& g, const Phys& ph, const
     return;
   }
   if (!inside) return;
-  collide_node<C, S, CTY>(g, ph, f, fn, psi, mask, side_in, side_out, rho_o, ux_o, uy_o, forcing, status, tx, ty, x,
-                          y, m, staged, s_f, s_psi);
+  collide_node<C, S, CTY, OP>(g, ph, f, fn, psi, mask, side_in, side_out, rho_o, ux_o, uy_o, forcing, status, tx, ty,
+                              x, y, m, staged, s_f, s_psi);
 }
 
-template <typename C, typename S>
+template <typename C, typename S, int OP = kCollCM>
 // FP32: at most 36 registers, so 7 blocks share an SM and more pulls are in flight (the pass
 // waits on DRAM: +10% over the default register budget; with FP16 storage 7 blocks and a few
 // spilled registers still beat 6 blocks without spills, 30.8 vs 32.6 us at 1536 x 768)
@@ -727,8 +783,8 @@ __global__ void __launch_bounds__(kCollTX* kCollTY, sizeof(C) == 4 ? 7 : 1)
               const uint8_t* __restrict__ mask, const C* __restrict__ side_in, C* __restrict__ side_out,
               C* __restrict__ rho_o, C* __restrict__ ux_o, C* __restrict__ uy_o, int forcing, int* status,
               const __grid_constant__ CUtensorMap tm_f, const __grid_constant__ CUtensorMap tm_psi, int staged) {
-  collide_tile<C, S, kCollTY>(g, ph, f, fn, psi, mask, side_in, side_out, rho_o, ux_o, uy_o, forcing, status,
-                              blockIdx.x, blockIdx.y, staged ? &tm_f : nullptr, staged ? &tm_psi : nullptr);
+  collide_tile<C, S, kCollTY, OP>(g, ph, f, fn, psi, mask, side_in, side_out, rho_o, ux_o, uy_o, forcing, status,
+                                  blockIdx.x, blockIdx.y, staged ? &tm_f : nullptr, staged ? &tm_psi : nullptr);
 }
 
 // ---------------------------------------------------------------- k_energy
@@ -1467,8 +1523,12 @@ int step_impl(const Geo& g, const Phys& ph, const Dev& d, int cur, int tcur, int
   const bool staged = d.tma && tma::encode<S>(&tm_f, f, g.nx, g.ny, g.pitch, g.plane, 9, CS::FW, CS::FH) &&
                       tma::encode<C>(&tm_psi, psi, g.nx, g.ny, g.pitch, g.plane, 1, CS::PW, CS::PH);
   pre(kKCollide);
-  k_collide<C, S><<<grd, blk, 0, s>>>(g, ph, f, fn, psi, d.mask, side_in, side_out, rho, ux, uy, forcing, d.status,
-                                      tm_f, tm_psi, staged ? 1 : 0);
+  if (d.collision == kCollBGK)
+    k_collide<C, S, kCollBGK><<<grd, blk, 0, s>>>(g, ph, f, fn, psi, d.mask, side_in, side_out, rho, ux, uy, forcing,
+                                                  d.status, tm_f, tm_psi, staged ? 1 : 0);
+  else
+    k_collide<C, S><<<grd, blk, 0, s>>>(g, ph, f, fn, psi, d.mask, side_in, side_out, rho, ux, uy, forcing, d.status,
+                                        tm_f, tm_psi, staged ? 1 : 0);
   post(kKCollide);
   *t_flipped = 0;
   if (energy && forcing) {

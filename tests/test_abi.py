@@ -39,7 +39,7 @@ def test_library_exports_every_declared_symbol(lib):
 def test_struct_sizes_match_header_layout():
     assert C.sizeof(N.Domain) == 16
     assert C.sizeof(N.Cylinder) == 56
-    assert C.sizeof(N.Params) == 16 * 8 + 8 + 16 + 16 + 8
+    assert C.sizeof(N.Params) == 16 * 8 + 8 + 16 + 16 + 8 + 8
     assert C.sizeof(N.Init) == 40
     assert C.sizeof(N.Info) == 15 * 8 + 4 * 8
     assert C.sizeof(N.WindowGrad) == 3 * 8 + 2 * 8
@@ -68,7 +68,7 @@ def _good():
 
 
 @pytest.mark.parametrize("what", ["small", "storage", "G", "Tr", "cyl_inlet", "cyl_wide", "nu", "psi_mode",
-                                  "walls_bits", "wall_periodic"])
+                                  "walls_bits", "wall_periodic", "collision", "reserved"])
 def test_invalid_parameters_are_rejected_on_the_host(lib, what):
     dom, cyl, prm = _good()
     if what == "small":
@@ -89,6 +89,10 @@ def test_invalid_parameters_are_rejected_on_the_host(lib, what):
         dom.walls = 4
     elif what == "wall_periodic":
         dom.walls, dom.periodic_x = 1, 1  # a wall at x = 0 replaces the inlet of a non-periodic domain
+    elif what == "collision":
+        prm.collision = 2
+    elif what == "reserved":
+        prm.reserved = 1
     elif what == "nu":
         prm.Re = 0.0  # nu_l = 0 and no Reynolds number: no valid relaxation rate
     st, h = _create(lib, dom, cyl, prm)

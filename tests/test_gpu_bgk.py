@@ -1,0 +1,92 @@
+"""The BGK comparison operator of Sec. III.B on the CUDA path (lbm_params.collision = 1): parity
+with the FP64 oracle on the multiphase cylinder case and on the double shear layer, and the
+shear-layer stability comparison with the CM collision at the paper's size."""
+import numpy as np
+import pytest
+
+import synthetic_inputs as si
+from oracle import Oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+
+    from oracle import build as ob
+    from paper_1912_02018_gb300 import build
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    build()
+    ob.build()
+    torch.cuda.set_device(0)
+
+
+def Sim():
+    from paper_1912_02018_gb300 import Sim as S
+
+    return S
+
+
+def errors(sim, ref, names):
+    """max |gpu - oracle| over fluid nodes, relative to the field's largest magnitude (the velocity
+    components to the largest speed)."""
+    got = sim.fields(names)
+    fluid = ref.field("solid") == 0
+    speed = np.hypot(ref.field("ux"), ref.field("uy"))[fluid].max()
+    out = {}
+    for k in names:
+        r = ref.field(k)
+        den = speed if k in ("ux", "uy") else np.abs(r[fluid]).max()
+        out[k] = np.abs(got[k] - r)[fluid].max() / den
+    return out
+
+
+@pytest.mark.parametrize("f64", [True, False], ids=["fp64", "fp32"])
+def test_bgk_parity_multiphase_cylinder(f64):
+    # the whole boiling step (interaction force, gravity, energy equation) with the BGK operator
+    case = si.SMALL.replace(collision=1)
+    steps = 400 if f64 else 200
+    init = {"drho": case.drho()}
+    sim = Sim().from_case(case, f64=f64, init=init).step(steps)
+    ref = Oracle(case, **init).step(steps)
+    err = errors(sim, ref, ("rho", "ux", "uy", "T", "psi"))
+    tol = 1e-12 if f64 else {"rho": 1e-5, "T": 1e-5, "ux": 1e-4, "uy": 1e-4, "psi": 1e-5}
+    tols = tol if isinstance(tol, dict) else {k: tol for k in err}
+    assert all(err[k] <= tols[k] for k in err), err
+
+
+def test_bgk_and_cm_steps_differ():
+    # the operator switch reaches the kernel: one step of each from the same state differs
+    case = si.SMALL
+    init = {"drho": case.drho()}
+    a = Sim().from_case(case, f64=True, init=init).step(5).fields(("ux",))["ux"]
+    b = Sim().from_case(case.replace(collision=1), f64=True, init=init).step(5).fields(("ux",))["ux"]
+    assert np.abs(a - b).max() > 1e-9
+
+
+@pytest.mark.parametrize("collision", [0, 1], ids=["cm", "bgk"])
+@pytest.mark.parametrize("f64", [True, False], ids=["fp64", "fp32"])
+def test_shear_layer_parity(collision, f64):
+    L, Ma, steps = 64, 0.3, 300
+    case = si.shear_layer_case(L, Ma, collision=collision)
+    ux, uy = si.shear_layer_velocity(L, Ma)
+    init = {"rho": np.ones((L, L)), "ux": ux, "uy": uy}
+    sim = Sim().from_case(case, f64=f64, init=init).step(steps)
+    ref = Oracle(case, **init).step(steps)
+    err = errors(sim, ref, ("rho", "ux", "uy"))
+    tol = 1e-12 if f64 else 1e-5
+    assert max(err.values()) <= tol, err
+
+
+def test_shear_layer_matches_the_driver_inputs():
+    from paper_1912_02018_gb300 import shear_layer
+
+    a = si.shear_layer_velocity(96, 0.6)
+    b = shear_layer.initial_velocity(96, 0.6)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    c, d = si.shear_layer_case(96, 0.6, collision=1), shear_layer.paper_case(96, 0.6, collision=1)
+    for k in ("nx", "ny", "periodic_x", "G", "energy", "nu_l", "g", "collision"):
+        assert getattr(c, k) == getattr(d, k), k
