@@ -90,3 +90,44 @@ def test_shear_layer_matches_the_driver_inputs():
     c, d = si.shear_layer_case(96, 0.6, collision=1), shear_layer.paper_case(96, 0.6, collision=1)
     for k in ("nx", "ny", "periodic_x", "G", "energy", "nu_l", "g", "collision"):
         assert getattr(c, k) == getattr(d, k), k
+
+
+def _golden():
+    import json
+    import os
+
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "shear_layer_energy_L512.json")
+    with open(path) as fh:
+        return {(r["Ma"], r["collision"]): r for r in json.load(fh)["runs"]}
+
+
+@pytest.mark.parametrize("Ma", [0.1, 0.3, 0.6])
+def test_shear_layer_L512_follows_the_oracle(Ma):
+    # the paper's size (L = 512, Re = 3e4) through the driver, FP32, against the FP64 oracle's
+    # kinetic-energy history (written by tests/golden/make_shear_layer_energy.py) at t/t0 = 0.1 .. 1
+    from paper_1912_02018_gb300 import shear_layer
+
+    gold = _golden()
+    res = {}
+    for op, name in ((0, "cm"), (1, "bgk")):
+        r = shear_layer.run(512, Ma, 3.0e4, op, t_end=1.0, samples=10)
+        g = gold[(Ma, name)]
+        res[name] = r
+        if g["status"] == "ok":
+            assert r["status"] == "ok", r["status"]
+            assert np.allclose(r["t_over_t0"], g["t_over_t0"], rtol=0, atol=1e-12)
+            assert np.allclose(r["E_over_E0"], g["E_over_E0"], rtol=0, atol=1e-3), (r["E_over_E0"], g["E_over_E0"])
+        else:
+            # a run the oracle saw blow up does so here too, in the same sampling interval or the one before
+            assert r["status"] != "ok"
+            assert len(g["E_over_E0"]) - 1 <= len(r["E_over_E0"]) <= len(g["E_over_E0"])
+            n = len(r["E_over_E0"])
+            assert np.allclose(r["E_over_E0"][: n - 1], g["E_over_E0"][: n - 1], rtol=0, atol=1e-3)
+    # Sec. III.B: the operators agree at Ma 0.1 and 0.3; at Ma 0.6 BGK blows up near t/t0 = 0.66
+    # while the CM collision runs on
+    if Ma < 0.5:
+        assert res["bgk"]["status"] == "ok"
+        assert np.abs(np.subtract(res["cm"]["E_over_E0"], res["bgk"]["E_over_E0"])).max() < 1e-3
+    else:
+        assert res["cm"]["status"] == "ok" and len(res["cm"]["E_over_E0"]) == 10
+        assert res["bgk"]["status"] != "ok" and 5 <= len(res["bgk"]["E_over_E0"]) <= 7
