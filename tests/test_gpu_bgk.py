@@ -70,8 +70,10 @@ def test_bgk_and_cm_steps_differ():
 @pytest.mark.parametrize("collision", [0, 1], ids=["cm", "bgk"])
 @pytest.mark.parametrize("f64", [True, False], ids=["fp64", "fp32"])
 def test_shear_layer_parity(collision, f64):
+    # Re 5000 at this size (at Re 3e4 the 64 x 64 layer is under-resolved and BGK blows up
+    # within 300 steps, in the oracle too)
     L, Ma, steps = 64, 0.3, 300
-    case = si.shear_layer_case(L, Ma, collision=collision)
+    case = si.shear_layer_case(L, Ma, Re=5000.0, collision=collision)
     ux, uy = si.shear_layer_velocity(L, Ma)
     init = {"rho": np.ones((L, L)), "ux": ux, "uy": uy}
     sim = Sim().from_case(case, f64=f64, init=init).step(steps)
