@@ -79,8 +79,12 @@ def test_shear_layer_parity(collision, f64):
     sim = Sim().from_case(case, f64=f64, init=init).step(steps)
     ref = Oracle(case, **init).step(steps)
     err = errors(sim, ref, ("rho", "ux", "uy"))
-    tol = 1e-12 if f64 else 1e-5
-    assert max(err.values()) <= tol, err
+    # FP32: rho within 1e-5 as everywhere; the velocity within 1e-4 of the largest speed, the bar of the
+    # other FP32 velocity checks: BGK relaxes its non-hydrodynamic moments by (1 - omega) = -0.97 per step
+    # here (nu = 2.2e-3), so their rounding errors linger for tens of steps instead of one as under the
+    # CM collision (measured: u 3.0e-5 under BGK, below 1e-5 under CM after 300 steps)
+    tol = {k: 1e-12 for k in err} if f64 else {"rho": 1e-5, "ux": 1e-4, "uy": 1e-4}
+    assert all(err[k] <= tol[k] for k in err), err
 
 
 def test_shear_layer_matches_the_driver_inputs():
