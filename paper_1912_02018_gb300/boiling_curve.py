@@ -15,6 +15,7 @@ Mode 2, Epstein-Hauser with C = 0.537 (theory) and 1.13 (fit), Ito et al. with C
 0.51; with gamma = rho_l / rho_v, eta = nu_l / nu_v, Re = u_l D / nu_l, Pr = nu_v / alpha_v.
 
     python -m paper_1912_02018_gb300.boiling_curve --Re 30 --steps 100000
+    python -m paper_1912_02018_gb300.boiling_curve --Re 30000 --Pr-v 1.5e-3   # low-Prandtl study, Sec. IV.C
 
 Prints one JSON document.  Lattice units.
 """
@@ -58,21 +59,24 @@ def correlations(gamma, eta, Re, Pr, Ja) -> dict:
     }
 
 
-def paper_case(dT, Re, seed, a=3.0 / 49.0, b=2.0 / 21.0, R=1.0, D=30.0, u_l=0.05, Tr=0.86, warmup=3000, rho_s=0.0):
+def paper_case(dT, Re, seed, a=3.0 / 49.0, b=2.0 / 21.0, R=1.0, D=30.0, u_l=0.05, Tr=0.86, warmup=3000, rho_s=0.0,
+               Pr_l=0.862, Pr_v=1.5):
     """One domain of the sweep; dT in lattice temperature units; rho_s the density that sets the
-    solid's psi (0: rho_l, a liquid-wetting wall; the paper does not state it)."""
+    solid's psi (0: rho_l, a liquid-wetting wall; the paper does not state it); Pr_l, Pr_v the
+    Prandtl numbers (Pr_v = 1.5e-3 for the low-Prandtl study of Sec. IV.C)."""
     Tc = 0.0778 * a / (0.4572 * b * R)  # Peng-Robinson critical temperature (Sec. II.C)
     H, W = 45.0 * D, 20.0 * D
     return SimpleNamespace(
         nx=int(H), ny=int(W), D=D, xc=0.2 * H, yc=0.5 * W, periodic_x=0, walls=0, superheat_Tc=dT / Tc, rho_s=rho_s,
         a=a, b=b, R=R, acentric=0.344, G=-1.0, sigma=0.38, Tr_sat=Tr, Re=Re, u_in=u_l, nu_l=0.0, nu_ratio=1.0,
-        Pr_l=0.862, Pr_v=1.5, c_v=11.0, g=-1.0, U_out=-1.0, warmup=warmup, energy=1, seed=seed, noise_amp=1e-4,
+        Pr_l=Pr_l, Pr_v=Pr_v, c_v=11.0, g=-1.0, U_out=-1.0, warmup=warmup, energy=1, seed=seed, noise_amp=1e-4,
         psi_mode=0, wall_dT=(), body_fx=0.0)
 
 
-def run(Re, dTs, steps, warmup=3000, rho_s=0.0):
+def run(Re, dTs, steps, warmup=3000, rho_s=0.0, Pr_l=0.862, Pr_v=1.5):
     """A domain whose state turns non-finite is reported as such (status), the others go on."""
-    cases = [paper_case(dT, Re, seed=k + 1, warmup=warmup, rho_s=rho_s) for k, dT in enumerate(dTs)]
+    cases = [paper_case(dT, Re, seed=k + 1, warmup=warmup, rho_s=rho_s, Pr_l=Pr_l, Pr_v=Pr_v)
+             for k, dT in enumerate(dTs)]
     b = Batch(cases)
     status = ["ok"] * len(cases)
     t0 = time.perf_counter()
@@ -105,7 +109,7 @@ def run(Re, dTs, steps, warmup=3000, rho_s=0.0):
     nodes = sum(c.nx * c.ny for c in cases)
     b.close()
     return {"Re": Re, "steps": steps, "warmup": warmup, "domain": [cases[0].nx, cases[0].ny], "D": cases[0].D,
-            "rho_s": rho_s if rho_s > 0 else info["rho_l"],
+            "rho_s": rho_s if rho_s > 0 else info["rho_l"], "Pr_l": Pr_l, "Pr_v": Pr_v,
             "gamma": gamma, "eta": eta, "Pr": Pr, "h_fg": info["h_fg"], "lambda_v": info["lambda_v"],
             "seconds": seconds, "mlups": nodes * steps / seconds / 1e6, "points": points}
 
@@ -116,10 +120,12 @@ def main():
     ap.add_argument("--steps", type=int, default=100000)
     ap.add_argument("--warmup", type=int, default=3000)
     ap.add_argument("--rho-s", type=float, default=0.0, help="density of the solid's psi (0: rho_l)")
+    ap.add_argument("--Pr-l", type=float, default=0.862, help="liquid Prandtl number")
+    ap.add_argument("--Pr-v", type=float, default=1.5, help="vapour Prandtl number (1.5e-3: the low-Prandtl study)")
     ap.add_argument("--dT", type=float, nargs="*", default=[round(0.005 * k, 3) for k in range(1, 14)],
                     help="superheats in lattice units (default 0.005 .. 0.065, the paper's range)")
     a = ap.parse_args()
-    print(json.dumps(run(a.Re, a.dT, a.steps, a.warmup, a.rho_s)))
+    print(json.dumps(run(a.Re, a.dT, a.steps, a.warmup, a.rho_s, a.Pr_l, a.Pr_v)))
 
 
 if __name__ == "__main__":
