@@ -68,7 +68,7 @@ def paper_case(dT, Re, seed, a=3.0 / 49.0, b=2.0 / 21.0, R=1.0, D=30.0, u_l=0.05
     H, W = 45.0 * D, 20.0 * D
     return SimpleNamespace(
         nx=int(H), ny=int(W), D=D, xc=0.2 * H, yc=0.5 * W, periodic_x=0, walls=0, superheat_Tc=dT / Tc, rho_s=rho_s,
-        a=a, b=b, R=R, acentric=0.344, G=-1.0, sigma=0.38, Tr_sat=Tr, Re=Re, u_in=u_l, nu_l=0.0, nu_ratio=1.0,
+        a=a, b=b, R=R, acentric=0.344, G=-2.0, sigma=0.38, Tr_sat=Tr, Re=Re, u_in=u_l, nu_l=0.0, nu_ratio=1.0,
         Pr_l=Pr_l, Pr_v=Pr_v, c_v=11.0, g=-1.0, U_out=-1.0, warmup=warmup, energy=1, seed=seed, noise_amp=1e-4,
         psi_mode=0, wall_dT=(), body_fx=0.0)
 

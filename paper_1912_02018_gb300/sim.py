@@ -12,7 +12,7 @@ import numpy as np
 
 from . import _native as N
 
-_PARAM_DEFAULTS = dict(a=2.0 / 49.0, b=2.0 / 21.0, R=1.0, acentric=0.344, G=-1.0, sigma=0.38, Tr_sat=0.86,
+_PARAM_DEFAULTS = dict(a=2.0 / 49.0, b=2.0 / 21.0, R=1.0, acentric=0.344, G=-2.0, sigma=0.38, Tr_sat=0.86,
                        Re=30.0, u_in=0.05, nu_l=0.0, nu_ratio=1.0, Pr_l=0.862, Pr_v=1.5, c_v=11.0, g=-1.0,
                        outlet_U=-1.0, warmup=0, energy=1, seed=0, noise_amp=1e-4, psi_mode=0, wall_dT=(),
                        body_fx=0.0, collision=0)

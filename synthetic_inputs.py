@@ -64,7 +64,7 @@ class Case:
     b: float = 2.0 / 21.0
     R: float = 1.0
     acentric: float = 0.344
-    G: float = -1.0
+    G: float = -2.0
     sigma: float = 0.38
     Tr_sat: float = 0.86
     superheat_Tc: float = 0.05

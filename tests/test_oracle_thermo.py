@@ -84,8 +84,8 @@ def test_psi_definition_and_radicand_positive():
         for T in (d.T_sat, d.T_wall):
             psi = fn["psi"](rho, T)
             assert psi > 0
-            # G cs^2 psi^2 / 2 = p - rho cs^2 with G = -1, Eq. (potential)
-            assert abs(-1.0 / 3.0 * psi ** 2 / 2 - (d.eos.p(rho, T) - rho / 3)) < 1e-14
+            # G cs^2 psi^2 / 2 = p - rho cs^2, Eq. (potential)
+            assert abs(case.G / 3.0 * psi ** 2 / 2 - (d.eos.p(rho, T) - rho / 3)) < 1e-14
 
 
 def test_gravity_from_froude_number_matches_paper():
