@@ -389,7 +389,7 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": case.name, "nx": case.nx, "ny": case.ny, "D": case.D, "Re": case.Re,
-                   "superheat_Tc": case.superheat_Tc, "storage": args.storage,
+                   "superheat_Tc": case.superheat_Tc, "G": case.G, "sigma": case.sigma, "storage": args.storage,
                    "psi": ["double-float (FP32 pairs)", "IEEE f64", "f32"][args.psi_mode],
                    "l2": "flushed (256 MB write) before every timed step", "parallelism": "replicas"},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
