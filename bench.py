@@ -182,7 +182,8 @@ def run_reference(args):
             "n_gpus": args.gpus, "steps": n, "warmup": args.warmup, "ms_per_step": ms_per_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": case.name, "nx": case.nx, "ny": case.ny,
-                                            "D": case.D, "l2": "inputs larger than L2 (CPU run)"},
+                                            "D": case.D, "Re": case.Re, "superheat_Tc": case.superheat_Tc,
+                                            "G": case.G, "sigma": case.sigma, "l2": "inputs larger than L2 (CPU run)"},
             "cpu_baseline": cpu,
             "e2e": {"value": cpu["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
