@@ -87,16 +87,6 @@ def test_shear_layer_parity(collision, f64):
     assert all(err[k] <= tol[k] for k in err), err
 
 
-def test_shear_layer_matches_the_driver_inputs():
-    from paper_1912_02018_gb300 import shear_layer
-
-    a = si.shear_layer_velocity(96, 0.6)
-    b = shear_layer.initial_velocity(96, 0.6)
-    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
-    c, d = si.shear_layer_case(96, 0.6, collision=1), shear_layer.paper_case(96, 0.6, collision=1)
-    for k in ("nx", "ny", "periodic_x", "G", "energy", "nu_l", "g", "collision"):
-        assert getattr(c, k) == getattr(d, k), k
-
 
 def _golden():
     import json
