@@ -105,3 +105,19 @@ def test_null_handles_are_rejected(lib):
     assert lib.lbm_step(None, 1) == N.LBM_EINVAL
     assert lib.lbm_sync(None) == N.LBM_EINVAL
     lib.lbm_destroy(None)
+
+
+@pytest.mark.parametrize("what", ["collision", "psi_mode", "storage"])
+def test_batch_takes_the_cm_collision_and_default_precision_only(lib, what):
+    # checked on the host before any domain is created
+    dom, cyl, prm = _good()
+    if what == "collision":
+        prm.collision = N.LBM_COLL_BGK
+    elif what == "psi_mode":
+        prm.psi_mode = 1
+    else:
+        prm.storage = N.LBM_STORE_F16S
+    h = C.c_void_p()
+    st = lib.lbm_batch_create(1, C.byref(dom), C.byref(cyl), C.byref(prm), None, None, C.byref(h))
+    assert st == N.LBM_EINVAL
+    assert not h.value

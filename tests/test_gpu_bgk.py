@@ -58,6 +58,29 @@ def test_bgk_parity_multiphase_cylinder(f64):
     assert all(err[k] <= tols[k] for k in err), err
 
 
+def test_bgk_with_other_population_storage():
+    # FP64 storage with FP32 arithmetic gives the FP32-storage bits; shifted FP16 storage stays within
+    # the bar of the CM collision's FP16 parity (2e-4 on rho and T after 200 steps)
+    case = si.SMALL.replace(collision=1)
+    init = {"drho": case.drho()}
+    a = Sim().from_case(case, f64=False, storage="f32", init=init).step(200).fields(("rho", "ux", "uy", "T"))
+    b = Sim().from_case(case, f64=False, storage="f64", init=init).step(200).fields(("rho", "ux", "uy", "T"))
+    for k in a:
+        assert np.array_equal(a[k], b[k]), k
+    sim = Sim().from_case(case, f64=False, storage="f16s", init=init).step(200)
+    ref = Oracle(case, **init).step(200)
+    err = errors(sim, ref, ("rho", "T"))
+    assert max(err.values()) < 2e-4, err
+
+
+def test_adjoint_rejects_the_bgk_operator():
+    from paper_1912_02018_gb300._native import LbmError
+
+    sim = Sim().from_case(si.SMALL.replace(collision=1), f64=True)
+    with pytest.raises(LbmError):
+        sim.adjoint_window(10, 5)
+
+
 def test_bgk_and_cm_steps_differ():
     # the operator switch reaches the kernel: one step of each from the same state differs
     case = si.SMALL
