@@ -365,6 +365,12 @@ lbm_status lbm_create(const lbm_domain* domain, const lbm_cylinder* cyl, const l
   phys.invTc2 = split(1.0 / eos.Tc);
   phys.cs22 = split(1.0 / 3.0);
   phys.k2 = split(P.G != 0 ? 2.0 / (P.G * (1.0 / 3.0)) : 0.0);
+  {
+    const double k = P.G != 0 ? 2.0 / (P.G * (1.0 / 3.0)) : 0.0;
+    phys.kR2 = split(k * P.R);
+    phys.ka2 = split(k * P.a);
+    phys.k32 = split(k / 3.0);
+  }
   phys.dpdT_c1 = (float)(eos.kappa * (1.0 + eos.kappa));
   phys.dpdT_c2 = (float)(eos.kappa * eos.kappa / eos.Tc);
   {

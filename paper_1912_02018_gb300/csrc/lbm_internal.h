@@ -52,6 +52,7 @@ struct Phys {
   PhysC<double> d;
   PhysC<float> f;
   F2 a2, b2, R2, kappa2, invTc2, cs22, k2;
+  F2 kR2, ka2, k32;  // k R, k a, k / 3 with k = 2 / (G cs^2): the double-float psi's folded constants
   float dpdT_c1, dpdT_c2;  // kappa (1 + kappa) and kappa^2 / Tc: (dp/dT)_rho of the FP32 energy pass
   float pop_shift[9];  // shifted FP16 storage keeps f_i - w_i rho_l; these are w_i rho_l
 };

@@ -171,14 +171,7 @@ __device__ __forceinline__ DF two_prod(float a, float b) {
   float p = __fmul_rn(a, b);
   return {p, __fmaf_rn(a, b, -p)};
 }
-__device__ __forceinline__ DF df_add(DF a, DF b) {
-  DF s = two_sum(a.hi, b.hi);
-  DF t = two_sum(a.lo, b.lo);
-  DF v = fast_two_sum(s.hi, __fadd_rn(s.lo, t.hi));
-  return fast_two_sum(v.hi, __fadd_rn(t.lo, v.lo));
-}
 __device__ __forceinline__ DF df_neg(DF a) { return {-a.hi, -a.lo}; }
-__device__ __forceinline__ DF df_sub(DF a, DF b) { return df_add(a, df_neg(b)); }
 __device__ __forceinline__ DF df_mul(DF a, DF b) {
   DF c = two_prod(a.hi, b.hi);
   float t = __fmaf_rn(a.lo, b.hi, __fmul_rn(a.hi, b.lo));
@@ -187,19 +180,6 @@ __device__ __forceinline__ DF df_mul(DF a, DF b) {
 __device__ __forceinline__ DF df_mulf(DF a, float b) {
   DF c = two_prod(a.hi, b);
   return fast_two_sum(c.hi, __fmaf_rn(a.lo, b, c.lo));
-}
-__device__ __forceinline__ DF df_div(DF a, DF b) {
-  float q1 = __fdividef(a.hi, b.hi);
-  DF r = df_sub(a, df_mulf(b, q1));
-  float q2 = __fdividef(r.hi, b.hi);
-  DF q = fast_two_sum(q1, q2);
-  r = df_sub(a, df_mul(b, q));
-  return df_add(q, {__fdividef(r.hi, b.hi), 0.0f});
-}
-__device__ __forceinline__ DF df_sqrt(DF a) {
-  float s = __fsqrt_rn(a.hi);
-  DF r = df_sub(a, two_prod(s, s));
-  return fast_two_sum(s, __fdividef(r.hi, __fmul_rn(2.0f, s)));
 }
 __device__ __forceinline__ DF df_of(F2 v) { return {v.hi, v.lo}; }
 
@@ -217,10 +197,13 @@ __device__ __forceinline__ double psi_eos(const Phys& ph, double rho, double T, 
   return sqrt(rad);
 }
 // The same in double-float arithmetic (inputs and result FP32), rearranged over one
-// denominator: with x = b rho and D = 1 + 2x - x^2,
-//   rad = k rho [R T D - a phi rho (1 - x) - (1 - x) D / 3] / ((1 - x) D),  k = 2/(G cs^2),
-// whose numerator has condition number ~2 over the liquid-vapour range, so the cheaper
-// double-word addition (Joldes et al., Alg. 5) keeps ~2^-44 relative accuracy.
+// denominator: with x = b rho and D = 1 + 2x - x^2 = 2 - (1 - x)^2,
+//   rad = rho [kR T D - ka phi rho (1 - x) - (k/3)(1 - x) D] / ((1 - x) D),  k = 2/(G cs^2)
+// (kR, ka, k/3 folded on the host), whose numerator has condition number ~2 over the
+// liquid-vapour range, so the cheaper double-word addition (Joldes et al., Alg. 5) keeps
+// ~2^-44 relative accuracy.  Square roots: the correctly rounded FP32 root s of the high word
+// and one Newton step s + (a - s^2) / (2s) with the residual from one fma (Karp and Markstein,
+// "High-precision division and square root", ACM TOMS 1997), which leaves ~2^-46.
 __device__ __forceinline__ DF df_add_s(DF a, DF b) {
   DF s = two_sum(a.hi, b.hi);
   return fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
@@ -231,21 +214,25 @@ __device__ __forceinline__ DF df_div_s(DF a, DF b) {
   DF r = df_sub_s(a, df_mulf(b, q1));
   return fast_two_sum(q1, __fdividef(r.hi, b.hi));
 }
+__device__ __forceinline__ DF df_sqrt_newton(DF a) {
+  const float s = __fsqrt_rn(a.hi);
+  const float e = __fadd_rn(__fmaf_rn(-s, s, a.hi), a.lo);
+  return {s, __fdividef(e, __fmul_rn(2.0f, s))};
+}
 __device__ __forceinline__ float psi_eos_df(const Phys& ph, float rho, float T, float& rad_hi) {
-  const DF one = {1.0f, 0.0f}, third = {0.333333343f, -9.93410776e-09f};
-  DF sq = df_sqrt(df_mulf(df_of(ph.invTc2), T));
+  const DF one = {1.0f, 0.0f}, two = {2.0f, 0.0f};
+  DF sq = df_sqrt_newton(df_mulf(df_of(ph.invTc2), T));
   DF s = df_add_s(one, df_mul(df_of(ph.kappa2), df_sub_s(one, sq)));
   DF phi = df_mul(s, s);
-  DF x = df_mulf(df_of(ph.b2), rho);
-  DF omx = df_sub_s(one, x);
-  DF D = df_sub_s(df_add_s(one, DF{2.0f * x.hi, 2.0f * x.lo}), df_mul(x, x));
+  DF omx = df_sub_s(one, df_mulf(df_of(ph.b2), rho));
+  DF D = df_sub_s(two, df_mul(omx, omx));
   DF den = df_mul(omx, D);
-  DF A = df_mul(df_mulf(df_of(ph.R2), T), D);
-  DF B = df_mul(df_mulf(df_mul(df_of(ph.a2), phi), rho), omx);
-  DF num = df_sub_s(df_sub_s(A, B), df_mul(den, third));
-  DF rad = df_div_s(df_mulf(df_mul(df_of(ph.k2), num), rho), den);
+  DF A = df_mul(df_mulf(df_of(ph.kR2), T), D);
+  DF B = df_mul(df_mulf(df_mul(df_of(ph.ka2), phi), rho), omx);
+  DF num = df_sub_s(df_sub_s(A, B), df_mul(den, df_of(ph.k32)));
+  DF rad = df_div_s(df_mulf(num, rho), den);
   rad_hi = rad.hi;
-  DF r = df_sqrt(rad);
+  const DF r = df_sqrt_newton(rad);
   return __fadd_rn(r.hi, r.lo);
 }
 // The same in plain FP32.
