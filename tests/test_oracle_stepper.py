@@ -320,9 +320,10 @@ def test_flat_interface_near_maxwell_with_the_default_interaction_strength():
 
 
 @pytest.mark.slow
-def test_laplace_law_pressure_jump_scales_as_inverse_radius():
+@pytest.mark.parametrize("G", [-1.0, -2.0])
+def test_laplace_law_pressure_jump_scales_as_inverse_radius(G):
     def bubble(R, n=64, steps=5000):
-        c = periodic_case(n, G=-1.0, sigma=0.38, energy=0, nu_l=0.1)
+        c = periodic_case(n, G=G, sigma=0.38, energy=0, nu_l=0.1)
         _, d = stepper.derive(c)
         y, x = np.mgrid[0:n, 0:n]
         r = np.hypot(x - n / 2 + 0.5, y - n / 2 + 0.5)
