@@ -1,8 +1,9 @@
-"""Pins of the oracle's flat walls and body force against the Poiseuille closed form (Sec. III.C).
+"""Pins of the oracle's flat walls, body force and phase change against closed forms.
 
-Halfway bounce-back on flat walls (link fraction 1/2) with the uniform force F_x = 8 nu U0 / L^2
-must converge to u_x = 4 U0 y' (L - y') / L^2 at second order in the channel width (the paper
-reports 2.04), with no transverse velocity and uniform density.
+Poiseuille (Sec. III.C): halfway bounce-back on flat walls (link fraction 1/2) with the uniform
+force F_x = 8 nu U0 / L^2 must converge to u_x = 4 U0 y' (L - y') / L^2 at second order in the
+channel width (the paper reports 2.04), with no transverse velocity and uniform density.
+Stefan (Sec. III.E): a vapour film on a heated wall grows as Welch's 2 beta sqrt(alpha_v t).
 """
 import numpy as np
 import pytest
@@ -50,3 +51,45 @@ def test_flat_walls_give_halfway_links_and_wall_normals():
     assert np.all(ny_[ys == 1] == 1.0) and np.all(ny_[ys == case.ny - 2] == -1.0)
     mid = (xs == 1) & (ys > 1) & (ys < case.ny - 2)
     assert mid.any() and np.all(nx_[mid] == 1.0) and np.all(ny_[mid] == 0.0)
+
+
+def _welch_beta(St):
+    from scipy import optimize, special
+
+    return optimize.brentq(lambda b: b * np.exp(b * b) * special.erf(b) - St / np.sqrt(np.pi), 1e-9, 5.0,
+                           xtol=1e-14)
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("Tr,dT", [(0.86, 0.010), (0.86, 0.023), (0.90, 0.010)])
+def test_stefan_film_grows_as_welch(Tr, dT):
+    # Sec. III.E with the readings of the workloads: G = -2 (sigma = 0.38 at Maxwell coexistence),
+    # alpha_v = 0.1, a vapour-wetting wall (rho_s = rho_v), a liquid diffusivity a tenth of the
+    # vapour's (the paper states only alpha_v), a 15-node initial film (5 nodes are about one
+    # interface width and do not survive), outlet speed 0.2.  The film thickness y_i grows as
+    # 2 beta sqrt(alpha_v t); the paper's three cases land within 15% of Welch's beta.
+    from oracle.thermo import PR
+
+    eos = PR(3.0 / 49.0, 2.0 / 21.0, 1.0, 0.344)
+    Ts = Tr * eos.Tc
+    rv, rl, _ = eos.maxwell(Ts)
+    alpha_v = 0.1
+    c = si.Case(nx=101, ny=5, D=0.0, xc=0.0, yc=0.0, walls=1, a=3.0 / 49.0, G=-2.0, sigma=0.38, Tr_sat=Tr,
+                superheat_Tc=dT / eos.Tc, u_in=0.0, nu_l=1.5 * alpha_v, nu_ratio=1.0, Pr_v=1.5, Pr_l=15.0, U_out=0.2,
+                rho_s=rv, g=0.0, noise_amp=0.0, name="stefan")
+    x = np.arange(c.nx, dtype=float)
+    rho = np.tile(rv + (rl - rv) * 0.5 * (1.0 + np.tanh((x - 15.0) / 2.0)), (c.ny, 1))
+    o = Oracle(c, rho=rho, ux=np.zeros_like(rho), uy=np.zeros_like(rho))
+    mid = 0.5 * (rl + rv)
+    t, y = [], []
+    for k in range(20):
+        o.step(1000)
+        r = o.field("rho").mean(axis=0)
+        j = int(np.argmax(r[1:] > mid)) + 1
+        t.append((k + 1) * 1000.0)
+        y.append((j - 1) + (mid - r[j - 1]) / (r[j] - r[j - 1]) - 0.5)
+    slope = np.polyfit(t[6:], np.square(y[6:]), 1)[0]
+    beta = np.sqrt(slope / (4.0 * alpha_v))
+    beta_w = _welch_beta(11.0 * dT / eos.h_fg(Ts))
+    assert y[-1] > y[0] + 5.0  # the film grows
+    assert abs(beta / beta_w - 1.0) < 0.15, (beta, beta_w)
