@@ -32,6 +32,11 @@
  *   6. temperature, Eq. (energy): two-stage Runge-Kutta (Heun), third-order
  *      upwind convection, isotropic 24-neighbour gradient and Laplacian (Sec. II.C).
  * For n < warmup the force and steps 5-6 are skipped (Sec. IV.A).
+ *
+ * Also here: flat walls and a uniform body force (the Poiseuille and Stefan
+ * set-ups of Sec. III.C and III.E) and, with collision = 1, the single-rate BGK
+ * operator that Sec. III.B compares the CM collision with (K = omega I on the
+ * same equilibrium and forcing central moments, no consistency terms).
  */
 #define _USE_MATH_DEFINES
 #include <math.h>
