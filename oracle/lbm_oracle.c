@@ -88,6 +88,8 @@ typedef struct {
     int32_t collision;          /* 0: CM collision (Sec. II.A); 1: single-rate BGK on the same equilibrium
                                    and forcing, the comparison operator of Sec. III.B */
     int32_t reserved;
+    double wall_q;              /* link fraction of the links into a flat wall: the wall surface lies
+                                   wall_q of a link from the last fluid node (<= 0: 1/2, halfway) */
 } orc_params;
 
 typedef struct {
@@ -467,9 +469,12 @@ orc_t *orc_create(const orc_params *p, const double *rho0, const double *ux0, co
                 if (p->periodic_x) sx = wrap(sx, nx);
                 if (sx < 0 || sx >= nx) continue;
                 if (o->solid[sy * nx + sx]) {
-                    /* the flat wall's surface lies halfway between its column and the next */
+                    /* a flat wall's surface lies wall_q of a link from the fluid node (halfway by
+                     * default); a wall parallel to the lattice cuts every link into it at the same
+                     * fraction, diagonal links included */
                     int cyl = is_cylinder_xy(p, sx, sy);
-                    o->qlink[id * Q + i] = cyl ? link_fraction(p, x, y, -CX[i], -CY[i]) : 0.5;
+                    double qw = p->wall_q > 0.0 ? p->wall_q : 0.5;
+                    o->qlink[id * Q + i] = cyl ? link_fraction(p, x, y, -CX[i], -CY[i]) : qw;
                     touches = 1;
                     touches_cyl |= cyl;
                 }

@@ -30,6 +30,7 @@ class OrcParams(C.Structure):
         ("n_wall", C.c_int32), ("walls", C.c_int32), ("wall_dT", C.POINTER(C.c_double)),
         ("body_fx", C.c_double),
         ("collision", C.c_int32), ("reserved", C.c_int32),
+        ("wall_q", C.c_double),
     ]
 
 
@@ -144,7 +145,8 @@ def derive(case) -> tuple[OrcParams, Derived]:
         rho_s=case.rho_s if case.rho_s > 0 else rho_l,
         nu_l=nu_l, nu_v=nu_v, alpha_l=alpha_l, alpha_v=alpha_v, c_v=case.c_v,
         g=g, u_in=case.u_in, U_out=U_out, walls=int(getattr(case, "walls", 0)),
-        body_fx=float(getattr(case, "body_fx", 0.0)), collision=int(getattr(case, "collision", 0)))
+        body_fx=float(getattr(case, "body_fx", 0.0)), collision=int(getattr(case, "collision", 0)),
+        wall_q=float(getattr(case, "wall_q", 0.5)))
     knots = np.ascontiguousarray(getattr(case, "wall_dT", ()) or (), dtype=np.float64)
     if knots.size:
         p.n_wall = knots.size

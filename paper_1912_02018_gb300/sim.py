@@ -62,6 +62,9 @@ def _torch_allocator(torch, device, enabled):
 
 
 def _case_kwargs(case):
+    if getattr(case, "wall_q", 0.5) != 0.5:
+        raise ValueError("the CUDA library places flat walls halfway between the last fluid node and the wall "
+                         "(link fraction 1/2)")
     names = [k for k in _PARAM_DEFAULTS if hasattr(case, k)]
     params = {k: getattr(case, k) for k in names}
     if hasattr(case, "U_out"):

@@ -58,6 +58,7 @@ class Case:
     yc: float
     periodic_x: int = 0
     walls: int = 0  # flat walls: bit 0 the column x = 0 (heated, instead of the inlet), bit 1 the rows y = 0, ny-1
+    wall_q: float = 0.5  # flat walls' surface: this fraction of a link from the last fluid node
     body_fx: float = 0.0  # uniform body force along +x
     collision: int = 0  # 0: the central-moment collision; 1: single-rate BGK (the comparison operator)
     a: float = 2.0 / 49.0

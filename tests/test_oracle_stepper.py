@@ -320,10 +320,16 @@ def test_flat_interface_near_maxwell_with_the_default_interaction_strength():
 
 
 @pytest.mark.slow
-@pytest.mark.parametrize("G", [-1.0, -2.0])
-def test_laplace_law_pressure_jump_scales_as_inverse_radius(G):
-    def bubble(R, n=64, steps=5000):
-        c = periodic_case(n, G=G, sigma=0.38, energy=0, nu_l=0.1)
+def test_laplace_law_pressure_jump_is_linear_in_inverse_radius():
+    # Sec. III.D: static vapour bubbles of several radii in a periodic box; the pressure jump between
+    # the bulk inside and outside, p_EOS(rho_in) - p_EOS(rho_out), is proportional to 1/R.  Four radii
+    # (equimolar radius of the settled bubble); acceptance: a straight-line fit of dp against 1/R with
+    # R^2 >= 0.99 and an intercept within 5% of the largest dp.  Measured at the default G = -2:
+    # R^2 = 0.9998, intercept -3.8% (bubbles from R = 14 add a Tolman-like 1/R^2 part: -5.4%).
+    n, steps = 128, 16000
+
+    def bubble(R):
+        c = periodic_case(n, sigma=0.38, energy=0, nu_l=1.0 / 6.0)
         _, d = stepper.derive(c)
         y, x = np.mgrid[0:n, 0:n]
         r = np.hypot(x - n / 2 + 0.5, y - n / 2 + 0.5)
@@ -334,7 +340,12 @@ def test_laplace_law_pressure_jump_scales_as_inverse_radius(G):
         Reff = np.sqrt(((rout - f) / (rout - rin)).sum() / np.pi)
         return d.eos.p(rin, d.T_sat) - d.eos.p(rout, d.T_sat), Reff
 
-    (dp1, R1), (dp2, R2) = bubble(13), bubble(16)
-    assert dp1 > dp2 > 0
-    # Delta p * R = surface tension, the same for both radii
-    assert abs(dp1 * R1 / (dp2 * R2) - 1) < 0.1
+    res = np.array([bubble(R) for R in (20, 28, 36, 44)])
+    dp, Reff = res[:, 0], res[:, 1]
+    assert np.all(np.diff(dp) < 0) and np.all(dp > 0)
+    A = np.vstack([1.0 / Reff, np.ones_like(Reff)]).T
+    (slope, icpt), *_ = np.linalg.lstsq(A, dp, rcond=None)
+    pred = A @ np.array([slope, icpt])
+    r2 = 1.0 - ((dp - pred) ** 2).sum() / ((dp - dp.mean()) ** 2).sum()
+    assert r2 >= 0.99, (dp, Reff, r2)
+    assert abs(icpt) <= 0.05 * dp.max(), (dp, Reff, icpt)
