@@ -3,8 +3,9 @@
 
 A step is one full lattice update of the workload (pull-streaming with boundary
 substitutions, rho/psi, interaction force, CM collision, wall heat flux, two Runge-Kutta
-stages of the temperature equation).  Default workload: the paper-shaped single domain,
-1536 x 768 lattice, cylinder D = 96 at (384, 384), Re = 300, superheat 0.10 Tc, FP32.
+stages of the temperature equation).  Default workload: the largest single domain of the
+measurement plan, 2048 x 1024 lattice, cylinder D = 128 at (512, 512), Re = 30000, film-boiling
+superheat 0.20 Tc, FP32 (the 1536 x 768 paper-shaped domain is --workload paper_shaped).
 
   value      MLUPS over the K timed steps, inputs resident in HBM, L2 flushed (a 256 MB
              write) before every timed step; CUDA events on the library's stream.
@@ -14,7 +15,10 @@ stages of the temperature equation).  Default workload: the paper-shaped single 
   roofline   the dominant kernel's algorithmic bytes per launch / its mean event-timed
              duration, against the measured HBM copy bandwidth.
   adjoint    cost of the checkpointed adjoint window (512 x 256, D = 32, 500 steps,
-             checkpoint every 50) relative to the forward window.
+             checkpoint every 50) relative to the forward window, FP32 (adjoint) and FP64
+             (adjoint_f64) builds.
+  probe      the 8192 x 4096 roofline probe (step MLUPS and HBM fraction).
+  batch      the 64-domain boiling-curve sweep, batched against sequential contexts.
   cpu_baseline  the FP64 CPU oracle on a bounded number of steps of the same workload.
 
 --impl reference times that oracle alone (the reference arm for this method: the
@@ -172,6 +176,14 @@ def oracle_sample(case, budget_s: float, max_steps: int):
                       f"({dt:.2f} s)"}, dt / n * 1e3, n
 
 
+def workload_config(case, args) -> dict:
+    """The `config` of a bench line: the same keys for the GPU arm and the oracle (reference) arm."""
+    return {"workload": case.name, "nx": case.nx, "ny": case.ny, "D": case.D, "Re": case.Re,
+            "superheat_Tc": case.superheat_Tc, "G": case.G, "sigma": case.sigma, "storage": args.storage,
+            "psi": ["double-float (FP32 pairs)", "IEEE f64", "f32"][args.psi_mode],
+            "l2": "flushed (256 MB write) before every timed step", "parallelism": "replicas"}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -181,13 +193,55 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": cpu["value"], "unit": UNIT,
             "n_gpus": args.gpus, "steps": n, "warmup": args.warmup, "ms_per_step": ms_per_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": case.name, "nx": case.nx, "ny": case.ny,
-                                            "D": case.D, "Re": case.Re, "superheat_Tc": case.superheat_Tc,
-                                            "G": case.G, "sigma": case.sigma, "l2": "inputs larger than L2 (CPU run)"},
+            "data": "synthetic", "config": workload_config(case, args),
             "cpu_baseline": cpu,
             "e2e": {"value": cpu["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def batch_sweep_record(steps: int, warmup: int) -> dict:
+    """The 64-domain boiling-curve sweep batched (tuned tiles, CUDA graph) against the same
+    domains stepped one after another through their own contexts (MLUPS of each, CUDA events)."""
+    import torch
+
+    from paper_1912_02018_gb300 import Batch, Sim
+
+    cases = si.batch_sweep(64, seed=1)
+    nodes = sum(c.nx * c.ny for c in cases)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    b = Batch(cases)
+    variant = b.tune(2)
+    b.step(warmup)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    b.step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_b = e0.elapsed_time(e1)
+    b.sync()
+    b.close()
+    sims = [Sim.from_case(c) for c in cases]
+    for _ in range(warmup):
+        for s in sims:
+            s.step(1)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(steps):
+        for s in sims:
+            s.step(1)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_s = e0.elapsed_time(e1)
+    for s in sims:
+        s.sync()
+        s.close()
+    return {"workload": "sweep64_12Dx6D_D40-128_Re300_fp32", "domains": len(cases), "nodes": nodes,
+            "steps": steps, "warmup": warmup, "tile_variant": variant,
+            "batched_mlups": nodes * steps / (ms_b / 1e3) / 1e6, "batched_ms_per_step": ms_b / steps,
+            "sequential_mlups": nodes * steps / (ms_s / 1e3) / 1e6, "sequential_ms_per_step": ms_s / steps,
+            "speedup_vs_sequential": ms_s / ms_b}
 
 
 def run_batch(args):
@@ -252,11 +306,46 @@ def aggregate_mlups(nodes: int, steps: int, world: int, seconds: float) -> float
     return nodes * steps * world / seconds / 1e6
 
 
-def adjoint_cost(window=500, ckpt_every=50, spin_up=2000):
+def probe_record(args, steps: int = 10, warmup: int = 3) -> dict:
+    """The 8192 x 4096 roofline probe (D = 512, 33.5 M nodes, far larger than L2): step MLUPS and
+    the HBM fraction of the step's algorithmic bytes, per-kernel mean event times."""
+    import torch
+
+    from paper_1912_02018_gb300 import Sim
+
+    case = WORKLOADS["probe"]
+    nodes = case.nx * case.ny
+    sim = Sim.from_case(case, f64=False, storage=args.storage, psi_mode=args.psi_mode)
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        sim.step(1)
+    sim.sync()
+    sim.profile(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    sim.step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    sim.sync()
+    ms = e0.elapsed_time(e1)
+    prof = sim.profile_read()
+    sim.close()
+    peak, kind = measured_peaks()
+    gbs = STEP_ALG_BYTES * nodes * steps / (ms / 1e3) / 1e9
+    return {"workload": case.name, "nodes": nodes, "steps": steps, "warmup": warmup,
+            "mlups": nodes * steps / (ms / 1e3) / 1e6, "ms_per_step": ms / steps,
+            "step_alg_bytes_per_lup": STEP_ALG_BYTES, "achieved_gbs": gbs, "frac": gbs / peak,
+            "peak_kind": f"{kind} copy bandwidth",
+            "kernels_us": {k: v[1] / v[0] * 1e3 for k, v in prof.items() if v[0]},
+            "l2": "inputs (3.7 GB) far larger than L2; no flush"}
+
+
+def adjoint_cost(window=500, ckpt_every=50, spin_up=2000, f64=False):
     """Cost of the adjoint window against the forward steps it differentiates, on the
-    512 x 256 lattice, D = 32, Re = 300 (FP32 forward and adjoint fields, FP64 parameter
-    sums): forward = lbm_step over the window; adjoint = lbm_adjoint_window (its own
-    checkpointed forward pass, then segment recompute and reverse steps)."""
+    512 x 256 lattice, D = 32, Re = 300 (FP32 or, with f64, FP64 forward and adjoint fields;
+    FP64 parameter sums): forward = lbm_step over the window; adjoint = lbm_adjoint_window (its
+    own checkpointed forward pass, then segment recompute and reverse steps)."""
     import ctypes as C
 
     import torch
@@ -265,7 +354,7 @@ def adjoint_cost(window=500, ckpt_every=50, spin_up=2000):
     from paper_1912_02018_gb300 import _native as N
 
     case = si.ADJOINT
-    sim = Sim.from_case(case, f64=False).step(spin_up)
+    sim = Sim.from_case(case, f64=f64).step(spin_up)
     state = sim.get_state()
     stream = torch.cuda.current_stream()
     L = N.lib()
@@ -285,7 +374,8 @@ def adjoint_cost(window=500, ckpt_every=50, spin_up=2000):
         e[3].record(stream)
         torch.cuda.synchronize()
         fwd, adj = e[0].elapsed_time(e[1]), e[2].elapsed_time(e[3])
-        res = {"workload": case.name, "window": window, "ckpt_every": ckpt_every, "spin_up": spin_up,
+        res = {"workload": case.name, "precision": "f64" if f64 else "f32", "window": window,
+               "ckpt_every": ckpt_every, "spin_up": spin_up,
                "forward_ms": fwd, "adjoint_window_ms": adj, "reverse_ms": adj - fwd,
                "ratio": (adj - fwd) / fwd, "ratio_incl_forward": adj / fwd, "J": g.J,
                "dJ_dsuperheat": g.dJ_dsuperheat, "dJ_du_in": g.dJ_du_in,
@@ -389,10 +479,7 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": case.name, "nx": case.nx, "ny": case.ny, "D": case.D, "Re": case.Re,
-                   "superheat_Tc": case.superheat_Tc, "G": case.G, "sigma": case.sigma, "storage": args.storage,
-                   "psi": ["double-float (FP32 pairs)", "IEEE f64", "f32"][args.psi_mode],
-                   "l2": "flushed (256 MB write) before every timed step", "parallelism": "replicas"},
+        "config": workload_config(case, args),
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "peak_kind": f"{peak_kind} copy bandwidth",
                      "alg_bytes_per_launch": alg},
@@ -401,6 +488,11 @@ def run_ours(args):
     }
     if world == 1 and not args.no_adjoint:
         line["adjoint"] = adjoint_cost()
+        line["adjoint_f64"] = adjoint_cost(f64=True)
+    if world == 1 and args.workload == "precision" and not args.no_probe:
+        line["probe"] = probe_record(args)
+    if world == 1 and not args.no_batch:
+        line["batch"] = batch_sweep_record(steps=60, warmup=6)
     if world == 1 and not args.no_cpu_baseline:
         cpu, _, _ = oracle_sample(case, budget_s=args.cpu_seconds, max_steps=10 ** 6)
         line["cpu_baseline"] = cpu
@@ -416,9 +508,11 @@ def main():
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=50)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["sweep64"], default="paper_shaped")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["sweep64"], default="precision")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint-window cost measurement")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 64-domain batched-sweep record")
+    ap.add_argument("--no-probe", action="store_true", help="skip the 8192 x 4096 roofline-probe record")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--storage", default="f32", choices=("f32", "f64", "f16s"),
                     help="population storage of the FP32 build (shifted FP16: f - w rho_l)")

@@ -190,13 +190,18 @@ lbm_status lbm_reset_heat_flux(lbm_ctx *ctx);
 #define LBM_FIELD_T 8u
 #define LBM_FIELD_PSI 16u
 #define LBM_FIELD_SOLID 32u
+#define LBM_FIELD_FX 64u
+#define LBM_FIELD_FY 128u
 
 /*
  * Copy macroscopic fields, as double, into dst: one [ny][nx] plane per set bit of
  * mask, in increasing bit order.  rho and u are those of the last collision, psi
  * that of the last step, T the current temperature; solid nodes report rho_solid,
- * u = 0, T_w; SOLID is 1.0 on solid nodes.  bytes must be at least
- * popcount(mask) * nx * ny * 8.  dst_on_device: 1 if dst is device memory.
+ * u = 0, T_w; SOLID is 1.0 on solid nodes.  FX, FY: the force F = F_m + F_g (+ body_fx)
+ * the last collision applied (the interaction force of Eq. (interForce) and gravity along
+ * -x, Sec. IV.A), recomputed from the psi and rho it used, bit-equal to the collision's own;
+ * zero on solid nodes, before the first step and after a warm-up step (no force).  bytes
+ * must be at least popcount(mask) * nx * ny * 8.  dst_on_device: 1 if dst is device memory.
  * Synchronises.
  */
 lbm_status lbm_fields(lbm_ctx *ctx, uint32_t mask, void *dst, size_t bytes, int dst_on_device);
@@ -211,7 +216,10 @@ lbm_status lbm_get_state(lbm_ctx *ctx, double *f, double *T, double *side, int64
 /* Restore (any subset of) a checkpoint written by lbm_get_state; NULL keeps that part.
  * steps < 0 keeps the step counter.  Host doubles are converted to the storage type.
  * T at solid nodes is the wall temperature from then on: pass the values lbm_get_state
- * returned there to keep the wall created with the context. */
+ * returned there to keep the wall created with the context.  A restore also clears a latched
+ * fault (LBM_EUNSTABLE, LBM_ETIMEOUT) and the energy pass's per-launch heat-flux
+ * bookkeeping, so a context that reported one continues from the restored state; the
+ * running heat-flux statistics are kept (lbm_reset_heat_flux clears them). */
 lbm_status lbm_set_state(lbm_ctx *ctx, const double *f, const double *T, const double *side, int64_t steps);
 
 /*
@@ -226,6 +234,21 @@ lbm_status lbm_set_state_native(lbm_ctx *ctx, const void *f, const void *T, cons
 
 /* Derived constants and counters. */
 lbm_status lbm_info(lbm_ctx *ctx, lbm_info_t *info);
+
+/*
+ * Test hook for the bounded device waits (the paper has no counterpart).  The next lbm_step
+ * starves one pass: every tile of it that would be staged into shared memory by TMA arms its
+ * barrier with the expected byte count but issues no copy, waits a short bound (64 tries)
+ * that runs out, waits that bound once more and produces nothing.  No copy is ever in flight,
+ * and the context stays usable: the next synchronising call reports LBM_ETIMEOUT with the pass
+ * named in lbm_last_error, and lbm_set_state / lbm_set_state_native (which clear the latched
+ * fault bits and the heat-flux bookkeeping) restore a state to continue from.
+ * kind: LBM_FAULT_STARVE_COLLIDE or LBM_FAULT_STARVE_ENERGY.  LBM_EINVAL for another kind,
+ * LBM_ESTATE when the context stages no tile (environment LBM_TMA=0 at creation) or, for the
+ * energy pass, runs without the energy equation.
+ */
+typedef enum { LBM_FAULT_STARVE_COLLIDE = 1, LBM_FAULT_STARVE_ENERGY = 2 } lbm_fault;
+lbm_status lbm_inject_fault(lbm_ctx *ctx, int32_t kind);
 
 /*
  * Per-kernel timing with CUDA events on the context's stream.  lbm_profile(ctx, 1)
@@ -255,8 +278,14 @@ lbm_status lbm_batch_create(int32_t n, const lbm_domain *domains, const lbm_cyli
                             const lbm_allocator *alloc, void *cuda_stream, lbm_batch **out);
 /* Enqueue n >= 0 steps of every domain (asynchronous). */
 lbm_status lbm_batch_step(lbm_batch *b, int64_t n);
-/* Autotuner: time each tile-shape variant on steps_per_variant real steps (they advance
- * the simulation), keep the fastest; *variant (may be NULL) receives its index. */
+/* Autotuner: time each tile-shape variant twice, in two interleaved rounds of
+ * steps_per_variant real steps each (they advance the simulation: 2 x variants x
+ * steps_per_variant steps), keep the variant with the fastest round; *variant (may be NULL)
+ * receives its index.  The choice is cached per set of domains (their lattice, walls and
+ * cylinder, energy and multiphase switches), precision and device (name, compute capability,
+ * SM count) for the life of the process and, when the environment variable LBM_TUNE_CACHE
+ * names a file, in that file across processes; a set tuned before is given the cached choice
+ * without timing and without taking a step. */
 lbm_status lbm_batch_tune(lbm_batch *b, int32_t steps_per_variant, int32_t *variant);
 /* CUDA-graph replay on (1, default) or off (0). */
 lbm_status lbm_batch_graph(lbm_batch *b, int enable);

@@ -15,14 +15,15 @@ STATUS_NAMES = {0: "LBM_OK", -1: "LBM_EINVAL", -2: "LBM_ENOMEM", -3: "LBM_ECUDA"
                 -5: "LBM_ETIMEOUT", -6: "LBM_ESTATE"}
 LBM_STORE_F64, LBM_STORE_F32, LBM_STORE_F16S = 0, 1, 2
 STORAGE = {"f64": LBM_STORE_F64, "f32": LBM_STORE_F32, "f16s": LBM_STORE_F16S}
-FIELD_BITS = {"rho": 1, "ux": 2, "uy": 4, "T": 8, "psi": 16, "solid": 32}
+FIELD_BITS = {"rho": 1, "ux": 2, "uy": 4, "T": 8, "psi": 16, "solid": 32, "Fx": 64, "Fy": 128}
 
 # every symbol include/lbm.h declares
 EXPORTS = ("lbm_create", "lbm_step", "lbm_sync", "lbm_wall_heat_flux", "lbm_reset_heat_flux", "lbm_fields",
            "lbm_get_state", "lbm_set_state", "lbm_info", "lbm_profile", "lbm_profile_read", "lbm_last_error",
            "lbm_destroy", "lbm_wall_heat_flux_noalloc", "lbm_batch_create", "lbm_batch_step", "lbm_batch_tune",
            "lbm_batch_graph", "lbm_batch_domain", "lbm_batch_destroy", "lbm_adjoint_window", "lbm_adjoint_step",
-           "lbm_get_state_native", "lbm_set_state_native")
+           "lbm_get_state_native", "lbm_set_state_native", "lbm_inject_fault")
+LBM_FAULT_STARVE_COLLIDE, LBM_FAULT_STARVE_ENERGY = 1, 2
 
 
 class Domain(C.Structure):
@@ -98,6 +99,7 @@ def lib():
     L.lbm_get_state_native.argtypes = [vp, vp, vp, vp, C.POINTER(i64)]
     L.lbm_set_state_native.argtypes = [vp, vp, vp, vp, i64]
     L.lbm_info.argtypes = [vp, C.POINTER(Info)]
+    L.lbm_inject_fault.argtypes = [vp, C.c_int32]
     L.lbm_profile.argtypes = [vp, C.c_int]
     L.lbm_profile_read.argtypes = [vp, C.POINTER(C.c_char_p), C.POINTER(i64), dp, C.c_int32,
                                    C.POINTER(C.c_int32)]

@@ -1,7 +1,6 @@
 // FP64 instantiation of the step kernels: double populations and double arithmetic.
 // Built with --fmad=false so that every product and sum is rounded separately, in the
 // order the kernels spell out (the paper's equations term by term).
-#include "lbm_adjoint.cuh"
 #include "lbm_kernels.cuh"
 
 namespace lbm {
@@ -34,20 +33,6 @@ int batch_step_f64(int variant, const BatchDomain* doms, const int* mp, int np, 
     case 1: return kern::batch_step_impl<double, double, kPsiF64, 16, 8>(doms, mp, np, mc, nc, me, ne, cur, tcur, step, need_psi, hd, hm, nd, s);
     default: return kern::batch_step_impl<double, double, kPsiF64, 8, 8>(doms, mp, np, mc, nc, me, ne, cur, tcur, step, need_psi, hd, hm, nd, s);
   }
-}
-
-int adjoint_step_f64(const AdjArgs<double>& a, cudaStream_t s) { return adj::adjoint_step_impl<double>(a, s); }
-int adjoint_setup_f64() { return adj::adjoint_setup_impl<double>(); }
-int adjoint_aux_f64(int op, const Geo& g, const uint8_t* mask, const void* src, void* dst, cudaStream_t s) {
-  const dim3 blk(32, 8), grd((g.nx + 31) / 32, (g.ny + 7) / 8);
-  switch (op) {
-    case 0: adj::k_impose_wall<double><<<grd, blk, 0, s>>>(g, mask, static_cast<const double*>(src), static_cast<double*>(dst)); break;
-    case 1: adj::k_adj_wall_seed<double><<<grd, blk, 0, s>>>(g, mask, static_cast<const double*>(src), static_cast<double*>(dst)); break;
-    case 2: adj::k_dense_to_plane<double><<<grd, blk, 0, s>>>(g, static_cast<const double*>(src), static_cast<double*>(dst)); break;
-    case 3: adj::k_plane_to_dense<double><<<grd, blk, 0, s>>>(g, static_cast<const double*>(src), static_cast<double*>(dst)); break;
-    default: return -1;
-  }
-  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 
 }  // namespace lbm

@@ -53,12 +53,20 @@ struct Phys {
   PhysC<float> f;
   F2 a2, b2, R2, kappa2, invTc2, cs22, k2;
   F2 kR2, ka2, k32;  // k R, k a, k / 3 with k = 2 / (G cs^2): the double-float psi's folded constants
+  F2 K12;            // 1 + kappa (the same)
   float dpdT_c1, dpdT_c2;  // kappa (1 + kappa) and kappa^2 / Tc: (dp/dT)_rho of the FP32 energy pass
   float pop_shift[9];  // shifted FP16 storage keeps f_i - w_i rho_l; these are w_i rho_l
 };
 
 // psi evaluation of the FP32 build (Eq. potential with Eq. eos); values of lbm_params.psi_mode.
 enum PsiMode { kPsiDF = 0, kPsiF64 = 1, kPsiF32 = 2 };
+// Launch flags of the single-domain collision and energy passes: bit 0 stage interior tiles by
+// TMA; bit 1 (test hook) arm each staged tile's barrier without issuing its copies and wait a
+// short bound, so that the bounded wait runs out with nothing in flight.
+constexpr int kLaunchStaged = 1, kLaunchStarve = 2;
+// Which pass lbm_inject_fault starves; latched status bits of a wait that ran out, per pass.
+constexpr int kStarveCollide = 1, kStarveEnergy = 2;
+constexpr int kStatusTimeoutCollide = 4, kStatusTimeoutEnergy = 8;
 // Collision operator (the values of lbm_collision): the CM collision of Sec. II.A, or the
 // single-rate BGK operator of the Sec. III.B comparison.
 enum CollisionOp { kCollCM = 0, kCollBGK = 1 };
@@ -79,6 +87,7 @@ struct Dev {
   const double* bn;  // their outward normals, [2][nb]
   int nb;
   int tma;           // 1: interior collision tiles are staged by TMA (environment LBM_TMA=0 turns it off)
+  int starve;        // test hook for the bounded waits (lbm_inject_fault): kStarve* bits of the next step
   int collision;     // LBM_COLL_CM or LBM_COLL_BGK
   double* hf;        // heat-flux accumulators: last, sum, sum of squares, count
   double* partial;   // one heat-flux partial sum per energy-kernel block (zero between launches)
@@ -183,8 +192,9 @@ int step_f32(const Geo& g, const Phys& ph, const Dev& d, int cur, int tcur, int 
              int storage, cudaStream_t s, const LaunchHook* hook, int* t_flipped, PsiChain* chain = nullptr);
 
 // Field export: copy a typed [ny][pitch] field (which: 0 rho, 1 ux, 2 uy, 3 T, 4 psi, 5 solid,
-// 10+i population plane i of buffer cur, 20+j outlet side row j of buffer cur) into a dense
-// double buffer.  T is taken from buffer tcur.
+// 10+i population plane i of buffer cur, 20+j outlet side row j of buffer cur, 30 + comp + 2 *
+// forcing the force component comp of the last collision) into a dense double buffer.  T is
+// taken from buffer tcur.
 int export_f64(const Geo& g, const Phys& ph, const Dev& d, int cur, int tcur, int which, double* dst, cudaStream_t s);
 int export_f32(const Geo& g, const Phys& ph, const Dev& d, int cur, int tcur, int which, int storage, double* dst,
                cudaStream_t s);

@@ -150,38 +150,82 @@ __device__ __forceinline__ C ldf(const Geo& g, const Phys& ph, const S* __restri
 }
 
 // ---------------------------------------------------------------- double-float arithmetic
-// Error-free transformations (Knuth's TwoSum, Dekker's FastTwoSum, FMA-based TwoProd) and
-// double-word operations after Joldes, Muller and Popescu, "Tight and rigorous error bounds
-// for basic building blocks of double-word arithmetic" (ACM TOMS 2017): about 2^-44
-// relative accuracy on the FP32 pipes.
+// A double-float value is a pair (hi, lo) of FP32 words standing for the real number hi + lo.
+// Building blocks: Knuth's TwoSum and Dekker's FastTwoSum (error-free sums), the FMA-based
+// exact product, and products, sums and a quotient of pairs after Joldes, Muller and Popescu,
+// "Tight and rigorous error bounds for basic building blocks of double-word arithmetic" (ACM
+// TOMS 2017), here in their cheapest forms: results are left unnormalised (|lo| a few ulps of
+// hi, never renormalised by a FastTwoSum), the lo * lo term of a product is dropped, and a
+// difference uses FastTwoSum of the high words where the order of the operands is known.
+// Square roots and the quotient start from the FP32 approximations (rsqrt.approx, rcp.approx)
+// and take one correction from an exact residual (Karp and Markstein, "High-precision division
+// and square root", ACM TOMS 1997).  Each result carries about 2^-44 relative error.
 struct DF {
   float hi, lo;
 };
-__device__ __forceinline__ DF two_sum(float a, float b) {
-  float s = __fadd_rn(a, b);
-  float bb = __fsub_rn(s, a);
-  float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-  return {s, e};
-}
-__device__ __forceinline__ DF fast_two_sum(float a, float b) {
-  float s = __fadd_rn(a, b);
-  return {s, __fsub_rn(b, __fsub_rn(s, a))};
-}
-__device__ __forceinline__ DF two_prod(float a, float b) {
-  float p = __fmul_rn(a, b);
-  return {p, __fmaf_rn(a, b, -p)};
-}
-__device__ __forceinline__ DF df_neg(DF a) { return {-a.hi, -a.lo}; }
-__device__ __forceinline__ DF df_mul(DF a, DF b) {
-  DF c = two_prod(a.hi, b.hi);
-  float t = __fmaf_rn(a.lo, b.hi, __fmul_rn(a.hi, b.lo));
-  return fast_two_sum(c.hi, __fadd_rn(c.lo, t));
-}
-__device__ __forceinline__ DF df_mulf(DF a, float b) {
-  DF c = two_prod(a.hi, b);
-  return fast_two_sum(c.hi, __fmaf_rn(a.lo, b, c.lo));
-}
 __device__ __forceinline__ DF df_of(F2 v) { return {v.hi, v.lo}; }
+__device__ __forceinline__ DF df_neg(DF a) { return {-a.hi, -a.lo}; }
+__device__ __forceinline__ float rcp_approx(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float rsqrt_approx(float x) {
+  float r;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+// a * f for an FP32 f
+__device__ __forceinline__ DF df_mulf(DF a, float f) {
+  const float p = __fmul_rn(a.hi, f);
+  return {p, __fmaf_rn(a.lo, f, __fmaf_rn(a.hi, f, -p))};
+}
+__device__ __forceinline__ DF df_mul(DF a, DF b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  return {p, __fmaf_rn(a.lo, b.hi, e)};
+}
+__device__ __forceinline__ DF df_sqr(DF a) {
+  const float p = __fmul_rn(a.hi, a.hi);
+  return {p, __fmaf_rn(__fadd_rn(a.hi, a.hi), a.lo, __fmaf_rn(a.hi, a.hi, -p))};
+}
+// c - a where |c.hi| >= |a.hi| (FastTwoSum of the high words)
+__device__ __forceinline__ DF df_csub(DF c, DF a) {
+  const float s = __fsub_rn(c.hi, a.hi);
+  const float t = __fsub_rn(__fsub_rn(c.hi, s), a.hi);
+  return {s, __fadd_rn(t, __fsub_rn(c.lo, a.lo))};
+}
+// c - a for an FP32 c with |c| >= |a.hi|
+__device__ __forceinline__ DF df_fsub(float c, DF a) {
+  const float s = __fsub_rn(c, a.hi);
+  const float t = __fsub_rn(__fsub_rn(c, s), a.hi);
+  return {s, __fsub_rn(t, a.lo)};
+}
+// a + b for any magnitudes (TwoSum of the high words)
+__device__ __forceinline__ DF df_add(DF a, DF b) {
+  const float s = __fadd_rn(a.hi, b.hi);
+  const float bb = __fsub_rn(s, a.hi);
+  const float t = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b.hi, bb));
+  return {s, __fadd_rn(t, __fadd_rn(a.lo, b.lo))};
+}
+// a / b: q1 = a.hi / b.hi from the approximate reciprocal, then the exact remainder
+// a - b q1 (a.hi - b.hi q1 is exact by Sterbenz's lemma) divided once more
+__device__ __forceinline__ DF df_div(DF a, DF b) {
+  const float r = rcp_approx(b.hi);
+  const float q1 = __fmul_rn(a.hi, r);
+  const float p = __fmul_rn(b.hi, q1);
+  const float e = __fmaf_rn(b.lo, q1, __fmaf_rn(b.hi, q1, -p));
+  const float d = __fadd_rn(__fsub_rn(a.hi, p), __fsub_rn(a.lo, e));
+  return {q1, __fmul_rn(d, r)};
+}
+// sqrt(a): s = a.hi rsqrt(a.hi), corrected by (a - s^2) / (2 s) with the residual from one fma
+__device__ __forceinline__ DF df_sqrt(DF a) {
+  const float r = rsqrt_approx(a.hi);
+  const float s = __fmul_rn(a.hi, r);
+  const float res = __fadd_rn(__fmaf_rn(-s, s, a.hi), a.lo);
+  return {s, __fmul_rn(res, __fmul_rn(0.5f, r))};
+}
 
 // ---------------------------------------------------------------- thermodynamics
 // Peng-Robinson EOS, Eq. (eos), and psi of Eq. (potential) in IEEE FP64.
@@ -196,43 +240,28 @@ __device__ __forceinline__ double psi_eos(const Phys& ph, double rho, double T, 
   rad = 2.0 * (p - rho * cs2) / (k.G * cs2);
   return sqrt(rad);
 }
-// The same in double-float arithmetic (inputs and result FP32), rearranged over one
-// denominator: with x = b rho and D = 1 + 2x - x^2 = 2 - (1 - x)^2,
-//   rad = rho [kR T D - ka phi rho (1 - x) - (k/3)(1 - x) D] / ((1 - x) D),  k = 2/(G cs^2)
-// (kR, ka, k/3 folded on the host), whose numerator has condition number ~2 over the
-// liquid-vapour range, so the cheaper double-word addition (Joldes et al., Alg. 5) keeps
-// ~2^-44 relative accuracy.  Square roots: the correctly rounded FP32 root s of the high word
-// and one Newton step s + (a - s^2) / (2s) with the residual from one fma (Karp and Markstein,
-// "High-precision division and square root", ACM TOMS 1997), which leaves ~2^-46.
-__device__ __forceinline__ DF df_add_s(DF a, DF b) {
-  DF s = two_sum(a.hi, b.hi);
-  return fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
-}
-__device__ __forceinline__ DF df_sub_s(DF a, DF b) { return df_add_s(a, df_neg(b)); }
-__device__ __forceinline__ DF df_div_s(DF a, DF b) {
-  float q1 = __fdividef(a.hi, b.hi);
-  DF r = df_sub_s(a, df_mulf(b, q1));
-  return fast_two_sum(q1, __fdividef(r.hi, b.hi));
-}
-__device__ __forceinline__ DF df_sqrt_newton(DF a) {
-  const float s = __fsqrt_rn(a.hi);
-  const float e = __fadd_rn(__fmaf_rn(-s, s, a.hi), a.lo);
-  return {s, __fdividef(e, __fmul_rn(2.0f, s))};
-}
+// The same in double-float arithmetic (inputs and result FP32), over one denominator: with
+// x = b rho and D = 1 + 2x - x^2 = 2 - (1 - x)^2,
+//   rad = rho [kR T D - ka phi rho (1 - x) - (k/3)(1 - x) D] / ((1 - x) D),  k = 2/(G cs^2),
+//   phi = (K1 - kappa sqrt(T/Tc))^2,  K1 = 1 + kappa
+// (kR, ka, k/3, K1 folded on the host).  The numerator has condition number ~2 over the
+// liquid-vapour range, so the cheap sums above keep the radicand within ~2^-42 of exact; psi
+// is then the correctly rounded FP32 value (checked on 20,000 sampled (rho, T) against a
+// 120-bit evaluation in a CPU emulation of these operations).  The FastTwoSum differences need
+// kappa sqrt(T/Tc) <= 1 + kappa (T <= 3.5 Tc) and b rho <= 1, which hold wherever Eq. (eos) is
+// defined on the lattice.
 __device__ __forceinline__ float psi_eos_df(const Phys& ph, float rho, float T, float& rad_hi) {
-  const DF one = {1.0f, 0.0f}, two = {2.0f, 0.0f};
-  DF sq = df_sqrt_newton(df_mulf(df_of(ph.invTc2), T));
-  DF s = df_add_s(one, df_mul(df_of(ph.kappa2), df_sub_s(one, sq)));
-  DF phi = df_mul(s, s);
-  DF omx = df_sub_s(one, df_mulf(df_of(ph.b2), rho));
-  DF D = df_sub_s(two, df_mul(omx, omx));
-  DF den = df_mul(omx, D);
-  DF A = df_mul(df_mulf(df_of(ph.kR2), T), D);
-  DF B = df_mul(df_mulf(df_mul(df_of(ph.ka2), phi), rho), omx);
-  DF num = df_sub_s(df_sub_s(A, B), df_mul(den, df_of(ph.k32)));
-  DF rad = df_div_s(df_mulf(num, rho), den);
+  const DF sq = df_sqrt(df_mulf(df_of(ph.invTc2), T));
+  const DF phi = df_sqr(df_csub(df_of(ph.K12), df_mul(df_of(ph.kappa2), sq)));
+  const DF omx = df_fsub(1.0f, df_mulf(df_of(ph.b2), rho));
+  const DF D = df_fsub(2.0f, df_sqr(omx));
+  const DF den = df_mul(omx, D);
+  const DF A = df_mul(df_mulf(df_of(ph.kR2), T), D);
+  const DF B = df_mul(df_mulf(df_mul(df_of(ph.ka2), phi), rho), omx);
+  const DF num = df_add(df_add(A, df_neg(B)), df_neg(df_mul(df_of(ph.k32), den)));
+  const DF rad = df_div(df_mulf(num, rho), den);
   rad_hi = rad.hi;
-  const DF r = df_sqrt_newton(rad);
+  const DF r = df_sqrt(rad);
   return __fadd_rn(r.hi, r.lo);
 }
 // The same in plain FP32.
@@ -723,7 +752,8 @@ __device__ __forceinline__ void collide_tile(const Geo& g, const Phys& ph, const
                                              const uint8_t* __restrict__ mask, const C* __restrict__ side_in,
                                              C* __restrict__ side_out, C* __restrict__ rho_o, C* __restrict__ ux_o,
                                              C* __restrict__ uy_o, int forcing, int* status, int bx, int by,
-                                             const CUtensorMap* tm_f = nullptr, const CUtensorMap* tm_psi = nullptr) {
+                                             const CUtensorMap* tm_f = nullptr, const CUtensorMap* tm_psi = nullptr,
+                                             bool starve = false) {
   using CS = CollStage<C, S, CTY>;
   constexpr int HX = CS::PW, HY = CS::PH;
   __shared__ __align__(128) S s_f[9 * CS::FH * CS::FW];
@@ -740,8 +770,10 @@ __device__ __forceinline__ void collide_tile(const Geo& g, const Phys& ph, const
     if (tid == 0) {
       const uint32_t bytes = sizeof(S) * 9 * CS::FH * CS::FW + (need_psi ? sizeof(C) * HX * HY : 0);
       tma::bar_expect_tx(&s_bar, bytes);
-      tma::load_3d(s_f, tm_f, &s_bar, x0 - CS::XA, y0 - 1, 0);
-      if (need_psi) tma::load_2d(s_psi, tm_psi, &s_bar, x0 - CS::PA, y0 - 2);
+      if (!starve) {  // the test hook leaves the barrier armed with no copy issued
+        tma::load_3d(s_f, tm_f, &s_bar, x0 - CS::XA, y0 - 1, 0);
+        if (need_psi) tma::load_2d(s_psi, tm_psi, &s_bar, x0 - CS::PA, y0 - 2);
+      }
     }
   } else if (need_psi) {
     psi_tile_plain<C, S, CTY>(g, psi, x0, y0, s_psi);
@@ -749,11 +781,12 @@ __device__ __forceinline__ void collide_tile(const Geo& g, const Phys& ph, const
   }
   const bool inside = x < g.nx && y < g.ny;
   const uint8_t m = inside ? mask[y * g.pitch + x] : kSolid;
-  if (staged && !tma::bar_wait(&s_bar, 0, tma::kWaitTries)) {
+  const int tries = starve ? tma::kStarveTries : tma::kWaitTries;
+  if (staged && !tma::bar_wait(&s_bar, 0, tries)) {
     // the copies did not land in time: report it, give them a second bound to land before the
     // block's shared memory is released, and produce nothing
-    if (tid == 0) atomicOr(status, 4);
-    tma::bar_wait(&s_bar, 0, tma::kWaitTries);
+    if (tid == 0) atomicOr(status, kStatusTimeoutCollide);
+    tma::bar_wait(&s_bar, 0, tries);
     return;
   }
   if (!inside) return;
@@ -769,9 +802,11 @@ __global__ void __launch_bounds__(kCollTX* kCollTY, sizeof(C) == 4 ? 7 : 1)
     k_collide(Geo g, Phys ph, const S* __restrict__ f, S* __restrict__ fn, const C* __restrict__ psi,
               const uint8_t* __restrict__ mask, const C* __restrict__ side_in, C* __restrict__ side_out,
               C* __restrict__ rho_o, C* __restrict__ ux_o, C* __restrict__ uy_o, int forcing, int* status,
-              const __grid_constant__ CUtensorMap tm_f, const __grid_constant__ CUtensorMap tm_psi, int staged) {
+              const __grid_constant__ CUtensorMap tm_f, const __grid_constant__ CUtensorMap tm_psi, int flags) {
+  const bool staged = flags & kLaunchStaged;
   collide_tile<C, S, kCollTY, OP>(g, ph, f, fn, psi, mask, side_in, side_out, rho_o, ux_o, uy_o, forcing, status,
-                                  blockIdx.x, blockIdx.y, staged ? &tm_f : nullptr, staged ? &tm_psi : nullptr);
+                                  blockIdx.x, blockIdx.y, staged ? &tm_f : nullptr, staged ? &tm_psi : nullptr,
+                                  (flags & kLaunchStarve) != 0);
 }
 
 // ---------------------------------------------------------------- k_energy
@@ -1016,6 +1051,61 @@ __device__ __forceinline__ void energy_rhs_pair<float>(const Phys& ph, const flo
   L[1] = Lp.y;
 }
 
+// Density of the pulled populations, rho = sum_i f*_i(x - c_i), at the nodes (x0, y) and
+// (x0 + 1, y), x0 even, for a pair none of whose pulls crosses the lattice edge or meets the
+// wall (1 <= x0, x0 + 2 <= nx - 1, 1 <= y <= ny - 2, no near-wall node): the planes with c_x = 0
+// are read as aligned vectors, the others as scalars, all from one base address; the sum runs
+// in the order i = 0..8, as in the general pull, so both give the same bits.
+template <typename S>
+struct PairLoad;
+template <>
+struct PairLoad<float> {
+  static __device__ __forceinline__ void ld(const float* q, float& a, float& b) {
+    const float2 v = *reinterpret_cast<const float2*>(q);
+    a = v.x, b = v.y;
+  }
+};
+template <>
+struct PairLoad<double> {
+  static __device__ __forceinline__ void ld(const double* q, double& a, double& b) {
+    const double2 v = *reinterpret_cast<const double2*>(q);
+    a = v.x, b = v.y;
+  }
+};
+template <>
+struct PairLoad<__half> {
+  static __device__ __forceinline__ void ld(const __half* q, __half& a, __half& b) {
+    const __half2 v = *reinterpret_cast<const __half2*>(q);
+    a = __low2half(v), b = __high2half(v);
+  }
+};
+template <typename C, typename S>
+__device__ __forceinline__ void pair_rho(const Geo& g, const Phys& ph, const S* __restrict__ f, int x0, int y,
+                                         C r[2]) {
+  const S* p = f + y * g.pitch + x0;
+  C v[9][2];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    const S* q = p + i * g.plane - cyv(i) * g.pitch - cxv(i);
+    S a, b;
+    if (cxv(i) == 0) {
+      PairLoad<S>::ld(q, a, b);
+    } else {
+      a = q[0];
+      b = q[1];
+    }
+    v[i][0] = PopIO<C, S>::ld(a, i, ph);
+    v[i][1] = PopIO<C, S>::ld(b, i, ph);
+  }
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    C t = v[0][k];
+#pragma unroll
+    for (int i = 1; i < 9; ++i) t = t + v[i][k];
+    r[k] = t;
+  }
+}
+
 // Heun stage 2 at the pair whose left node is (x, y), T^{n+1} = (T + T1 + L(T1)) / 2, from
 // shared tiles: inputs sT, sL, sU, sV, sR, sM (row stride ax, pair at index a) and the stage-1
 // temperature sT1 (row stride bx, pair at index b); fz: the pair's frozen parts.  Nodes with
@@ -1057,18 +1147,32 @@ __device__ __forceinline__ void stage2_pair(const Geo& g, const Phys& ph, const 
   }
   if constexpr (FUSE) {
     if (psi_out) {
+      const uint8_t m0 = sM[a], m1 = sM[a + 1];
+      C r[2];
+      // a pair away from the wall, the open edges and the periodic seams pulls from one base
+      // address; the others take the general pull with its boundary substitutions
+      if (!((m0 | m1) & kNearWall) && y >= 1 && y + 1 < g.ny && x0 >= 1 && x0 + 3 <= g.nx) {
+        pair_rho<C, S>(g, ph, fnew, x0, y, r);
+      } else {
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+          r[k] = C(0);
+          if (x0 + k < g.nx && y < ylim) {
+            C fo[9];
+            pull_node<C, S>(g, ph, fnew, mask, side_new, nullptr, x0 + k, y, k ? m1 : m0, fo);
+            C t = fo[0];
+#pragma unroll
+            for (int i = 1; i < 9; ++i) t = t + fo[i];
+            r[k] = t;
+          }
+        }
+      }
 #pragma unroll
       for (int k = 0; k < 2; ++k) {
         const int x = x0 + k;
         if (x < g.nx && y < ylim) {
-          const uint8_t m = sM[a + k];
-          C fo[9];
-          pull_node<C, S>(g, ph, fnew, mask, side_new, nullptr, x, y, m, fo);
-          C r = fo[0];
-#pragma unroll
-          for (int i = 1; i < 9; ++i) r = r + fo[i];
-          if (m & kSolid) r = pc<C>(ph).rho_s;
-          psi_out[y * g.pitch + x] = psi_of<C, PSI>(ph, r, tnew[k], status);
+          const C rho = ((k ? m1 : m0) & kSolid) ? pc<C>(ph).rho_s : r[k];
+          psi_out[y * g.pitch + x] = psi_of<C, PSI>(ph, rho, tnew[k], status);
         }
       }
     }
@@ -1131,11 +1235,13 @@ __device__ __forceinline__ void energy_tile(const Geo& g, const Phys& ph, const 
                                             int n_wall_tiles, int bx, int by, int bid, int nblocks,
                                             const S* __restrict__ fnew = nullptr, const C* __restrict__ side_new = nullptr,
                                             C* __restrict__ psi_out = nullptr, int* status = nullptr,
-                                            C* __restrict__ t1_out = nullptr, const EnergyMaps* maps = nullptr) {
+                                            C* __restrict__ t1_out = nullptr, const EnergyMaps* maps = nullptr,
+                                            bool starve = false) {
   constexpr int TX = EnergyTile<C, ETY>::TX, TY = EnergyTile<C, ETY>::TY, NT = EnergyTile<C, ETY>::NT;
   constexpr int H = 4, AX = TX + 2 * H, AY = TY + 2 * H;  // inputs: tile + 4
   constexpr int BX = TX + 4, BY = TY + 4;                 // stage 1: tile + 2
   static_assert(AX * AY * sizeof(C) % 128 == 0 && AX * sizeof(C) % 16 == 0, "TMA boxes of the input tile");
+  static_assert(AX % 4 == 0 && (AX * AY) % 4 == 0, "word-wise mask and float4 lambda staging");
   __shared__ __align__(128) C sT[AY * AX];
   __shared__ __align__(128) C sL[AY * AX];
   __shared__ __align__(128) C sRUV[3 * AY * AX];  // rho, u_x, u_y: the planes of one TMA box
@@ -1145,7 +1251,7 @@ __device__ __forceinline__ void energy_tile(const Geo& g, const Phys& ph, const 
   __shared__ uint64_t s_bar;
   __shared__ __align__(16) C sT1[BY * BX];
   __shared__ Frozen<C> sF[TX * TY];
-  __shared__ uint8_t sM[AY * AX];
+  __shared__ __align__(16) uint8_t sM[AY * AX];
   __shared__ double red[NT / 32];
   __shared__ int done_last;
   const int tid = threadIdx.x;
@@ -1159,18 +1265,36 @@ __device__ __forceinline__ void energy_tile(const Geo& g, const Phys& ph, const 
     __syncthreads();
     if (tid == 0) {
       tma::bar_expect_tx(&s_bar, 4 * AX * AY * sizeof(C));
-      tma::load_2d(sT, &maps->T, &s_bar, x0 - H, y0 - H);
-      tma::load_3d(sRUV, &maps->ruv, &s_bar, x0 - H, y0 - H, 0);
+      if (!starve) {  // the test hook leaves the barrier armed with no copy issued
+        tma::load_2d(sT, &maps->T, &s_bar, x0 - H, y0 - H);
+        tma::load_3d(sRUV, &maps->ruv, &s_bar, x0 - H, y0 - H, 0);
+      }
     }
-    for (int p = tid; p < AX * AY; p += NT) sM[p] = mask[(y0 + p / AX - H) * g.pitch + x0 + p % AX - H];
-    const bool landed = tma::bar_wait(&s_bar, 0, tma::kWaitTries);
+    // the mask as 32-bit words (x0 - 4 and the row pitch are multiples of 4 bytes)
+    for (int p = tid; p < (AX / 4) * AY; p += NT) {
+      const int r = p / (AX / 4), c = p - r * (AX / 4);
+      reinterpret_cast<uint32_t*>(sM)[p] =
+          *reinterpret_cast<const uint32_t*>(mask + (y0 + r - H) * g.pitch + x0 - H + 4 * c);
+    }
+    const int tries = starve ? tma::kStarveTries : tma::kWaitTries;
+    const bool landed = tma::bar_wait(&s_bar, 0, tries);
     if (__syncthreads_or(!landed)) {
       // a copy did not land in time: report it, let the copies land (bounded) and stop the tile
-      if (tid == 0) atomicOr(status, 4);
-      tma::bar_wait(&s_bar, 0, tma::kWaitTries);
+      // (a tile that holds wall nodes then misses its heat-flux partial; restoring a state with
+      // lbm_set_state resets that bookkeeping)
+      if (tid == 0) atomicOr(status, kStatusTimeoutEnergy);
+      tma::bar_wait(&s_bar, 0, tries);
       return;
     }
-    for (int p = tid; p < AX * AY; p += NT) sL[p] = lam_of(ph, sR[p]);
+    if constexpr (sizeof(C) == 4) {
+      for (int p = tid; p < AX * AY / 4; p += NT) {  // four nodes per thread
+        const float4 r4 = reinterpret_cast<const float4*>(sR)[p];
+        reinterpret_cast<float4*>(sL)[p] =
+            make_float4(lam_of(ph, r4.x), lam_of(ph, r4.y), lam_of(ph, r4.z), lam_of(ph, r4.w));
+      }
+    } else {
+      for (int p = tid; p < AX * AY; p += NT) sL[p] = lam_of(ph, sR[p]);
+    }
   } else {
     for (int p = tid; p < AX * AY; p += NT) {
       const int gx = x0 + p % AX - H, gy = y0 + p / AX - H;
@@ -1235,11 +1359,13 @@ __global__ void __launch_bounds__(EnergyTile<C>::NT, sizeof(C) == 4 ? (sizeof(S)
              const C* __restrict__ ux, const C* __restrict__ uy, const uint8_t* __restrict__ mask,
              double* partial, unsigned* counter, double* hf, int nb, int do_hf, int n_wall_tiles,
              const S* __restrict__ fnew, const C* __restrict__ side_new, C* __restrict__ psi_out, int* status,
-             C* __restrict__ t1_out, const __grid_constant__ EnergyMaps maps, int staged) {
+             C* __restrict__ t1_out, const __grid_constant__ EnergyMaps maps, int flags) {
   energy_tile<C, EnergyTile<C>::TY, S, PSI, true>(g, ph, Tin, Tout, rho, ux, uy, mask, partial, counter, hf, nb,
                                                    do_hf, n_wall_tiles, blockIdx.x, blockIdx.y,
                                                    blockIdx.y * gridDim.x + blockIdx.x, gridDim.x * gridDim.y, fnew,
-                                                   side_new, psi_out, status, t1_out, staged ? &maps : nullptr);
+                                                   side_new, psi_out, status, t1_out,
+                                                   (flags & kLaunchStaged) ? &maps : nullptr,
+                                                   (flags & kLaunchStarve) != 0);
 }
 
 // ---------------------------------------------------------------- batched passes
@@ -1448,6 +1574,40 @@ static __global__ void k_export_solid(Geo g, const uint8_t* __restrict__ mask, d
   dst[y * g.nx + x] = (mask[y * g.pitch + x] & kSolid) ? 1.0 : 0.0;
 }
 
+// Component comp (0: x, 1: y) of the force F = F_m + F_g (+ the body force) that the collision
+// applied at every node (Eq. interForce with gravity along -x, Sec. IV.A), recomputed from the
+// psi and rho that collision used with the same stencil code and roundings; zero on solid nodes
+// and when the step ran without forcing (warm-up).
+template <typename C>
+__global__ void k_export_force(Geo g, Phys ph, const C* __restrict__ psi, const C* __restrict__ rho,
+                               const uint8_t* __restrict__ mask, int forcing, int comp, double* __restrict__ dst) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y;
+  if (x >= g.nx || y >= g.ny) return;
+  const int id = y * g.pitch + x;
+  double out = 0.0;
+  if (forcing && !(mask[id] & kSolid)) {
+    const PhysC<C>& k = pc<C>(ph);
+    const C cs2 = C(1.0 / 3.0);
+    C Fmx = C(0), Fmy = C(0);
+    if (k.G != C(0)) {
+      C w[25];
+#pragma unroll
+      for (int r = 0; r < 5; ++r)
+#pragma unroll
+        for (int c = 0; c < 5; ++c) w[r * 5 + c] = psi[map_y(g, y + r - 2) * g.pitch + map_x(g, x + c - 2)];
+      C sx, sy;
+      grad_t(&w[12], 5, sx, sy);
+      Fmx = -k.G * cs2 * w[12] * sx;
+      Fmy = -k.G * cs2 * w[12] * sy;
+    }
+    C Fx = sub(Fmx, mul(sub(rho[id], k.rho_l), k.g));
+    if (k.body_fx != C(0)) Fx = add(Fx, k.body_fx);
+    out = comp == 0 ? (double)Fx : (double)Fmy;
+  }
+  dst[y * g.nx + x] = out;
+}
+
 template <typename C, typename S>
 __global__ void k_export_pop(Geo g, Phys ph, const S* __restrict__ src, int i, double* __restrict__ dst) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1510,12 +1670,13 @@ int step_impl(const Geo& g, const Phys& ph, const Dev& d, int cur, int tcur, int
   const bool staged = d.tma && tma::encode<S>(&tm_f, f, g.nx, g.ny, g.pitch, g.plane, 9, CS::FW, CS::FH) &&
                       tma::encode<C>(&tm_psi, psi, g.nx, g.ny, g.pitch, g.plane, 1, CS::PW, CS::PH);
   pre(kKCollide);
+  const int cflags = staged ? (kLaunchStaged | ((d.starve & kStarveCollide) ? kLaunchStarve : 0)) : 0;
   if (d.collision == kCollBGK)
     k_collide<C, S, kCollBGK><<<grd, blk, 0, s>>>(g, ph, f, fn, psi, d.mask, side_in, side_out, rho, ux, uy, forcing,
-                                                  d.status, tm_f, tm_psi, staged ? 1 : 0);
+                                                  d.status, tm_f, tm_psi, cflags);
   else
     k_collide<C, S><<<grd, blk, 0, s>>>(g, ph, f, fn, psi, d.mask, side_in, side_out, rho, ux, uy, forcing, d.status,
-                                        tm_f, tm_psi, staged ? 1 : 0);
+                                        tm_f, tm_psi, cflags);
   post(kKCollide);
   *t_flipped = 0;
   if (energy && forcing) {
@@ -1532,7 +1693,9 @@ int step_impl(const Geo& g, const Phys& ph, const Dev& d, int cur, int tcur, int
     k_energy<C, S, PSI><<<grd, blk, 0, s>>>(g, ph, T, Tn, rho, ux, uy, d.mask, d.partial, d.counter, d.hf, d.nb,
                                             do_hf, d.wall_tiles[ET::TY == 16 ? 1 : 0], fuse ? fn : nullptr,
                                             side_out, fuse ? static_cast<C*>(d.psi_next) : nullptr, d.status,
-                                            static_cast<C*>(d.t1_out), em, e_staged ? 1 : 0);
+                                            static_cast<C*>(d.t1_out), em,
+                                            e_staged ? (kLaunchStaged | ((d.starve & kStarveEnergy) ? kLaunchStarve : 0))
+                                                     : 0);
     post(kKEnergy);
     *t_flipped = 1;
     if (chain) chain->made = fuse ? 1 : 0;
@@ -1554,6 +1717,10 @@ int export_impl(const Geo& g, const Phys& ph, const Dev& d, int cur, int tcur, i
     k_export_pop<C, S><<<dim3((g.nx + 255) / 256, g.ny), blk, 0, s>>>(g, ph, src, which - 10, dst);
   } else if (which == 5) {
     k_export_solid<<<dim3((g.nx + 255) / 256, g.ny), blk, 0, s>>>(g, d.mask, dst);
+  } else if (which >= 30 && which < 34) {  // 30 + comp + 2 forcing: the force of the last collision
+    k_export_force<C><<<dim3((g.nx + 255) / 256, g.ny), blk, 0, s>>>(
+        g, ph, static_cast<const C*>(d.psi), static_cast<const C*>(d.rho), d.mask, (which - 30) >> 1, (which - 30) & 1,
+        dst);
   } else {
     const void* p = which == 0 ? d.rho : which == 1 ? d.ux : which == 2 ? d.uy : which == 3 ? d.T[tcur] : d.psi;
     k_export<C><<<dim3((g.nx + 255) / 256, g.ny), blk, 0, s>>>(g, static_cast<const C*>(p), g.pitch, g.ny, dst, g.nx);

@@ -61,6 +61,8 @@ __device__ __forceinline__ void load_3d(void* dst, const CUtensorMap* map, uint6
 // Tries of the bounded wait: each try blocks for a hardware-defined slice; a tile copy takes
 // a few microseconds, the bound a fraction of a second.
 constexpr int kWaitTries = 1 << 18;
+// The bound of a tile starved on purpose by the test hook (lbm_inject_fault).
+constexpr int kStarveTries = 64;
 
 template <typename E>
 struct DType;

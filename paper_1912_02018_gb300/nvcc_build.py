@@ -6,7 +6,8 @@ Translation units, compiled in parallel:
   lbm_api.cu  host side of the C ABI (-ffp-contract=off so host FP64 thermodynamics
               round the same on x86-64 and aarch64)
   lbm_noalloc.cu  the allocation-free wall heat flux
-  lbm_adjoint_api.cu  host side of the adjoint window (its kernels sit in the two precision units)
+  lbm_adjoint_api.cu  host side of the adjoint window (the FP32 reverse kernels sit in lbm_f32.cu)
+  lbm_adjoint_f64.cu  FP64 reverse kernels of the adjoint, FMA contraction allowed
 """
 from __future__ import annotations
 
@@ -32,6 +33,7 @@ UNITS = {
     "lbm_api.cu": [],
     "lbm_noalloc.cu": [],
     "lbm_adjoint_api.cu": [],
+    "lbm_adjoint_f64.cu": ["--fmad=true"],
 }
 
 

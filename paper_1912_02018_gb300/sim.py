@@ -283,6 +283,14 @@ class Sim:
         return {"f": fo, "T": To, "side": so, "Tw": dTw, "u_in": du.value}
 
     # ------------------------------------------------------------------ timing
+    def inject_fault(self, kind: str):
+        """Test hook of the bounded device waits: the next step starves the TMA-staged tiles of
+        one pass ("collide" or "energy"), whose short bounded waits then run out (LBM_ETIMEOUT at
+        the next synchronising call; set_state restores a state to continue from)."""
+        k = {"collide": N.LBM_FAULT_STARVE_COLLIDE, "energy": N.LBM_FAULT_STARVE_ENERGY}[kind]
+        self._chk(N.lib().lbm_inject_fault(self.h, k))
+        return self
+
     def profile(self, enable=True):
         self._chk(N.lib().lbm_profile(self.h, 1 if enable else 0))
 

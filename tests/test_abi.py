@@ -104,6 +104,7 @@ def test_invalid_parameters_are_rejected_on_the_host(lib, what):
 def test_null_handles_are_rejected(lib):
     assert lib.lbm_step(None, 1) == N.LBM_EINVAL
     assert lib.lbm_sync(None) == N.LBM_EINVAL
+    assert lib.lbm_inject_fault(None, N.LBM_FAULT_STARVE_COLLIDE) == N.LBM_EINVAL
     lib.lbm_destroy(None)
 
 

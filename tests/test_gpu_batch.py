@@ -79,12 +79,17 @@ def test_tuned_batch_keeps_results():
     from paper_1912_02018_gb300 import Batch
 
     b = Batch(CASES)
-    v = b.tune(2)  # 4 variants x 2 real steps
+    v = b.tune(2)  # 2 rounds x 4 variants x 2 real steps (none when the choice is cached)
     assert 0 <= v < 4
+    tuned = b.domain(0).info()["steps"]
+    assert tuned in (0, 16)
     b.step(12)
     # another tile height is another template instantiation: with FMA contraction allowed its
     # FP32 rounding may differ by an ulp, so the FP32 parity bar applies instead of bit equality
-    assert_same(b, singles(CASES, 20), hf_tol=1e-5, field_tol=1e-5)
+    assert_same(b, singles(CASES, tuned + 12), hf_tol=1e-5, field_tol=1e-5)
+    # the same set of domains is given the cached choice without timing or stepping
+    b2 = Batch(CASES)
+    assert b2.tune(2) == v and b2.domain(0).info()["steps"] == 0
 
 
 def test_fp64_batch_matches_oracle():

@@ -99,6 +99,43 @@ def test_fp32_parity_200_steps_plain_method_case():
     assert abs(hg["q_mean"] - hr["q_mean"]) <= 1e-3 * abs(hr["q_mean"])
 
 
+def test_force_planes_are_those_of_the_last_collision():
+    # lbm_fields' FX, FY: F_m of Eq. (interForce) from the psi the collision used, plus gravity
+    # (Sec. IV.A); the FP64 build against the oracle's force on the same psi and rho fields
+    from oracle import stepper
+
+    case = si.SMALL
+    sim = Sim().from_case(case, f64=True, init={"drho": case.drho()})
+    z = sim.fields(("Fx", "Fy"))
+    assert not z["Fx"].any() and not z["Fy"].any()  # no collision yet
+    sim.step(30)
+    got = sim.fields(("rho", "psi", "solid", "Fx", "Fy"))
+    fx, fy = stepper.interaction_force(case, got["psi"])
+    _, d = stepper.derive(case)
+    fx = fx - (got["rho"] - d.rho_l) * d.g
+    fluid = got["solid"] == 0
+    scale = np.hypot(fx, fy)[fluid].max()
+    assert scale > 0
+    assert np.abs(got["Fx"] - fx)[fluid].max() <= 1e-12 * scale
+    assert np.abs(got["Fy"] - fy)[fluid].max() <= 1e-12 * scale
+    assert not got["Fx"][~fluid].any() and not got["Fy"][~fluid].any()
+    # a warm-up step applies no force
+    warm = Sim().from_case(case.replace(warmup=5), f64=False).step(3)
+    w = warm.fields(("Fx", "Fy"))
+    assert not w["Fx"].any() and not w["Fy"].any()
+
+
+def test_fp32_parity_200_steps_on_mostly_staged_tiles():
+    # 512 x 256, D = 32, Re = 300: 82% of the collision tiles and 77% of the energy tiles are
+    # staged by TMA, so the staged interior code paths carry the 200-step FP32 bar
+    case = si.ADJOINT
+    sim, ref = pair(case, 200, False)
+    assert_fields(sim, ref, {"rho": 1e-5, "T": 1e-5}, names=("rho", "T"))
+    fluid = ref.field("solid") == 0
+    got = sim.fields(("psi",))
+    assert rel(got["psi"], ref.field("psi"), fluid) < 1e-5
+
+
 @pytest.mark.parametrize("storage,tol", [("f64", 1e-5), ("f16s", 2e-4)])
 def test_fp32_compute_with_other_population_storage(storage, tol):
     # FP32 arithmetic with populations stored as FP64 or as shifted FP16 (h = f - w rho_l)
