@@ -6,6 +6,7 @@
 // allocating.  Its only working memory is the file-scope array below: one (sum, count)
 // pair per thread block plus a completion counter.  Every GPU that loads the library
 // holds this array until the process exits.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -136,9 +137,39 @@ __global__ void __launch_bounds__(kThreads)
   }
 }
 
-// Per-device address of g_scratch, looked up once per device with that device current.
+// Per-device address of g_scratch, looked up once per device (and CUDA context) with that device current.
 std::mutex g_mu;
 double* g_addr[kMaxDevices] = {};
+unsigned long long g_ctx_id[kMaxDevices] = {};  // the CUDA context the address was looked up in
+
+// Unique id of the calling thread's current CUDA context (0 if it cannot be had): the driver's
+// cuCtxGetCurrent and cuCtxGetId, reached through the runtime's driver entry points.  A device
+// reset (cudaDeviceReset) destroys the primary context and unloads the library's device code,
+// so an address looked up in the old context is stale; the new context has a new id.
+unsigned long long current_ctx_id() {
+  using GetCurrent = CUresult (*)(CUcontext*);
+  using GetId = CUresult (*)(CUcontext, unsigned long long*);
+  static GetCurrent get_current = []() -> GetCurrent {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    return cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+                   q == cudaDriverEntryPointSuccess
+               ? reinterpret_cast<GetCurrent>(p)
+               : nullptr;
+  }();
+  static GetId get_id = []() -> GetId {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    return cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+                   q == cudaDriverEntryPointSuccess
+               ? reinterpret_cast<GetId>(p)
+               : nullptr;
+  }();
+  CUcontext ctx = nullptr;
+  unsigned long long id = 0;
+  if (get_current && get_id && get_current(&ctx) == CUDA_SUCCESS && ctx && get_id(ctx, &id) == CUDA_SUCCESS) return id;
+  return 0;
+}
 
 // Peng-Robinson EOS and Maxwell's equal-area rule at T, on the host (no allocation).
 struct Eos {
@@ -212,10 +243,13 @@ extern "C" lbm_status lbm_wall_heat_flux_noalloc(const lbm_domain* dom, const lb
   double* scratch;
   {
     std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_addr[dev]) {
+    // set-up, once per device and context: the device address of the scratch array
+    const unsigned long long id = g_addr[dev] ? current_ctx_id() : 0;
+    if (!g_addr[dev] || id != g_ctx_id[dev]) {
       void* p = nullptr;
       if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess) return LBM_ECUDA;
       g_addr[dev] = static_cast<double*>(p);
+      g_ctx_id[dev] = current_ctx_id();  // the lookup made the device's context current
     }
     scratch = g_addr[dev];
   }

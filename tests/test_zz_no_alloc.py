@@ -41,8 +41,10 @@ def _structs(N, case):
     return dom, cyl, prm
 
 
-@pytest.mark.parametrize("case", [si.SMALL, si.SMALL.replace(nx=96, ny=48, D=12.0, xc=24.3, yc=23.6, nu_ratio=2.0)],
-                         ids=["128x64_D16", "96x48_D12_offgrid"])
+@pytest.mark.parametrize("case", [si.SMALL, si.SMALL.replace(nx=96, ny=48, D=12.0, xc=24.3, yc=23.6, nu_ratio=2.0),
+                                  si.cylinder_case(1024, 512, 64.0, Re=300.0, superheat_Tc=0.1),
+                                  si.SMALL.replace(periodic_x=1)],
+                         ids=["128x64_D16", "96x48_D12_offgrid", "1024x512_D64_2048_tiles", "128x64_periodic_x"])
 def test_noalloc_heat_flux_matches_context_sample_on_two_calls(lib, case):
     import torch
 
