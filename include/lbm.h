@@ -360,7 +360,10 @@ lbm_status lbm_adjoint_step(lbm_ctx *ctx, const double *fb, const double *Tb, co
  * library keeps until the process exits: lattices above 8,388,608 nodes (more than
  * 32,768 tiles) are rejected with LBM_EINVAL, as are D <= 0 and nx or ny < 5.  The first
  * call on a device looks up that array's device address with the device current; make
- * that first call before any stream capture.  All calls share the one array, so calls
+ * that first call before any stream capture.  The address is kept with the id of the CUDA
+ * context it was looked up in: after a device reset (cudaDeviceReset), which unloads the
+ * library's device code, the next call on that device looks it up again (that call, too,
+ * belongs outside a stream capture).  All calls share the one array, so calls
  * whose kernels overlap on the GPU race; serialise them (one stream, or events).  The
  * call allocates nothing and is asynchronous; synchronise cuda_stream before reading
  * q_out.  LBM_ECUDA if a CUDA call fails; lbm_last_error does not apply (no context).

@@ -48,10 +48,14 @@ def cases():
 
 
 def run_batch(cs, steps, f64, chunk):
-    """Step the domains of cs together; returns one record per domain and the run's MLUPS."""
+    """Step the domains of cs together; returns one record per domain and the run's MLUPS.  Each
+    record carries the history of the wall heat flux: the mean of the samples of every chunk of
+    steps after the warm-up (from the running sums the library keeps)."""
     b = Batch(cs, f64=f64)
     first = cs[0].warmup + (steps - cs[0].warmup) // 2
     status = ["ok"] * len(cs)
+    hist = [[] for _ in cs]
+    last = [(0.0, 0) for _ in cs]  # running sum and count of the samples since the last reset
     t0 = time.perf_counter()
     done = 0
     while done < steps:
@@ -63,16 +67,21 @@ def run_batch(cs, steps, f64, chunk):
                 continue
             try:
                 d = b.domain(i)
-                d.sync()
+                hf = d.heat_flux()
+                tot, cnt = hf["q_mean"] * hf["count"], hf["count"]
+                if cnt > last[i][1]:
+                    hist[i].append([done, (tot - last[i][0]) / (cnt - last[i][1])])
+                last[i] = (tot, cnt)
                 if done == first:
                     d.reset_heat_flux()  # average over the second half of the run
+                    last[i] = (0.0, 0)
             except LbmError as e:
                 status[i] = f"unstable between steps {done - n} and {done}: {e}"
     b._torch.cuda.current_stream().synchronize()
     seconds = time.perf_counter() - t0
     out = []
     for i in range(len(cs)):
-        rec = {"Re": cs[i].Re, "superheat_Tc": cs[i].superheat_Tc, "status": status[i]}
+        rec = {"Re": cs[i].Re, "superheat_Tc": cs[i].superheat_Tc, "status": status[i], "q_history": hist[i]}
         if status[i] == "ok":
             hf = b.domain(i).heat_flux()
             rec.update(Nu_mean=hf["nu_mean"], q_mean=hf["q_mean"], q_std=hf["q_std"], samples=hf["count"])
@@ -82,7 +91,7 @@ def run_batch(cs, steps, f64, chunk):
     return out, nodes * steps / seconds / 1e6, seconds
 
 
-def run(steps, f64_cases=(), chunk=10000):
+def run(steps, f64_cases=(), chunk=5000):
     cs = cases()
     fp32, mlups, secs = run_batch(cs, steps, False, chunk)
     res = {"domain": [cs[0].nx, cs[0].ny], "D": cs[0].D, "steps": steps, "warmup": cs[0].warmup,
@@ -104,7 +113,7 @@ def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--steps", type=int, default=200000)
     ap.add_argument("--f64", type=int, nargs="*", default=[], help="case indices to repeat with the FP64 build")
-    ap.add_argument("--chunk", type=int, default=10000, help="steps between status checks")
+    ap.add_argument("--chunk", type=int, default=5000, help="steps between status checks (and heat-flux history points)")
     a = ap.parse_args()
     print(json.dumps(run(a.steps, tuple(a.f64), a.chunk)))
 

@@ -68,6 +68,12 @@ def interface_position(profile, mid):
     return (j - 1) + (mid - p[j - 1]) / (p[j] - p[j - 1]) - 0.5
 
 
+def initial_density(case, rv, rl, xi0=15.0, width=2.0):
+    """The film: rho_v at the wall rising to rho_l through a tanh of half-width `width` at xi0."""
+    x = np.arange(case.nx, dtype=np.float64)
+    return np.tile(rv + (rl - rv) * 0.5 * (1.0 + np.tanh((x - xi0) / width)), (case.ny, 1))
+
+
 def run(Tr=0.86, dT=0.010, steps=20000, every=500, xi0=15.0, width=2.0, f64=False, **kw):
     case = paper_case(Tr, dT, **kw)
     probe = Sim.from_case(SimpleNamespace(**{**vars(case), "rho_s": 0.0}), f64=f64)
@@ -76,8 +82,7 @@ def run(Tr=0.86, dT=0.010, steps=20000, every=500, xi0=15.0, width=2.0, f64=Fals
     rv, rl = info["rho_v"], info["rho_l"]
     if case.rho_s < 0:
         case.rho_s = rv
-    x = np.arange(case.nx, dtype=np.float64)
-    rho = np.tile(rv + (rl - rv) * 0.5 * (1.0 + np.tanh((x - xi0) / width)), (case.ny, 1))
+    rho = initial_density(case, rv, rl, xi0, width)
     sim = Sim.from_case(case, f64=f64, init={"rho": rho, "ux": np.zeros_like(rho), "uy": np.zeros_like(rho)})
     mid = 0.5 * (rl + rv)
     t, y = [], []
@@ -94,7 +99,8 @@ def run(Tr=0.86, dT=0.010, steps=20000, every=500, xi0=15.0, width=2.0, f64=Fals
     slope = float(np.polyfit(np.array(t[h:], float), np.array(y[h:]) ** 2, 1)[0]) if ok else float("nan")
     alpha_v = case.nu_l / case.Pr_v
     beta_num = math.sqrt(slope / (4.0 * alpha_v)) if slope > 0 else 0.0
-    return {"Tr": Tr, "dT": dT, "G": case.G, "rho_s": case.rho_s, "Pr_l": case.Pr_l, "U_out": case.U_out, "xi0": xi0,
+    return {"Tr": Tr, "dT": dT, "G": case.G, "rho_s": case.rho_s, "rho_v": rv, "rho_l": rl, "Pr_l": case.Pr_l,
+            "U_out": case.U_out, "xi0": xi0, "width": width,
             "h_fg": info["h_fg"], "beta_welch": beta, "beta_sim": beta_num, "t": t, "y_i": y, "seconds": seconds}
 
 

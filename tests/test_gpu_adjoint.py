@@ -231,7 +231,9 @@ def test_full_size_window_512x256_against_central_differences():
         fd = (_window_J(case.replace(wall_dT=tuple(p)), state, nw) -
               _window_J(case.replace(wall_dT=tuple(m)), state, nw)) / (2 * h)
         assert got["wall_dT"][k] == pytest.approx(fd, rel=1e-4), k
+    # the FP32 build: its forward J is 1.2e-4 from the FP64 one (wall temperature rounding over the
+    # window), and its gradients (measured 1.3e-4 to 2.2e-4 from the FP64 adjoint) inherit that
     a = out[False]
     errs = {k: abs(a[k] - got[k]) / abs(got[k]) for k in ("J", "superheat", "u_in")}
     errs["wall_dT"] = _rel(a["wall_dT"], got["wall_dT"])
-    assert max(errs.values()) < 1e-2, errs
+    assert max(errs.values()) < 5e-4, errs
