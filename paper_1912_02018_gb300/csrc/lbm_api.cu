@@ -557,6 +557,11 @@ lbm_status lbm_create(const lbm_domain* domain, const lbm_cylinder* cyl, const l
     const char* e = std::getenv("LBM_TMA");
     d.tma = (e && e[0] == '0' && e[1] == 0) ? 0 : 1;
   }
+  {
+    const char* e = std::getenv("LBM_PDL");
+    d.pdl = (e && e[0] == '0' && e[1] == 0) ? 0 : 1;
+  }
+  d.f_ready = 0;
   static_assert(lbm::kCollCM == LBM_COLL_CM && lbm::kCollBGK == LBM_COLL_BGK, "collision operator codes");
   d.collision = P.collision;
   int* dbn = static_cast<int*>(dalloc(c, sizeof(int) * (bnode.size() + 1)));
@@ -672,18 +677,24 @@ lbm_status lbm_step(lbm_ctx* c, int64_t n) {
   if (n < 0) return fail(c, LBM_EINVAL, "negative step count");
   lbm::LaunchHook hook{hook_before, hook_after, c};
   const lbm::LaunchHook* hk = c->prof ? &hook : nullptr;
+  int energy_last = 0;
   for (int64_t s = 0; s < n; ++s) {
     const int forcing = c->steps >= c->prm.warmup_steps;
     int flipped = 0;
     // psi of this step may already have been made by the last energy pass (into psi_next)
     if (c->psi_pending) std::swap(c->dev.psi, c->dev.psi_next);
     lbm::PsiChain chain{c->psi_pending, 1, 0};
+    // from the second step of a call on, the kernel before the collision is the last step's
+    // energy pass, which leaves the populations alone
+    c->dev.f_ready = s > 0 && energy_last;
     const int k = c->f64 ? lbm::step_f64(c->geo, c->ph, c->dev, c->cur, c->tcur, forcing, c->prm.energy,
                                          c->prm.psi_mode, c->stream, hk, &flipped, &chain)
                          : lbm::step_f32(c->geo, c->ph, c->dev, c->cur, c->tcur, forcing, c->prm.energy,
                                          c->prm.psi_mode, c->prm.storage, c->stream, hk, &flipped, &chain);
     c->psi_pending = chain.made;
     c->dev.starve = 0;  // the test hook of lbm_inject_fault covers one step
+    c->dev.f_ready = 0;
+    energy_last = flipped;
     if (k < 0) return fail(c, LBM_ECUDA, "kernel launch failed: %s", cudaGetErrorString(cudaGetLastError()));
     c->launches += k;
     c->cur ^= 1;

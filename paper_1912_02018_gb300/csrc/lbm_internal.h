@@ -64,6 +64,9 @@ enum PsiMode { kPsiDF = 0, kPsiF64 = 1, kPsiF32 = 2 };
 // TMA; bit 1 (test hook) arm each staged tile's barrier without issuing its copies and wait a
 // short bound, so that the bounded wait runs out with nothing in flight.
 constexpr int kLaunchStaged = 1, kLaunchStarve = 2;
+// The collision may copy its populations before the previous kernel in the stream has ended
+// (that kernel is the energy pass of the step before, which does not write them).
+constexpr int kLaunchEarlyF = 4;
 // Which pass lbm_inject_fault starves; latched status bits of a wait that ran out, per pass.
 constexpr int kStarveCollide = 1, kStarveEnergy = 2;
 constexpr int kStatusTimeoutCollide = 4, kStatusTimeoutEnergy = 8;
@@ -88,6 +91,10 @@ struct Dev {
   int nb;
   int tma;           // 1: interior collision tiles are staged by TMA (environment LBM_TMA=0 turns it off)
   int starve;        // test hook for the bounded waits (lbm_inject_fault): kStarve* bits of the next step
+  int pdl;           // 1: the step's passes are launched as programmatic dependents of the kernel
+                     // before them (environment LBM_PDL=0 turns it off)
+  int f_ready;       // 1: this step's populations were written before the kernel preceding its
+                     // collision (set by lbm_step for all but the first step of a call)
   int collision;     // LBM_COLL_CM or LBM_COLL_BGK
   double* hf;        // heat-flux accumulators: last, sum, sum of squares, count
   double* partial;   // one heat-flux partial sum per energy-kernel block (zero between launches)

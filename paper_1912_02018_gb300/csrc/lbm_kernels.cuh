@@ -30,6 +30,18 @@
 namespace lbm {
 namespace kern {
 
+// ---------------------------------------------------------------- programmatic dependent launch
+// A pass launched with the programmatic-stream-serialization attribute may start while the
+// kernel before it in the stream is still running (sm_90+).  wait(): the calling thread blocks
+// until that kernel has completed and its writes are visible; trigger(): once every block of
+// this pass has called it (or exited), the next such pass may start.  Both are no-ops in a
+// pass launched without the attribute.  A pass reads nothing the previous kernel writes, and
+// writes nothing at all, before wait().
+namespace pdl {
+__device__ __forceinline__ void wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+}  // namespace pdl
+
 // ---------------------------------------------------------------- lattice tables
 // D2Q9 velocities, Eq. (velVec).
 __device__ __forceinline__ constexpr int cxv(int i) {
@@ -753,7 +765,7 @@ __device__ __forceinline__ void collide_tile(const Geo& g, const Phys& ph, const
                                              C* __restrict__ side_out, C* __restrict__ rho_o, C* __restrict__ ux_o,
                                              C* __restrict__ uy_o, int forcing, int* status, int bx, int by,
                                              const CUtensorMap* tm_f = nullptr, const CUtensorMap* tm_psi = nullptr,
-                                             bool starve = false) {
+                                             bool starve = false, bool early_f = false) {
   using CS = CollStage<C, S, CTY>;
   constexpr int HX = CS::PW, HY = CS::PH;
   __shared__ __align__(128) S s_f[9 * CS::FH * CS::FW];
@@ -770,14 +782,22 @@ __device__ __forceinline__ void collide_tile(const Geo& g, const Phys& ph, const
     if (tid == 0) {
       const uint32_t bytes = sizeof(S) * 9 * CS::FH * CS::FW + (need_psi ? sizeof(C) * HX * HY : 0);
       tma::bar_expect_tx(&s_bar, bytes);
-      if (!starve) {  // the test hook leaves the barrier armed with no copy issued
-        tma::load_3d(s_f, tm_f, &s_bar, x0 - CS::XA, y0 - 1, 0);
-        if (need_psi) tma::load_2d(s_psi, tm_psi, &s_bar, x0 - CS::PA, y0 - 2);
-      }
+      // (the test hook leaves the barrier armed with no copy issued)
+      if (!starve && early_f) tma::load_3d(s_f, tm_f, &s_bar, x0 - CS::XA, y0 - 1, 0);
     }
-  } else if (need_psi) {
-    psi_tile_plain<C, S, CTY>(g, psi, x0, y0, s_psi);
-    __syncthreads();
+    pdl::wait();  // psi is the previous kernel's output
+    pdl::trigger();
+    if (tid == 0 && !starve) {
+      if (!early_f) tma::load_3d(s_f, tm_f, &s_bar, x0 - CS::XA, y0 - 1, 0);
+      if (need_psi) tma::load_2d(s_psi, tm_psi, &s_bar, x0 - CS::PA, y0 - 2);
+    }
+  } else {
+    pdl::wait();
+    pdl::trigger();
+    if (need_psi) {
+      psi_tile_plain<C, S, CTY>(g, psi, x0, y0, s_psi);
+      __syncthreads();
+    }
   }
   const bool inside = x < g.nx && y < g.ny;
   const uint8_t m = inside ? mask[y * g.pitch + x] : kSolid;
@@ -806,7 +826,7 @@ __global__ void __launch_bounds__(kCollTX* kCollTY, sizeof(C) == 4 ? 7 : 1)
   const bool staged = flags & kLaunchStaged;
   collide_tile<C, S, kCollTY, OP>(g, ph, f, fn, psi, mask, side_in, side_out, rho_o, ux_o, uy_o, forcing, status,
                                   blockIdx.x, blockIdx.y, staged ? &tm_f : nullptr, staged ? &tm_psi : nullptr,
-                                  (flags & kLaunchStarve) != 0);
+                                  (flags & kLaunchStarve) != 0, (flags & kLaunchEarlyF) != 0);
 }
 
 // ---------------------------------------------------------------- k_energy
@@ -1265,10 +1285,10 @@ __device__ __forceinline__ void energy_tile(const Geo& g, const Phys& ph, const 
     __syncthreads();
     if (tid == 0) {
       tma::bar_expect_tx(&s_bar, 4 * AX * AY * sizeof(C));
-      if (!starve) {  // the test hook leaves the barrier armed with no copy issued
-        tma::load_2d(sT, &maps->T, &s_bar, x0 - H, y0 - H);
-        tma::load_3d(sRUV, &maps->ruv, &s_bar, x0 - H, y0 - H, 0);
-      }
+      // T comes from the energy pass before the previous kernel (the collision, which does not
+      // write it): its copy starts before that kernel ends; the test hook leaves the barrier
+      // armed with no copy issued
+      if (!starve) tma::load_2d(sT, &maps->T, &s_bar, x0 - H, y0 - H);
     }
     // the mask as 32-bit words (x0 - 4 and the row pitch are multiples of 4 bytes)
     for (int p = tid; p < (AX / 4) * AY; p += NT) {
@@ -1276,6 +1296,9 @@ __device__ __forceinline__ void energy_tile(const Geo& g, const Phys& ph, const 
       reinterpret_cast<uint32_t*>(sM)[p] =
           *reinterpret_cast<const uint32_t*>(mask + (y0 + r - H) * g.pitch + x0 - H + 4 * c);
     }
+    pdl::wait();  // rho, u and the new populations are the collision's output
+    pdl::trigger();
+    if (tid == 0 && !starve) tma::load_3d(sRUV, &maps->ruv, &s_bar, x0 - H, y0 - H, 0);
     const int tries = starve ? tma::kStarveTries : tma::kWaitTries;
     const bool landed = tma::bar_wait(&s_bar, 0, tries);
     if (__syncthreads_or(!landed)) {
@@ -1296,6 +1319,8 @@ __device__ __forceinline__ void energy_tile(const Geo& g, const Phys& ph, const 
       for (int p = tid; p < AX * AY; p += NT) sL[p] = lam_of(ph, sR[p]);
     }
   } else {
+    pdl::wait();
+    pdl::trigger();
     for (int p = tid; p < AX * AY; p += NT) {
       const int gx = x0 + p % AX - H, gy = y0 + p / AX - H;
       const int nid = interior ? gy * g.pitch + gx : map_y(g, gy) * g.pitch + map_x(g, gx);
@@ -1635,6 +1660,22 @@ __global__ void k_import(Geo g, E* __restrict__ dst, int dst_pitch, int rows, co
 }  // namespace kern
 
 // ---------------------------------------------------------------- launchers
+// Launch kernel k on stream s, as a programmatic dependent of the kernel before it when pdl is set.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_dep(bool pdl, dim3 grd, dim3 blk, cudaStream_t s, void (*k)(KArgs...), Args&&... args) {
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grd;
+  cfg.blockDim = blk;
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cfg.attrs = at;
+  cfg.numAttrs = pdl ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, k, static_cast<Args&&>(args)...);
+}
+
 template <typename C, typename S, int PSI>
 int step_impl(const Geo& g, const Phys& ph, const Dev& d, int cur, int tcur, int forcing, int energy, cudaStream_t s,
               const LaunchHook* hook, int* t_flipped, PsiChain* chain) {
@@ -1670,13 +1711,15 @@ int step_impl(const Geo& g, const Phys& ph, const Dev& d, int cur, int tcur, int
   const bool staged = d.tma && tma::encode<S>(&tm_f, f, g.nx, g.ny, g.pitch, g.plane, 9, CS::FW, CS::FH) &&
                       tma::encode<C>(&tm_psi, psi, g.nx, g.ny, g.pitch, g.plane, 1, CS::PW, CS::PH);
   pre(kKCollide);
-  const int cflags = staged ? (kLaunchStaged | ((d.starve & kStarveCollide) ? kLaunchStarve : 0)) : 0;
+  const int cflags = staged ? (kLaunchStaged | ((d.starve & kStarveCollide) ? kLaunchStarve : 0) |
+                               ((d.pdl && d.f_ready) ? kLaunchEarlyF : 0))
+                            : 0;
   if (d.collision == kCollBGK)
-    k_collide<C, S, kCollBGK><<<grd, blk, 0, s>>>(g, ph, f, fn, psi, d.mask, side_in, side_out, rho, ux, uy, forcing,
-                                                  d.status, tm_f, tm_psi, cflags);
+    launch_dep(d.pdl, grd, blk, s, k_collide<C, S, kCollBGK>, g, ph, f, fn, psi, d.mask, side_in, side_out, rho, ux,
+               uy, forcing, d.status, tm_f, tm_psi, cflags);
   else
-    k_collide<C, S><<<grd, blk, 0, s>>>(g, ph, f, fn, psi, d.mask, side_in, side_out, rho, ux, uy, forcing, d.status,
-                                        tm_f, tm_psi, cflags);
+    launch_dep(d.pdl, grd, blk, s, k_collide<C, S, kCollCM>, g, ph, f, fn, psi, d.mask, side_in, side_out, rho, ux, uy,
+               forcing, d.status, tm_f, tm_psi, cflags);
   post(kKCollide);
   *t_flipped = 0;
   if (energy && forcing) {
@@ -1690,12 +1733,11 @@ int step_impl(const Geo& g, const Phys& ph, const Dev& d, int cur, int tcur, int
     const bool ruv = ux == rho + g.plane && uy == rho + 2 * (size_t)g.plane;  // consecutive planes
     const bool e_staged = d.tma && ruv && tma::encode<C>(&em.T, T, g.nx, g.ny, g.pitch, g.plane, 1, AX, AY) &&
                           tma::encode<C>(&em.ruv, rho, g.nx, g.ny, g.pitch, g.plane, 3, AX, AY);
-    k_energy<C, S, PSI><<<grd, blk, 0, s>>>(g, ph, T, Tn, rho, ux, uy, d.mask, d.partial, d.counter, d.hf, d.nb,
-                                            do_hf, d.wall_tiles[ET::TY == 16 ? 1 : 0], fuse ? fn : nullptr,
-                                            side_out, fuse ? static_cast<C*>(d.psi_next) : nullptr, d.status,
-                                            static_cast<C*>(d.t1_out), em,
-                                            e_staged ? (kLaunchStaged | ((d.starve & kStarveEnergy) ? kLaunchStarve : 0))
-                                                     : 0);
+    launch_dep(d.pdl, grd, blk, s, k_energy<C, S, PSI>, g, ph, T, Tn, rho, ux, uy, d.mask, d.partial, d.counter,
+               d.hf, d.nb, do_hf, d.wall_tiles[ET::TY == 16 ? 1 : 0], fuse ? static_cast<const S*>(fn) : nullptr,
+               static_cast<const C*>(side_out), fuse ? static_cast<C*>(d.psi_next) : nullptr, d.status,
+               static_cast<C*>(d.t1_out), em,
+               e_staged ? (kLaunchStaged | ((d.starve & kStarveEnergy) ? kLaunchStarve : 0)) : 0);
     post(kKEnergy);
     *t_flipped = 1;
     if (chain) chain->made = fuse ? 1 : 0;

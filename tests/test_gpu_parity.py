@@ -262,6 +262,34 @@ def test_tma_staged_and_plain_collision_tiles_agree_bitwise(monkeypatch, f64, st
     assert out["1"][2] == out["0"][2]
 
 
+@pytest.mark.parametrize("f64,storage", [(False, "f32"), (True, "f64"), (False, "f16s")])
+def test_dependent_launches_give_the_same_bits(monkeypatch, f64, storage):
+    # the collision and energy passes are launched as programmatic dependents of the kernel
+    # before them (from the second step of a call on, the collision copies its populations while
+    # the previous energy pass ends); LBM_PDL=0 (read at creation) launches them plainly: same
+    # bits through the warm-up (collisions back to back), the switch-on, one-step calls with reads
+    # in between, and a restore
+    case = si.Case(nx=1024, ny=384, D=48.0, xc=256.0, yc=192.0, Re=300.0, superheat_Tc=0.1, warmup=25,
+                   name="1024x384_D48")
+    out = {}
+    for flag in ("1", "0"):
+        monkeypatch.setenv("LBM_PDL", flag)
+        s = Sim().from_case(case, f64=f64, storage=storage).step(60)
+        mid = s.fields()
+        for _ in range(5):
+            s.step(1)
+        st = s.get_state_native()
+        s.step(30)
+        s.set_state_native(*st)
+        s.step(20)
+        out[flag] = (mid, s.fields(), s.get_state_native()[0], s.heat_flux()["q_mean"])
+    for k in FIELDS:
+        assert np.array_equal(out["1"][0][k], out["0"][0][k]), k
+        assert np.array_equal(out["1"][1][k], out["0"][1][k]), k
+    assert np.array_equal(out["1"][2], out["0"][2])
+    assert out["1"][3] == out["0"][3]
+
+
 def test_checkpoint_restart_is_bit_exact():
     case = si.SMALL
     drho = case.drho()
