@@ -9,11 +9,14 @@ superheat 0.20 Tc, FP32 (the 1536 x 768 paper-shaped domain is --workload paper_
 
   value      MLUPS over the K timed steps, inputs resident in HBM, L2 flushed (a 256 MB
              write) before every timed step; CUDA events on the library's stream.
-  e2e        the same metric through the C ABI with host buffers: each step restores the
-             state from pinned host memory (lbm_set_state_native, the context's own formats),
-             steps once and reads T back in its own format (lbm_get_state_native) plus the heat flux.
+  e2e        the same metric through the C ABI with host buffers: each step takes its state
+             from pinned host memory (the context's own formats; staged on the context's copy
+             stream while the step before runs, lbm_stage_state_native / lbm_take_staged),
+             steps once and reads T back in its own format (lbm_get_state_native) plus the heat
+             flux; sync_restore_value: the same with the synchronous lbm_set_state_native.
   roofline   the dominant kernel's algorithmic bytes per launch / its mean event-timed
-             duration, against the measured HBM copy bandwidth.
+             duration, against the measured HBM copy bandwidth (the kernels' durations come
+             from a second pass of the K steps with an event pair around every kernel).
   adjoint    cost of the checkpointed adjoint window (512 x 256, D = 32, 500 steps,
              checkpoint every 50) relative to the forward window, FP32 (adjoint) and FP64
              (adjoint_f64) builds.
@@ -109,7 +112,7 @@ def ncu_traffic(kernel: str, workload: str):
 
 
 class Clocks:
-    """nvidia-smi sampler (every 200 ms) for SM clock and throttle reasons."""
+    """nvidia-smi sampler (every 50 ms) for SM clock and throttle reasons."""
 
     Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
          "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
@@ -120,7 +123,7 @@ class Clocks:
         self.mark = None
         try:
             self.p = subprocess.Popen(["nvidia-smi", "-i", str(index), f"--query-gpu={self.Q}",
-                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                       "--format=csv,noheader,nounits", "-lms", "50"],
                                       stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -320,16 +323,19 @@ def probe_record(args, steps: int = 10, warmup: int = 3) -> dict:
     for _ in range(warmup):
         sim.step(1)
     sim.sync()
-    sim.profile(True)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    e0.record(stream)
-    sim.step(steps)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    sim.sync()
-    ms = e0.elapsed_time(e1)
+    ms = {}
+    for per_kernel in (False, True):  # the timed steps, then the same steps with per-kernel events
+        sim.profile(per_kernel)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        sim.step(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        sim.sync()
+        ms[per_kernel] = e0.elapsed_time(e1)
     prof = sim.profile_read()
+    ms = ms[False]
     sim.close()
     peak, kind = measured_peaks()
     gbs = STEP_ALG_BYTES * nodes * steps / (ms / 1e3) / 1e9
@@ -407,56 +413,82 @@ def run_ours(args):
         flush.zero_()
         sim.step(1)
     sim.sync()
+
+    def timed_steps(per_kernel):
+        # K steps, each after the L2 flush, one event pair per step on the library's stream;
+        # with per_kernel the library also brackets every kernel with an event pair
+        sim.profile(per_kernel)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        w0 = time.time()
+        for k in range(args.steps):
+            flush.zero_()
+            ev[k][0].record(stream)
+            sim.step(1)
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        w1 = time.time()
+        if world > 1:
+            dist.barrier()
+        sim.sync()
+        return sum(a.elapsed_time(b) for a, b in ev), w0, w1
+
+    # the timed region carries no per-kernel events: an event between the step's two passes
+    # costs time and stops the energy pass from starting while the collision ends
     launches0 = sim.info()["kernel_launches"]
-    sim.profile(True)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    t_wall0 = time.time()
-    for k in range(args.steps):
-        flush.zero_()
-        ev[k][0].record(stream)
-        sim.step(1)
-        ev[k][1].record(stream)
-    torch.cuda.synchronize()
-    t_wall1 = time.time()
-    if world > 1:
-        dist.barrier()
-    sim.sync()
-    ms = sum(a.elapsed_time(b) for a, b in ev)
+    ms, t_wall0, t_wall1 = timed_steps(False)
+    launches = sim.info()["kernel_launches"] - launches0
+    # per-kernel durations: the same K steps once more, every kernel between its own events
+    ms_k, _, _ = timed_steps(True)
     prof = sim.profile_read()
     sim.profile(False)
-    launches = sim.info()["kernel_launches"] - launches0
     ms = max_over_ranks(ms, world)
+    ms_k = max_over_ranks(ms_k, world)
     value = aggregate_mlups(nodes, args.steps, world, ms / 1e3)
 
-    # end to end through the C ABI with pinned host buffers: the state in the context's own
-    # formats (lbm_set_state_native), the new T read back in its own format too
+    # end to end through the C ABI with pinned host buffers: every step takes its state from
+    # host memory in the context's own formats and reads the new T back in its own format too,
+    # plus the heat flux.  The state of step i + 1 is staged (copied on the context's copy
+    # stream, lbm_stage_state_native) while step i runs, then swapped in (lbm_take_staged);
+    # e2e_sync repeats the loop with the synchronous restore (lbm_set_state_native)
     f0, T0, side0, n0 = sim.get_state_native()
     f_h = torch.from_numpy(f0).pin_memory()
     T_h = torch.from_numpy(T0).pin_memory()
     out_h = torch.empty_like(T_h).pin_memory()
-    import ctypes as C
-
     from paper_1912_02018_gb300 import _native as N
 
     L = N.lib()
-    e2e_steps = max(1, min(args.steps, 10))
-    torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
-    t = time.perf_counter()
-    for _ in range(e2e_steps):
-        N.check(L.lbm_set_state_native(sim.h, f_h.data_ptr(), T_h.data_ptr(), None, -1), sim.h)
-        N.check(L.lbm_step(sim.h, 1), sim.h)
-        N.check(L.lbm_get_state_native(sim.h, None, out_h.data_ptr(), None, None), sim.h)
-        sim.heat_flux()
-    e2e_s = time.perf_counter() - t
-    e2e_s = max_over_ranks(e2e_s, world)
+    e2e_steps = max(1, min(args.steps, 50))
+
+    def e2e_run(staged):
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        t = time.perf_counter()
+        if staged:
+            N.check(L.lbm_stage_state_native(sim.h, f_h.data_ptr(), T_h.data_ptr(), None, -1), sim.h)
+        for i in range(e2e_steps):
+            if staged:
+                N.check(L.lbm_take_staged(sim.h), sim.h)
+            else:
+                N.check(L.lbm_set_state_native(sim.h, f_h.data_ptr(), T_h.data_ptr(), None, -1), sim.h)
+            N.check(L.lbm_step(sim.h, 1), sim.h)
+            if staged and i + 1 < e2e_steps:
+                N.check(L.lbm_stage_state_native(sim.h, f_h.data_ptr(), T_h.data_ptr(), None, -1), sim.h)
+            N.check(L.lbm_get_state_native(sim.h, None, out_h.data_ptr(), None, None), sim.h)
+            sim.heat_flux()
+        return max_over_ranks(time.perf_counter() - t, world)
+
+    e2e_run(True)  # the first staging allocates the staging buffers
+    e2e_s = e2e_run(True)
+    e2e_sync_s = e2e_run(False)
     e2e = {"value": aggregate_mlups(nodes, e2e_steps, world, e2e_s), "unit": UNIT,
            "h2d_bytes_per_step": int(f_h.numel() * f_h.element_size() + T_h.numel() * T_h.element_size()),
-           "d2h_bytes_per_step": int(out_h.numel() * out_h.element_size() + 5 * 8), "steps": e2e_steps}
+           "d2h_bytes_per_step": int(out_h.numel() * out_h.element_size() + 5 * 8), "steps": e2e_steps,
+           "restore": "staged: step i + 1's state is copied on the context's copy stream while step i runs",
+           "sync_restore_value": aggregate_mlups(nodes, e2e_steps, world, e2e_sync_s)}
 
     if rank != 0:
         if world > 1:
@@ -485,6 +517,10 @@ def run_ours(args):
                      "alg_bytes_per_launch": alg},
         "step_roofline": {"alg_bytes_per_lup": step_bytes, "achieved_gbs": step_gbs, "frac": step_gbs / peak},
         "kernels": kernels, "gpu_launches": launches, "e2e": e2e, "clocks": clk,
+        "kernel_timing": {"steps": args.steps, "ms_per_step": ms_k / args.steps,
+                          "note": "kernels' event-timed durations come from a second pass of the same K flushed "
+                                  "steps with an event pair around every kernel (its per-step time here); the "
+                                  "timed region above has one event pair per step"},
     }
     if world == 1 and not args.no_adjoint:
         line["adjoint"] = adjoint_cost()
@@ -505,7 +541,7 @@ def run_ours(args):
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--steps", type=int, default=3000)
     ap.add_argument("--warmup", type=int, default=50)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["sweep64"], default="precision")

@@ -232,6 +232,26 @@ lbm_status lbm_set_state(lbm_ctx *ctx, const double *f, const double *T, const d
 lbm_status lbm_get_state_native(lbm_ctx *ctx, void *f, void *T, void *side, int64_t *steps);
 lbm_status lbm_set_state_native(lbm_ctx *ctx, const void *f, const void *T, const void *side, int64_t steps);
 
+/*
+ * Staged restore, for streaming states through one context (an ensemble kept in host memory,
+ * checkpoints replayed in turn): the copy of the next state runs while the context steps.
+ * lbm_stage_state_native starts copying a native-format state (the layouts and types of
+ * lbm_get_state_native; f and T required, side may be NULL to keep the outlet rows) from host
+ * memory into staging buffers of the context, on a copy stream of its own, and returns without
+ * waiting.  lbm_take_staged makes the last staged state the current one: the context's stream
+ * waits for that copy on the device (the host does not wait), the buffers are exchanged (no
+ * device copy), and the rules of lbm_set_state_native apply (steps >= 0 given at staging sets the
+ * step counter; a latched fault and the per-launch heat-flux bookkeeping are cleared).
+ * Pinned host memory makes the copy asynchronous; the host arrays must stay unchanged until a
+ * synchronising call that follows lbm_take_staged (lbm_sync, lbm_wall_heat_flux, lbm_fields,
+ * lbm_get_state*) has returned.  Staging again before a take replaces the staged state.  The
+ * first call allocates the staging buffers (9 population planes, one T plane, the outlet rows).
+ * Errors: LBM_EINVAL (null ctx, f or T), LBM_ESTATE (a batch's domain; take with nothing
+ * staged), LBM_ENOMEM, LBM_ECUDA.
+ */
+lbm_status lbm_stage_state_native(lbm_ctx *ctx, const void *f, const void *T, const void *side, int64_t steps);
+lbm_status lbm_take_staged(lbm_ctx *ctx);
+
 /* Derived constants and counters. */
 lbm_status lbm_info(lbm_ctx *ctx, lbm_info_t *info);
 

@@ -22,7 +22,8 @@ EXPORTS = ("lbm_create", "lbm_step", "lbm_sync", "lbm_wall_heat_flux", "lbm_rese
            "lbm_get_state", "lbm_set_state", "lbm_info", "lbm_profile", "lbm_profile_read", "lbm_last_error",
            "lbm_destroy", "lbm_wall_heat_flux_noalloc", "lbm_batch_create", "lbm_batch_step", "lbm_batch_tune",
            "lbm_batch_graph", "lbm_batch_domain", "lbm_batch_destroy", "lbm_adjoint_window", "lbm_adjoint_step",
-           "lbm_get_state_native", "lbm_set_state_native", "lbm_inject_fault")
+           "lbm_get_state_native", "lbm_set_state_native", "lbm_inject_fault", "lbm_stage_state_native",
+           "lbm_take_staged")
 LBM_FAULT_STARVE_COLLIDE, LBM_FAULT_STARVE_ENERGY = 1, 2
 
 
@@ -98,6 +99,8 @@ def lib():
     L.lbm_set_state.argtypes = [vp, vp, vp, vp, i64]
     L.lbm_get_state_native.argtypes = [vp, vp, vp, vp, C.POINTER(i64)]
     L.lbm_set_state_native.argtypes = [vp, vp, vp, vp, i64]
+    L.lbm_stage_state_native.argtypes = [vp, vp, vp, vp, i64]
+    L.lbm_take_staged.argtypes = [vp]
     L.lbm_info.argtypes = [vp, C.POINTER(Info)]
     L.lbm_inject_fault.argtypes = [vp, C.c_int32]
     L.lbm_profile.argtypes = [vp, C.c_int]

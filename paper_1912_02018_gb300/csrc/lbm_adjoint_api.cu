@@ -133,6 +133,9 @@ int forward_slot(lbm_ctx* c, lbm_adjoint_work* w, int j, cudaStream_t st) {
   v.hf = w->hf;
   v.nb = 0;  // the recompute needs no heat-flux sample
   v.t1_out = w->aT1[j];
+  // plain launches inside the segment's graph: programmatic dependent launch of its many small
+  // passes (512 x 256: one wave each) measured slower there
+  v.pdl = 0;
   int flipped = 0;
   lbm::PsiChain chain{j > 0 ? 1 : 0, 1, 0};
   const int k = c->f64 ? lbm::step_f64(c->geo, c->ph, v, 0, 0, 1, 1, c->prm.psi_mode, st, nullptr, &flipped, &chain)

@@ -844,6 +844,59 @@ lbm_status lbm_set_state_native(lbm_ctx* c, const void* f, const void* T, const 
   return native_io(c, const_cast<void*>(f), const_cast<void*>(T), const_cast<void*>(side), true);
 }
 
+lbm_status lbm_stage_state_native(lbm_ctx* c, const void* f, const void* T, const void* side, int64_t steps) {
+  if (!c || !f || !T) return LBM_EINVAL;
+  if (c->batch_owned) return fail(c, LBM_ESTATE, "this domain belongs to a batch");
+  const lbm::Geo& g = c->geo;
+  const size_t es = c->f64 ? sizeof(double) : sizeof(float);
+  const size_t ps = c->prm.storage == LBM_STORE_F64 ? 8 : (c->prm.storage == LBM_STORE_F16S ? 2 : 4);
+  const size_t N = (size_t)g.plane;
+  if (!c->copy_stream) {
+    c->stage_f = dalloc(c, 9 * N * ps);
+    c->stage_T = dalloc(c, N * es);
+    c->stage_side = dalloc(c, 3 * (size_t)g.ny * es);
+    if (!c->stage_f || !c->stage_T || !c->stage_side)
+      return fail(c, LBM_ENOMEM, "device allocation of the staging buffers failed");
+    // the pitch's padding columns are never read; zero them once all the same
+    LBM_CUDA(c, cudaMemsetAsync(c->stage_f, 0, 9 * N * ps, c->stream));
+    LBM_CUDA(c, cudaMemsetAsync(c->stage_T, 0, N * es, c->stream));
+    LBM_CUDA(c, cudaEventCreateWithFlags(&c->ev_copied, cudaEventDisableTiming));
+    LBM_CUDA(c, cudaEventCreateWithFlags(&c->ev_released, cudaEventDisableTiming));
+    LBM_CUDA(c, cudaEventRecord(c->ev_released, c->stream));  // after the zeroing
+    LBM_CUDA(c, cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
+  }
+  // the staging buffers may still be in use by work the context's stream had before the last take
+  LBM_CUDA(c, cudaStreamWaitEvent(c->copy_stream, c->ev_released, 0));
+  const size_t hpf = g.nx * ps, dpf = g.pitch * ps, hpt = g.nx * es, dpt = g.pitch * es;
+  LBM_CUDA(c, cudaMemcpy2DAsync(c->stage_f, dpf, f, hpf, hpf, 9 * (size_t)g.ny, cudaMemcpyHostToDevice,
+                                c->copy_stream));
+  LBM_CUDA(c, cudaMemcpy2DAsync(c->stage_T, dpt, T, hpt, hpt, g.ny, cudaMemcpyHostToDevice, c->copy_stream));
+  if (side)
+    LBM_CUDA(c, cudaMemcpyAsync(c->stage_side, side, 3 * (size_t)g.ny * es, cudaMemcpyHostToDevice, c->copy_stream));
+  LBM_CUDA(c, cudaEventRecord(c->ev_copied, c->copy_stream));
+  c->staged = side ? 2 : 1;
+  c->staged_steps = steps;
+  return LBM_OK;
+}
+
+lbm_status lbm_take_staged(lbm_ctx* c) {
+  if (!c) return LBM_EINVAL;
+  if (!c->staged) return fail(c, LBM_ESTATE, "no state is staged (lbm_stage_state_native)");
+  LBM_CUDA(c, cudaStreamWaitEvent(c->stream, c->ev_copied, 0));
+  lbm::Dev& d = c->dev;
+  // the staged buffers become the current state; the current ones become the staging buffers
+  std::swap(d.f[c->cur], c->stage_f);
+  std::swap(d.T[c->tcur], c->stage_T);
+  if (c->staged == 2) std::swap(d.side[c->cur], c->stage_side);
+  // everything the context's stream has so far may use the buffers now held for staging
+  LBM_CUDA(c, cudaEventRecord(c->ev_released, c->stream));
+  c->staged = 0;
+  c->psi_pending = 0;  // the state changes: psi of the next step is no longer known
+  clear_latched(c);
+  if (c->staged_steps >= 0) c->steps = c->staged_steps;
+  return LBM_OK;
+}
+
 lbm_status lbm_info(lbm_ctx* c, lbm_info_t* info) {
   if (!c || !info) return LBM_EINVAL;
   info->Tc = c->Tc;
@@ -925,6 +978,12 @@ const char* lbm_last_error(const lbm_ctx* c) { return c ? c->err.c_str() : g_cre
 void lbm_destroy(lbm_ctx* c) {
   if (!c || c->batch_owned) return;
   cudaStreamSynchronize(c->stream);
+  if (c->copy_stream) {
+    cudaStreamSynchronize(c->copy_stream);
+    cudaStreamDestroy(c->copy_stream);
+    cudaEventDestroy(c->ev_copied);
+    cudaEventDestroy(c->ev_released);
+  }
   for (auto& p : c->pending) {
     cudaEventDestroy(p.e0);
     cudaEventDestroy(p.e1);

@@ -52,6 +52,17 @@ struct lbm_ctx {
   std::vector<int> wall_node, wall_k0, wall_k1;  // wall_node: y * nx + x
   std::vector<double> wall_t;
   lbm_adjoint_work* adjw = nullptr;  // buffers of the adjoint window (created on first use)
+  // staged restores (lbm_stage_state_native / lbm_take_staged), made on first use: a copy
+  // stream, the staging buffers of f, T and the outlet rows, and two events: copied (the
+  // staged state has landed) and released (the context's stream no longer uses the buffers
+  // that became the staging buffers at the last take)
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t ev_copied = nullptr, ev_released = nullptr;
+  void* stage_f = nullptr;
+  void* stage_T = nullptr;
+  void* stage_side = nullptr;
+  int staged = 0;  // 0: nothing staged; else 1 + (1 if the outlet rows were staged)
+  int64_t staged_steps = -1;
 };
 
 namespace lbm {

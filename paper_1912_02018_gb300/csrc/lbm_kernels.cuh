@@ -1660,16 +1660,18 @@ __global__ void k_import(Geo g, E* __restrict__ dst, int dst_pitch, int rows, co
 }  // namespace kern
 
 // ---------------------------------------------------------------- launchers
-// Launch kernel k on stream s, as a programmatic dependent of the kernel before it when pdl is set.
+// Launch kernel k (smem bytes of dynamic shared memory) on stream s, as a programmatic dependent
+// of the kernel before it when pdl is set.
 template <typename... KArgs, typename... Args>
-cudaError_t launch_dep(bool pdl, dim3 grd, dim3 blk, cudaStream_t s, void (*k)(KArgs...), Args&&... args) {
+cudaError_t launch_dep(bool pdl, dim3 grd, dim3 blk, size_t smem, cudaStream_t s, void (*k)(KArgs...),
+                       Args&&... args) {
   cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
   at[0].val.programmaticStreamSerializationAllowed = 1;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = grd;
   cfg.blockDim = blk;
-  cfg.dynamicSmemBytes = 0;
+  cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
   cfg.attrs = at;
   cfg.numAttrs = pdl ? 1 : 0;
@@ -1715,10 +1717,10 @@ int step_impl(const Geo& g, const Phys& ph, const Dev& d, int cur, int tcur, int
                                ((d.pdl && d.f_ready) ? kLaunchEarlyF : 0))
                             : 0;
   if (d.collision == kCollBGK)
-    launch_dep(d.pdl, grd, blk, s, k_collide<C, S, kCollBGK>, g, ph, f, fn, psi, d.mask, side_in, side_out, rho, ux,
+    launch_dep(d.pdl, grd, blk, 0, s, k_collide<C, S, kCollBGK>, g, ph, f, fn, psi, d.mask, side_in, side_out, rho, ux,
                uy, forcing, d.status, tm_f, tm_psi, cflags);
   else
-    launch_dep(d.pdl, grd, blk, s, k_collide<C, S, kCollCM>, g, ph, f, fn, psi, d.mask, side_in, side_out, rho, ux, uy,
+    launch_dep(d.pdl, grd, blk, 0, s, k_collide<C, S, kCollCM>, g, ph, f, fn, psi, d.mask, side_in, side_out, rho, ux, uy,
                forcing, d.status, tm_f, tm_psi, cflags);
   post(kKCollide);
   *t_flipped = 0;
@@ -1733,7 +1735,7 @@ int step_impl(const Geo& g, const Phys& ph, const Dev& d, int cur, int tcur, int
     const bool ruv = ux == rho + g.plane && uy == rho + 2 * (size_t)g.plane;  // consecutive planes
     const bool e_staged = d.tma && ruv && tma::encode<C>(&em.T, T, g.nx, g.ny, g.pitch, g.plane, 1, AX, AY) &&
                           tma::encode<C>(&em.ruv, rho, g.nx, g.ny, g.pitch, g.plane, 3, AX, AY);
-    launch_dep(d.pdl, grd, blk, s, k_energy<C, S, PSI>, g, ph, T, Tn, rho, ux, uy, d.mask, d.partial, d.counter,
+    launch_dep(d.pdl, grd, blk, 0, s, k_energy<C, S, PSI>, g, ph, T, Tn, rho, ux, uy, d.mask, d.partial, d.counter,
                d.hf, d.nb, do_hf, d.wall_tiles[ET::TY == 16 ? 1 : 0], fuse ? static_cast<const S*>(fn) : nullptr,
                static_cast<const C*>(side_out), fuse ? static_cast<C*>(d.psi_next) : nullptr, d.status,
                static_cast<C*>(d.t1_out), em,

@@ -244,6 +244,34 @@ class Sim:
         self._chk(N.lib().lbm_set_state_native(self.h, *[a.ctypes.data if a is not None else None for a in keep],
                                                int(steps)))
 
+    def stage_state_native(self, f, T, side=None, steps=-1):
+        """Start copying a native-format state into the staging buffers (lbm_stage_state_native);
+        returns at once.  The arrays (numpy, or pinned CPU torch tensors for an asynchronous
+        copy) are kept referenced here until the next staging."""
+        fdt, tdt = self.native_dtypes()
+
+        def ptr(a, dt):
+            if a is None:
+                return None, None
+            if hasattr(a, "data_ptr"):  # a CPU torch tensor (pinned for an asynchronous copy)
+                if a.device.type != "cpu" or not a.is_contiguous() or a.element_size() != np.dtype(dt).itemsize:
+                    raise ValueError("expected a contiguous CPU tensor of the native type")
+                return a, a.data_ptr()
+            a = np.ascontiguousarray(a, dtype=dt)
+            return a, a.ctypes.data
+
+        kf, pf = ptr(f, fdt)
+        kT, pT = ptr(T, tdt)
+        ks, ps = ptr(side, tdt)
+        self._staged_keep = (kf, kT, ks)
+        self._chk(N.lib().lbm_stage_state_native(self.h, pf, pT, ps, int(steps)))
+        return self
+
+    def take_staged(self):
+        """Make the staged state the current one (lbm_take_staged; no host wait)."""
+        self._chk(N.lib().lbm_take_staged(self.h))
+        return self
+
     def info(self) -> dict:
         inf = N.Info()
         self._chk(N.lib().lbm_info(self.h, C.byref(inf)))

@@ -105,6 +105,8 @@ def test_null_handles_are_rejected(lib):
     assert lib.lbm_step(None, 1) == N.LBM_EINVAL
     assert lib.lbm_sync(None) == N.LBM_EINVAL
     assert lib.lbm_inject_fault(None, N.LBM_FAULT_STARVE_COLLIDE) == N.LBM_EINVAL
+    assert lib.lbm_stage_state_native(None, None, None, None, -1) == N.LBM_EINVAL
+    assert lib.lbm_take_staged(None) == N.LBM_EINVAL
     lib.lbm_destroy(None)
 
 

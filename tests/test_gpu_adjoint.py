@@ -179,6 +179,27 @@ def test_fp32_adjoint_against_fp64_adjoint(sub_case):
     assert max(errs.values()) < 1e-3, errs
 
 
+@pytest.mark.parametrize("f64", [True, False])
+def test_window_gradient_is_the_same_with_plain_launches(monkeypatch, f64):
+    # the window's forward pass steps with programmatic dependent launches (LBM_PDL=0 at creation
+    # launches plainly), its checkpoints then seed the recompute: the same gradient bits, on a
+    # lattice of many blocks per pass
+    from paper_1912_02018_gb300 import Sim
+
+    case = _fixed(si.cylinder_case(256, 128, 16.0, Re=300.0, superheat_Tc=0.05,
+                                   wall_dT=tuple(0.01 * si.uniform_pm1(5, 200)), name="256x128_D16"))
+    state = _spun_up(case, 200, f64=f64)
+    out = {}
+    for flag in ("1", "0"):
+        monkeypatch.setenv("LBM_PDL", flag)
+        sim = Sim.from_case(case, f64=f64)
+        sim.set_state(*state)
+        out[flag] = sim.adjoint_window(60, ckpt_every=20)
+    for k in ("J", "superheat", "u_in"):
+        assert out["1"][k] == out["0"][k], k
+    assert np.array_equal(np.asarray(out["1"]["wall_dT"]), np.asarray(out["0"]["wall_dT"]))
+
+
 def test_torch_autograd_function_gives_the_window_gradient(sub_case):
     import torch
 

@@ -290,6 +290,42 @@ def test_dependent_launches_give_the_same_bits(monkeypatch, f64, storage):
     assert out["1"][3] == out["0"][3]
 
 
+@pytest.mark.parametrize("f64,storage", [(False, "f32"), (True, "f64"), (False, "f16s")])
+def test_staged_restore_matches_the_synchronous_one(f64, storage):
+    # lbm_stage_state_native copies a state on the context's copy stream while the context
+    # steps; lbm_take_staged swaps it in.  Against lbm_set_state_native: same bits after the
+    # restore, with the copy overlapping steps of another state, and repeated takes of the same
+    # host arrays (pinned torch tensors); then the step counter and outlet rows kept
+    import torch
+
+    case = si.SMALL.replace(warmup=5)
+    a = Sim().from_case(case, f64=f64, storage=storage).step(30)
+    st = a.get_state_native()
+    a.step(7)
+    ref = Sim().from_case(case, f64=f64, storage=storage)
+    ref.set_state_native(*st)
+    ref.step(12)
+    want = (ref.fields(), ref.get_state_native())
+    f_h, T_h = torch.from_numpy(st[0]).pin_memory(), torch.from_numpy(st[1]).pin_memory()
+    for rep in range(3):
+        a.stage_state_native(f_h, T_h, st[2], st[3])
+        a.step(3)  # the current state steps while the staged one is copied
+        a.take_staged().step(12)
+        got = (a.fields(), a.get_state_native())
+        for k in FIELDS:
+            assert np.array_equal(got[0][k], want[0][k]), (rep, k)
+        for x, y in zip(got[1], want[1]):
+            assert np.array_equal(x, y), rep
+    # outlet rows kept (side None) and steps kept (-1): the counter continues from the take
+    n0 = a.get_state_native()[3]
+    a.stage_state_native(st[0], st[1]).take_staged()
+    assert a.get_state_native()[3] == n0
+    assert np.array_equal(a.get_state_native()[1], st[1])
+    from paper_1912_02018_gb300._native import LbmError
+    with pytest.raises(LbmError, match="ESTATE"):
+        a.take_staged()
+
+
 def test_checkpoint_restart_is_bit_exact():
     case = si.SMALL
     drho = case.drho()
