@@ -357,6 +357,7 @@ lbm_status lbm_create(const lbm_domain* domain, const lbm_cylinder* cyl, const l
   ph.body_fx = P.body_fx;
   ph.u_in = P.u_in;
   ph.U_out = P.outlet_U >= 0 ? P.outlet_U : P.u_in;
+  ph.U_k = ph.U_out / (1.0 + ph.U_out);
   c->lambda_v = rho_v * P.c_v * ph.alpha_v;
   {
     lbm::PhysC<float>& pf = phys.f;
@@ -365,6 +366,7 @@ lbm_status lbm_create(const lbm_domain* domain, const lbm_cylinder* cyl, const l
     pf.rho_l = (float)ph.rho_l, pf.rho_v = (float)ph.rho_v, pf.rho_s = (float)ph.rho_s;
     pf.nu_l = (float)ph.nu_l, pf.nu_v = (float)ph.nu_v, pf.alpha_l = (float)ph.alpha_l, pf.alpha_v = (float)ph.alpha_v;
     pf.c_v = (float)ph.c_v, pf.g = (float)ph.g, pf.u_in = (float)ph.u_in, pf.U_out = (float)ph.U_out;
+    pf.U_k = (float)ph.U_k;
     pf.body_fx = (float)ph.body_fx;
   }
   auto split = [](double v) {

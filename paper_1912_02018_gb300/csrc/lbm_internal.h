@@ -41,6 +41,7 @@ struct PhysC {
   C rho_l, rho_v, rho_s;
   C nu_l, nu_v, alpha_l, alpha_v, c_v;
   C g, u_in, U_out;
+  C U_k;      // U_out / (1 + U_out): the convective outlet's relaxation factor
   C body_fx;  // uniform body force along +x (0: none)
 };
 
